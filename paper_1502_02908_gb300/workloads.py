@@ -1,0 +1,274 @@
+"""Seeded synthetic inputs for the SISe / SISe3 event-based simulation.
+
+This module only draws inputs (herds, initial counts, per-replicate parameters
+and scheduled-event lists).  It holds none of the simulation arithmetic, so both
+the CUDA library and the CPU oracle can be fed from it.
+
+The paper's workloads (Sec. 4.1: the VTEC O157 model on 37,221 Swedish herds with
+register events; Sec. 4.2: a synthetic SIS benchmark) use data that is not
+available here.  The generators below draw inputs with the same shape: heavy
+tailed herd sizes, many more single-node (E1) than two-node (E2) events per day,
+power-law sources and preferential-attachment destinations.  Every array comes
+from ``numpy.random.Generator(PCG64(seed))``.
+
+Compartment order inside one node is class-major: SISe ``[S, I]``; SISe3
+``[S1, I1, S2, I2, S3, I3]`` (calves, young stock, adults).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SISE = 1
+SISE3 = 3
+
+EXIT, ENTER, INTERNAL, EXTERNAL = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Params:
+    """Per-replicate model constants, arrays with a leading replicate axis.
+
+    upsilon, gamma: [R, 3] (SISe uses column 0); alpha, epsilon: [R];
+    beta: [R, 4] seasonal decay values for day-of-year bins
+    [0, 91], (91, 182], (182, 273], (273, 364] (Sec. 4.1, seasonal beta).
+    """
+    upsilon: np.ndarray
+    gamma: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+    epsilon: np.ndarray
+
+    @staticmethod
+    def broadcast(R, upsilon, gamma, alpha, beta, epsilon):
+        ups = np.zeros((R, 3)); gam = np.zeros((R, 3))
+        u = np.atleast_1d(np.asarray(upsilon, dtype=np.float64))
+        g = np.atleast_1d(np.asarray(gamma, dtype=np.float64))
+        ups[:, :u.size] = u; gam[:, :g.size] = g
+        b = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+        bet = np.empty((R, 4)); bet[:] = b if b.size == 4 else b[0]
+        return Params(ups, gam, np.full(R, float(alpha)), bet, np.full(R, float(epsilon)))
+
+    def replicate(self, r):
+        return Params(self.upsilon[r:r + 1].copy(), self.gamma[r:r + 1].copy(),
+                      self.alpha[r:r + 1].copy(), self.beta[r:r + 1].copy(),
+                      self.epsilon[r:r + 1].copy())
+
+
+@dataclasses.dataclass
+class Events:
+    """Scheduled events as int32 structure-of-arrays (Sec. 3.2, E1/E2 records).
+
+    kind: EXIT / ENTER / INTERNAL (aging, class cls -> cls+1) / EXTERNAL
+    (node -> dest).  cls = -1 selects every class where sampling is involved.
+    dest = -1 for single-node events.
+    """
+    day: np.ndarray
+    kind: np.ndarray
+    node: np.ndarray
+    dest: np.ndarray
+    count: np.ndarray
+    cls: np.ndarray
+
+    def __len__(self):
+        return int(self.day.size)
+
+    @staticmethod
+    def empty():
+        z = np.zeros(0, np.int32)
+        return Events(z, z.copy(), z.copy(), z.copy(), z.copy(), z.copy())
+
+    def select(self, mask):
+        return Events(*(np.ascontiguousarray(getattr(self, f.name)[mask])
+                        for f in dataclasses.fields(self)))
+
+    def stable_by_day(self):
+        order = np.argsort(self.day, kind="stable")
+        return self.select(order)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    model: int
+    N: int
+    T: int
+    R: int
+    u0: np.ndarray          # [Nc, N] int32
+    phi0: np.ndarray        # [N] float64
+    params: Params
+    events: Events
+    seed: int               # Philox key
+
+    @property
+    def nc(self):
+        return 2 * (1 if self.model == SISE else 3)
+
+
+def _round_half_even(x):
+    return np.rint(x).astype(np.int64)
+
+
+def _split_classes(herd, frac=(0.2, 0.2, 0.6)):
+    """Largest-remainder split of each herd into three age classes."""
+    herd = np.asarray(herd, np.int64)
+    exact = herd[:, None] * np.asarray(frac)[None, :]
+    base = np.floor(exact).astype(np.int64)
+    rem = herd - base.sum(1)
+    frac_part = exact - base
+    # ties broken by class order (lower class first)
+    order = np.argsort(-frac_part, axis=1, kind="stable")
+    for k in range(3):
+        give = rem > k
+        rows = np.nonzero(give)[0]
+        base[rows, order[rows, k]] += 1
+    return base
+
+
+def _initial_counts(model, herd, prevalence=0.05):
+    if model == SISE:
+        i0 = _round_half_even(prevalence * herd)
+        return np.stack([herd - i0, i0]).astype(np.int32)
+    cls = _split_classes(herd)
+    out = np.zeros((6, herd.size), np.int32)
+    for j in range(3):
+        i0 = _round_half_even(prevalence * cls[:, j])
+        out[2 * j] = cls[:, j] - i0
+        out[2 * j + 1] = i0
+    return out
+
+
+def _uniform_events(rng, N, T, n_events, mix, max_count=5, aging=False):
+    """Events with uniform day and node, destination uniform != node."""
+    kinds = rng.choice(len(mix), size=n_events, p=np.asarray(mix, float))
+    day = rng.integers(0, T, size=n_events)
+    node = rng.integers(0, N, size=n_events)
+    dest = rng.integers(0, N - 1, size=n_events)
+    dest = dest + (dest >= node)                     # uniform over nodes != node
+    count = rng.integers(1, max_count + 1, size=n_events)
+    kind_map = np.array([EXIT, ENTER, EXTERNAL] if not aging else [EXIT, ENTER, INTERNAL, EXTERNAL])
+    kind = kind_map[kinds]
+    cls = np.where(kind == ENTER, 0, -1)
+    dest = np.where(kind == EXTERNAL, dest, -1)
+    ev = Events(day.astype(np.int32), kind.astype(np.int32), node.astype(np.int32),
+                dest.astype(np.int32), count.astype(np.int32), cls.astype(np.int32))
+    return ev.stable_by_day()
+
+
+def sise_plain(N=1000, T=365, n_events=20_000, seed=1, R=1, herd_lo=20, herd_hi=200,
+               upsilon=0.0357, gamma=0.1, alpha=1.0, beta=0.005, epsilon=1e-6, gen_seed=1):
+    """SISe on N nodes, herds U{20..200}, 5% initial prevalence, phi0 = 0; events
+    exit/enter/external 50/30/20 %, uniform day and node, 1-5 animals."""
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    herd = rng.integers(herd_lo, herd_hi + 1, size=N)
+    u0 = _initial_counts(SISE, herd)
+    ev = _uniform_events(rng, N, T, n_events, (0.5, 0.3, 0.2)) if n_events else Events.empty()
+    params = Params.broadcast(R, upsilon, gamma, alpha, beta, epsilon)
+    return Workload("sise_plain", SISE, N, T, R, u0, np.zeros(N), params, ev, seed)
+
+
+VTEC_UPSILON = (8e-3, 7e-3, 1e-3)          # Sec. 4.1, per age class
+VTEC_DELTA = (28.0, 25.0, 22.0)           # mean infectious period, days
+VTEC_BETA_DIV = (14.0, 26.0, 20.0, 12.0)  # beta = log(2)/k per season
+
+
+def vtec_beta():
+    return np.array([math.log(2.0) / k for k in VTEC_BETA_DIV])
+
+
+def _national_events(rng, N, T, n_events, mix=(0.4, 0.3, 0.2, 0.1), max_count=5,
+                     power=2.2):
+    """Register-shaped events: sources drawn with power-law weights (out-degree
+    exponent 2.2), external-transfer destinations by preferential attachment over
+    the events in day order (P(j) ~ in-degree so far + 1, j != source)."""
+    weights = rng.zipf(power, size=N).astype(np.float64)
+    weights = np.minimum(weights, N)
+    p = weights / weights.sum()
+    kinds = rng.choice(4, size=n_events, p=np.asarray(mix, float))
+    kind = np.array([EXIT, ENTER, INTERNAL, EXTERNAL])[kinds]
+    day = rng.integers(0, T, size=n_events)
+    node = rng.choice(N, size=n_events, p=p)
+    count = rng.integers(1, max_count + 1, size=n_events)
+    cls = np.full(n_events, -1, np.int64)
+    cls[kind == ENTER] = 0
+    aging = kind == INTERNAL
+    cls[aging] = rng.integers(0, 2, size=int(aging.sum()))
+    order = np.argsort(day, kind="stable")
+    day, kind, node, count, cls = day[order], kind[order], node[order], count[order], cls[order]
+    dest = np.full(n_events, -1, np.int64)
+    ext = np.nonzero(kind == EXTERNAL)[0]
+    # urn holding each node (in-degree + 1) times; uniform picks from it are
+    # preferential attachment
+    urn = np.empty(N + ext.size, np.int64)
+    urn[:N] = np.arange(N)
+    size = N
+    picks = rng.random(size=4 * ext.size + 16)
+    pi = 0
+    for e in ext:
+        src = node[e]
+        while True:
+            if pi >= picks.size:
+                picks = rng.random(size=picks.size)
+                pi = 0
+            j = urn[int(picks[pi] * size)]
+            pi += 1
+            if j != src:
+                break
+        dest[e] = j
+        urn[size] = j
+        size += 1
+    return Events(day.astype(np.int32), kind.astype(np.int32), node.astype(np.int32),
+                  dest.astype(np.int32), count.astype(np.int32), cls.astype(np.int32))
+
+
+def sise3_national(N=37_000, T=1460, n_events=3_000_000, seed=1, R=1, gen_seed=2):
+    """SISe3 with VTEC O157 constants (Sec. 4.1) on a national-scale synthetic
+    network: herds lognormal (median 50, sigma 1, capped at 5000) split 20/20/60
+    into calves/young/adults, 5% infected per class; seasonal beta."""
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    herd = np.minimum(5000, np.maximum(1, _round_half_even(rng.lognormal(math.log(50.0), 1.0, size=N))))
+    u0 = _initial_counts(SISE3, herd)
+    ev = _national_events(rng, N, T, n_events) if n_events else Events.empty()
+    gam = [1.0 / d for d in VTEC_DELTA]
+    params = Params.broadcast(R, VTEC_UPSILON, gam, 1.0, vtec_beta(), 1e-6)
+    return Workload("sise3_national", SISE3, N, T, R, u0, np.zeros(N), params, ev, seed)
+
+
+def sise3_batched(R=256, T=365, seed=1, base=None):
+    """The national SISe3 network and its events for days [0, T), R replicates,
+    each with its own (upsilon, gamma) log-uniform over +/-50% of the SISe
+    values 0.0357 and 0.1, shared by the three age classes."""
+    w = base if base is not None else sise3_national()
+    ev = w.events.select(w.events.day < T)
+    rng = np.random.Generator(np.random.PCG64(3))
+    ups = np.exp(rng.uniform(math.log(0.5 * 0.0357), math.log(1.5 * 0.0357), size=R))
+    gam = np.exp(rng.uniform(math.log(0.05), math.log(0.15), size=R))
+    params = Params(np.repeat(ups[:, None], 3, 1), np.repeat(gam[:, None], 3, 1),
+                    np.ones(R), np.repeat(vtec_beta()[None, :], R, 0), np.full(R, 1e-6))
+    return Workload("sise3_batched", SISE3, w.N, T, R, w.u0.copy(), w.phi0.copy(), params, ev, seed)
+
+
+def sise_gradient(N=10_000, R=4096, T=365, seed=4):
+    """SISe, config-1 style herds and events at 20 events per node-year."""
+    w = sise_plain(N=N, T=T, n_events=20 * N * T // 365, seed=seed, R=R, gen_seed=4)
+    w.name = "sise_gradient"
+    return w
+
+
+def tiny_node(model=SISE, herd=10, infected=1, R=1, copies=1, **kw):
+    """One herd (optionally repeated as independent nodes) with no events."""
+    if model == SISE:
+        u0 = np.array([[herd - infected], [infected]], np.int32)
+    else:
+        u0 = np.zeros((6, 1), np.int32)
+        u0[0, 0] = herd - infected
+        u0[1, 0] = infected
+    u0 = np.repeat(u0, copies, axis=1)
+    p = dict(upsilon=0.0, gamma=0.1, alpha=0.0, beta=0.0, epsilon=0.0)
+    p.update(kw.pop("params", {}))
+    params = Params.broadcast(R, **p)
+    phi0 = np.full(copies, float(kw.pop("phi0", 0.0)))
+    return Workload("tiny", model, copies, kw.pop("T", 1), R, u0, phi0, params,
+                    Events.empty(), kw.pop("seed", 1))
