@@ -1,0 +1,184 @@
+/*
+ * episim.h — C ABI of the GB300 event-based epidemic simulation library
+ * (libepisim.so), after Bauer, Engblom & Widgren, "Fast event-based
+ * epidemiological simulations on national scales" (arXiv:1502.02908).
+ *
+ * One simulated day, for every node (herd) and every replicate, is
+ *   1. the stochastic step: Gillespie's direct method per node on [d, d+1)
+ *      with the environmental variable phi frozen (Sec. 3.1 Eq. (numstep3);
+ *      Sec. 3.3 Eqs. (sampling), (sampling2); Alg. 1 lines 3-10);
+ *   2. the deterministic step: the day's scheduled events, applied so that the
+ *      result equals their input order (Sec. 3.2 Eq. (event); Sec. 3.3; Alg. 1
+ *      line 13);
+ *   3. the continuous-state update phi <- phi (1 - beta) + alpha I / N + epsilon
+ *      (Eq. (numstep5) with Eq. (siminfpressure); Alg. 1 line 14).
+ * Models: SISe (compartments S, I; S->I at upsilon phi S, I->S at gamma I) and
+ * SISe3 (the same per age class; Sec. 4.1 Eqs. (vtectrans)-(recovery_rates)).
+ *
+ * Conventions
+ *   - Compartments inside a node are class-major: SISe [S, I]; SISe3
+ *     [S1, I1, S2, I2, S3, I3].  Count arrays are int32 [R][Nc][N] (replicate,
+ *     compartment, node); phi is double [R][N].
+ *   - "host" pointers are read or written by the CPU; "device" pointers are
+ *     CUDA global-memory addresses on the current device.
+ *   - Every call returns a sim_status and never aborts or prints; the text of
+ *     the last error is sim_last_error(h).  Outputs are written only on SIM_OK.
+ *   - A handle belongs to one host thread at a time.  It owns all device memory
+ *     it allocates; it never frees memory the caller owns.
+ *   - Randomness is counter-based (Philox4x32-10): results do not depend on the
+ *     launch configuration, on how days are split across calls, or on which
+ *     other replicates run alongside.
+ */
+#ifndef EPISIM_H
+#define EPISIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sim_status {
+    SIM_OK = 0,
+    SIM_E_INVALID_ARG = 1,   /* an argument is out of range; nothing changed      */
+    SIM_E_OOM = 2,           /* host or device allocation failed                  */
+    SIM_E_CUDA = 3,          /* a CUDA call failed (launch, copy, stream)         */
+    SIM_E_UNDERFLOW = 4,     /* ERROR policy: an event asked for absent animals   */
+    SIM_E_TIMEOUT = 5,       /* a bounded device-side wait ran out                */
+    SIM_E_STATE = 6          /* call not valid in the handle's current state      */
+} sim_status;
+
+enum { SIM_SISE = 1, SIM_SISE3 = 3 };
+enum { SIM_UNDERFLOW_CLAMP = 0, SIM_UNDERFLOW_ERROR = 1 };
+enum { SIM_EXIT = 0, SIM_ENTER = 1, SIM_INTERNAL = 2, SIM_EXTERNAL = 3 };
+enum { SIM_HOST = 0, SIM_DEVICE = 1 };
+/* sim_config.flags */
+enum {
+    SIM_FLAG_PHI_PRE_EVENT = 1,  /* phi from post-SSA, pre-event counts (Eq. (numstep5) as printed) */
+    SIM_FLAG_SCORE = 2           /* accumulate score-function terms (sim_score) */
+};
+
+typedef struct sim_config {
+    int32_t model;            /* SIM_SISE or SIM_SISE3 */
+    int32_t n_nodes;          /* N >= 1 */
+    int32_t n_replicates;     /* R >= 1 */
+    int32_t max_days;         /* horizon; days [0, max_days) can be simulated */
+    int32_t underflow_policy; /* SIM_UNDERFLOW_CLAMP (default) or SIM_UNDERFLOW_ERROR */
+    int32_t flags;            /* SIM_FLAG_* */
+    uint64_t seed;            /* Philox key */
+} sim_config;
+
+/* Per-replicate model constants, host arrays with a leading replicate axis:
+ * upsilon, gamma [R][3] (SISe reads column 0), alpha, epsilon [R], beta [R][4]:
+ * decay for day-of-year bins [0,91], (91,182], (182,273], (273,364] (Sec. 4.1). */
+typedef struct sim_params {
+    const double* upsilon;
+    const double* gamma;
+    const double* alpha;
+    const double* beta;
+    const double* epsilon;
+} sim_params;
+
+typedef struct sim_handle sim_handle;
+
+/* Creates a simulation at day 0.  u0: host int32 [Nc][N] initial counts, the same
+ * for every replicate (>= 0); phi0: host double [N]; params: see sim_params.
+ * All inputs are copied.  Allocates the device state on the current device.
+ * *out is set only on SIM_OK. */
+sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,
+                      const sim_params* params, sim_handle** out);
+
+/* Loads the scheduled events (Sec. 3.2 Eq. (event)): n host int32 arrays in
+ * input order.  kind: SIM_EXIT / SIM_ENTER / SIM_INTERNAL (aging: class cls to
+ * cls+1 of the same node) / SIM_EXTERNAL (node -> dest).  cls: age class, or -1
+ * for "every class" (ENTER then means class 0).  count >= 0.  dest is read only
+ * for SIM_EXTERNAL and must differ from node.  Events on days >= max_days are
+ * kept but never reached.  Builds the per-day dependency levels (host, O(n)) and
+ * uploads them.  Callable once per handle, at day 0 (again after sim_reset with
+ * events cleared by sim_reset(h, 1)).  Errors: SIM_E_INVALID_ARG naming the first
+ * bad event, SIM_E_OOM, SIM_E_STATE. */
+sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const int32_t* kind,
+                           const int32_t* node, const int32_t* dest, const int32_t* count,
+                           const int32_t* cls);
+
+/* Advances every replicate by ndays days (ndays >= 0, day + ndays <= max_days),
+ * asynchronously on the CUDA stream `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Returns launch errors at once.  Device-side conditions
+ * (SIM_E_UNDERFLOW under the ERROR policy) are latched and returned by the next
+ * synchronising call (sim_state, sim_stats, sim_score, sim_sync). */
+sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream);
+
+/* Waits for the handle's work on `stream` and returns any latched device error. */
+sim_status sim_sync(sim_handle* h, void* stream);
+
+/* Copies the state at the start of the current day: counts int32 [R][Nc][N],
+ * phi double [R][N] (either may be NULL), and *day.  where = SIM_HOST or
+ * SIM_DEVICE says what the output pointers are.  Synchronises `stream`. */
+sim_status sim_state(sim_handle* h, int32_t* counts, double* phi, int32_t* day, int32_t where,
+                     void* stream);
+
+/* Replaces the state (checkpoint restore): counts [R][Nc][N] and phi [R][N] at
+ * the start of day `day` (0 <= day <= max_days).  Runs resumed from a state
+ * taken by sim_state are bit-identical to uninterrupted runs.  Statistics of
+ * days >= day are cleared.  Synchronises `stream`. */
+sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi, int32_t day,
+                         int32_t where, void* stream);
+
+/* Daily statistics since day 0: infected[R][max_days] and animals[R][max_days]
+ * (after each day's events; int64), counters[R][4] = SSA transitions fired,
+ * events applied, events clamped, events skipped (ERROR policy).  Any output
+ * may be NULL.  Host pointers.  Synchronises `stream`. */
+sim_status sim_stats(sim_handle* h, int64_t* infected, int64_t* animals, int64_t* counters,
+                     void* stream);
+
+/* Score-function terms (needs SIM_FLAG_SCORE): per node, d log p(path) /
+ * d theta for theta = [upsilon_1..3, gamma_1..3, beta, alpha], double
+ * [R][8][N] (host), accumulated since day 0 (or since the last sim_reset /
+ * sim_set_state).  The likelihood of a path is the product of the fired
+ * transitions' rates times exp(-integral of a0), from the direct method's
+ * sampling law; phi's dependence on beta and alpha is carried through Eq.
+ * (numstep5).  Synchronises `stream`. */
+sim_status sim_score(sim_handle* h, double* score, void* stream);
+
+/* Back to day 0 with the initial counts and phi; statistics and score cleared.
+ * clear_events = 1 also drops the loaded events. */
+sim_status sim_reset(sim_handle* h, int32_t clear_events);
+
+/* Frees everything the handle owns.  NULL is accepted. */
+void sim_destroy(sim_handle* h);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle.  NULL handle: text of the last sim_create failure. */
+const char* sim_last_error(const sim_handle* h);
+
+/* Event preprocessing alone, on the host, with no device and no handle: the
+ * validation and execution schedule sim_load_events builds (stable sort by day,
+ * then per-day dependency levels; Sec. 3.4 rearrangement with the ordering rule
+ * 2(b) of Sec. 3.6 applied per node).  For the n input events (same arrays and
+ * rules as sim_load_events) it writes, for the *n_scheduled events on days
+ * < max_days, in execution order (day, level, position): order[k] = the event's
+ * position in the day-stable order, level[k] = its level (>= 1).  Outputs are
+ * host arrays of at least n entries; any may be NULL.  Applying the levels in
+ * order, each level in any order, equals applying the events in input order. */
+sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days, int64_t n,
+                               const int32_t* day, const int32_t* kind, const int32_t* node,
+                               const int32_t* dest, const int32_t* count, const int32_t* cls,
+                               int64_t* order, int32_t* level, int64_t* n_scheduled);
+
+/* Test hook (not part of the simulation path): evaluates the library's
+ * -log(u) for u = (2 j + 1) 2^-53 on the GPU, for n device inputs j (uint64)
+ * into n device doubles.  Synchronous. */
+sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n);
+
+/* Test hook: the event schedule built by sim_load_events, host int64 [n]:
+ * the event's position in the day-stable order, listed in execution order
+ * (day, then dependency level, then position), and the level of each listed
+ * event (int32 [n]).  Either output may be NULL. */
+sim_status sim_debug_schedule(const sim_handle* h, int64_t* order, int32_t* level);
+/* Number of entries sim_debug_schedule writes (-1 for a NULL handle). */
+int64_t sim_debug_schedule_size(const sim_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPISIM_H */

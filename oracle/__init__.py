@@ -63,6 +63,9 @@ def load(path):
                          [P(ctypes.c_int32)] * 6 + \
                          [P(ctypes.c_int64), P(ctypes.c_int64), P(OrcCounters),
                           P(ctypes.c_double), P(ctypes.c_double)]
+    L.orc_apply_events.restype = ctypes.c_int
+    L.orc_apply_events.argtypes = [P(OrcCfg), P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_int64)] + \
+                                  [P(ctypes.c_int32)] * 6 + [P(OrcCounters)]
     L.orc_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
     L.orc_uniform.restype = ctypes.c_double
     L.orc_uniform.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -178,3 +181,17 @@ def run(w, ndays=None, d0=0, replicates=None, counts=None, phi=None, phi_pre_eve
         if score:
             sc[i] = s.reshape(8, w.N)
     return Result(out_c, out_p, pi, pn, ctrs, sc)
+
+
+def apply_events(w, counts, pos, events, replicate=0, underflow_error=False):
+    """Applies ``events`` (already in the wanted order) to ``counts`` [Nc, N] in place,
+    event k with Philox position pos[k]; returns the counters."""
+    L = lib()
+    cfg = make_cfg(w.model, w.N, w.params, replicate, w.seed, underflow_error=underflow_error)
+    ctr = OrcCounters()
+    pos = np.ascontiguousarray(pos, np.int64)
+    arr = [np.ascontiguousarray(a, np.int32) for a in (events.day, events.kind, events.node, events.dest,
+                                                       events.count, events.cls)]
+    L.orc_apply_events(ctypes.byref(cfg), _ptr(counts, ctypes.c_int32), len(pos), _ptr(pos, ctypes.c_int64),
+                       *[_ptr(a, ctypes.c_int32) for a in arr], ctypes.byref(ctr))
+    return (ctr.transitions, ctr.events_applied, ctr.events_clamped, ctr.events_skipped)

@@ -502,3 +502,19 @@ uint32_t orc_lemire_draw(uint64_t seed, int32_t replicate, int64_t ev_index, int
     for (uint32_t i = 0; i <= nth; ++i) r = lemire(&ws, s);
     return r;
 }
+
+/* Applies n scheduled events in the listed order (no stochastic step, no phi
+ * update); event k uses Philox counter word 0 = pos[k] and day day[k].  Used to
+ * check that an execution schedule reproduces the input order. */
+int orc_apply_events(const orc_cfg* c, int32_t* counts, int64_t n, const int64_t* pos,
+                     const int32_t* day, const int32_t* kind, const int32_t* node,
+                     const int32_t* dest, const int32_t* count, const int32_t* cls,
+                     orc_counters* ctr)
+{
+    const int32_t N = c->n_nodes;
+    orc_counters local = {0, 0, 0, 0};
+    if (!ctr) ctr = &local;
+    for (int64_t k = 0; k < n; ++k)
+        apply_event(c, counts, N, pos[k], day[k], kind[k], node[k], dest[k], count[k], cls[k], ctr);
+    return 0;
+}

@@ -1,0 +1,237 @@
+"""ctypes binding of libepisim (include/episim.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing or no CUDA
+device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_LIB = None
+_LOCK = threading.Lock()
+HEADER = pathlib.Path(__file__).resolve().parent.parent / "include" / "episim.h"
+
+SIM_OK, SIM_E_INVALID_ARG, SIM_E_OOM, SIM_E_CUDA, SIM_E_UNDERFLOW, SIM_E_TIMEOUT, SIM_E_STATE = range(7)
+SIM_HOST, SIM_DEVICE = 0, 1
+FLAG_PHI_PRE_EVENT, FLAG_SCORE = 1, 2
+STATUS_NAMES = {0: "SIM_OK", 1: "SIM_E_INVALID_ARG", 2: "SIM_E_OOM", 3: "SIM_E_CUDA",
+                4: "SIM_E_UNDERFLOW", 5: "SIM_E_TIMEOUT", 6: "SIM_E_STATE"}
+
+
+class SimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SimConfig(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("n_replicates", ctypes.c_int32), ("max_days", ctypes.c_int32),
+                ("underflow_policy", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class SimParams(ctypes.Structure):
+    _fields_ = [("upsilon", ctypes.POINTER(ctypes.c_double)), ("gamma", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("epsilon", ctypes.POINTER(ctypes.c_double))]
+
+
+def library_path() -> pathlib.Path:
+    from .build import LIB
+    return LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libepisim.so (building it first when missing)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = library_path()
+        if not path.exists():
+            if not build_if_missing:
+                raise FileNotFoundError(f"{path} not built")
+            from .build import build
+            build()
+        L = ctypes.CDLL(str(path))
+        P, i32, i64, vp = ctypes.POINTER, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        pi32, pi64, pd = P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double)
+        sigs = {
+            "sim_create": [P(SimConfig), pi32, pd, P(SimParams), P(vp)],
+            "sim_load_events": [vp, i64, pi32, pi32, pi32, pi32, pi32, pi32],
+            "sim_run_days": [vp, i32, vp],
+            "sim_sync": [vp, vp],
+            "sim_state": [vp, vp, vp, pi32, i32, vp],
+            "sim_set_state": [vp, vp, vp, i32, i32, vp],
+            "sim_stats": [vp, pi64, pi64, pi64, vp],
+            "sim_score": [vp, pd, vp],
+            "sim_reset": [vp, i32],
+            "sim_schedule_events": [i32, i32, i32, i64, pi32, pi32, pi32, pi32, pi32, pi32, pi64, pi32, pi64],
+            "sim_debug_neglog": [vp, vp, i64],
+            "sim_debug_schedule": [vp, pi64, pi32],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.sim_destroy.argtypes = [vp]
+        L.sim_destroy.restype = None
+        L.sim_last_error.argtypes = [vp]
+        L.sim_last_error.restype = ctypes.c_char_p
+        L.sim_debug_schedule_size.argtypes = [vp]
+        L.sim_debug_schedule_size.restype = ctypes.c_int64
+        _LIB = L
+        return L
+
+
+def header_symbols():
+    """Names of the functions include/episim.h declares."""
+    import re
+    text = HEADER.read_text()
+    return sorted(set(re.findall(r"^\s*(?:sim_status|void|const char\*|int64_t)\s+(sim_\w+)\s*\(", text, re.M)))
+
+
+def _p(a, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(L, h, status):
+    if status != SIM_OK:
+        msg = L.sim_last_error(h)
+        raise SimError(status, msg.decode() if msg else "")
+
+
+def current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def schedule_events(events: W.Events, n_nodes: int, model: int, max_days: int):
+    """Host-only event preprocessing: (order, level) in execution order."""
+    L = load_library()
+    n = len(events)
+    order = np.zeros(max(n, 1), np.int64)
+    level = np.zeros(max(n, 1), np.int32)
+    ns = ctypes.c_int64(0)
+    arr = [np.ascontiguousarray(a, np.int32) for a in (events.day, events.kind, events.node, events.dest,
+                                                       events.count, events.cls)]
+    st = L.sim_schedule_events(n_nodes, model, max_days, n, *[_p(a, ctypes.c_int32) for a in arr],
+                               _p(order, ctypes.c_int64), _p(level, ctypes.c_int32), ctypes.byref(ns))
+    _check(L, None, st)
+    return order[:ns.value].copy(), level[:ns.value].copy()
+
+
+class Sim:
+    """One simulation handle: R replicates of one model on N nodes."""
+
+    def __init__(self, model, u0, phi0, params: W.Params, max_days, seed=1,
+                 underflow_error=False, phi_pre_event=False, score=False):
+        self.L = load_library()
+        u0 = np.ascontiguousarray(u0, np.int32)
+        self.nc, self.N = u0.shape
+        self.model = model
+        self.R = params.upsilon.shape[0]
+        self.max_days = max_days
+        cfg = SimConfig(model, self.N, self.R, max_days, 1 if underflow_error else 0,
+                        (FLAG_PHI_PRE_EVENT if phi_pre_event else 0) | (FLAG_SCORE if score else 0), seed)
+        self._keep = [np.ascontiguousarray(x, np.float64) for x in
+                      (params.upsilon, params.gamma, params.alpha, params.beta, params.epsilon)]
+        sp = SimParams(*[_p(a, ctypes.c_double) for a in self._keep])
+        h = ctypes.c_void_p()
+        phi0 = np.ascontiguousarray(phi0, np.float64)
+        _check(self.L, None, self.L.sim_create(ctypes.byref(cfg), _p(u0, ctypes.c_int32), _p(phi0, ctypes.c_double),
+                                               ctypes.byref(sp), ctypes.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, w: W.Workload, events=True, max_days=None, **kw):
+        s = cls(w.model, w.u0, w.phi0, w.params, w.T if max_days is None else max_days, seed=w.seed, **kw)
+        if events and len(w.events):
+            s.load_events(w.events)
+        return s
+
+    def _stream(self, stream):
+        if stream is None:
+            return current_stream()
+        return ctypes.c_void_p(stream)
+
+    def load_events(self, ev: W.Events):
+        arr = [np.ascontiguousarray(a, np.int32) for a in (ev.day, ev.kind, ev.node, ev.dest, ev.count, ev.cls)]
+        _check(self.L, self.h, self.L.sim_load_events(self.h, len(ev), *[_p(a, ctypes.c_int32) for a in arr]))
+
+    def run(self, days, stream=None):
+        _check(self.L, self.h, self.L.sim_run_days(self.h, int(days), self._stream(stream)))
+
+    def sync(self, stream=None):
+        _check(self.L, self.h, self.L.sim_sync(self.h, self._stream(stream)))
+
+    def state(self, stream=None):
+        counts = np.empty((self.R, self.nc, self.N), np.int32)
+        phi = np.empty((self.R, self.N), np.float64)
+        day = ctypes.c_int32(0)
+        _check(self.L, self.h, self.L.sim_state(self.h, _p(counts, ctypes.c_int32), _p(phi, ctypes.c_double),
+                                                ctypes.byref(day), SIM_HOST, self._stream(stream)))
+        return counts, phi, day.value
+
+    def state_device(self, counts_t, phi_t, stream=None):
+        """Copies the state into torch CUDA tensors (int32 [R,Nc,N], float64 [R,N])."""
+        day = ctypes.c_int32(0)
+        _check(self.L, self.h, self.L.sim_state(self.h, ctypes.c_void_p(counts_t.data_ptr()),
+                                                ctypes.c_void_p(phi_t.data_ptr()), ctypes.byref(day),
+                                                SIM_DEVICE, self._stream(stream)))
+        return day.value
+
+    def set_state(self, counts, phi, day, stream=None):
+        counts = np.ascontiguousarray(counts, np.int32)
+        phi = np.ascontiguousarray(phi, np.float64)
+        _check(self.L, self.h, self.L.sim_set_state(self.h, counts.ctypes.data_as(ctypes.c_void_p),
+                                                    phi.ctypes.data_as(ctypes.c_void_p), int(day), SIM_HOST,
+                                                    self._stream(stream)))
+
+    def stats(self, stream=None):
+        pi = np.zeros((self.R, self.max_days), np.int64)
+        pn = np.zeros((self.R, self.max_days), np.int64)
+        ctr = np.zeros((self.R, 4), np.int64)
+        _check(self.L, self.h, self.L.sim_stats(self.h, _p(pi, ctypes.c_int64), _p(pn, ctypes.c_int64),
+                                                _p(ctr, ctypes.c_int64), self._stream(stream)))
+        return pi, pn, ctr
+
+    def score(self, stream=None):
+        out = np.zeros((self.R, 8, self.N), np.float64)
+        _check(self.L, self.h, self.L.sim_score(self.h, _p(out, ctypes.c_double), self._stream(stream)))
+        return out
+
+    def reset(self, clear_events=False):
+        _check(self.L, self.h, self.L.sim_reset(self.h, 1 if clear_events else 0))
+
+    def schedule(self):
+        n = self.L.sim_debug_schedule_size(self.h)
+        order = np.zeros(max(n, 1), np.int64)
+        level = np.zeros(max(n, 1), np.int32)
+        _check(self.L, self.h, self.L.sim_debug_schedule(self.h, _p(order, ctypes.c_int64), _p(level, ctypes.c_int32)))
+        return order[:n], level[:n]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def debug_neglog(j_dev_ptr, out_dev_ptr, n):
+    L = load_library()
+    st = L.sim_debug_neglog(ctypes.c_void_p(j_dev_ptr), ctypes.c_void_p(out_dev_ptr), int(n))
+    _check(L, None, st)

@@ -1,0 +1,514 @@
+// Host side of libepisim: the C ABI of include/episim.h, the event preprocessing
+// (stable sort by day, per-day dependency levels; Sec. 3.4 rearrangement and
+// the ordering rule 2(b) of Sec. 3.6, applied per node), device memory, and the
+// per-day launch sequence (Alg. 1: stochastic step, events, phi update).
+#include "../../include/episim.h"
+#include "internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace episim;
+
+struct sim_handle {
+  sim_config cfg{};
+  int n_age = 1, nc = 2;
+  std::vector<int32_t> u0;          // [Nc][N]
+  std::vector<double> phi0;         // [N]
+  std::vector<DevParams> params;    // [R]
+  // device state
+  int32_t* d_counts = nullptr;
+  double* d_phi = nullptr;
+  DevParams* d_params = nullptr;
+  unsigned long long* d_prev_i = nullptr;
+  unsigned long long* d_prev_n = nullptr;
+  unsigned long long* d_ctr = nullptr;
+  int32_t* d_err = nullptr;
+  double* d_score = nullptr;
+  double* d_tang = nullptr;
+  int32_t* d_u0 = nullptr;          // [Nc][N] master copy for resets
+  double* d_phi0 = nullptr;
+  // event schedule
+  bool events_loaded = false;
+  int4* d_rec = nullptr;
+  int32_t* d_lvl_start = nullptr;
+  int32_t* d_day_lvl = nullptr;
+  std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
+  std::vector<int32_t> sched_level;
+  std::vector<int32_t> day_lvl;      // [max_days + 1]
+  int32_t day = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+sim_status fail(sim_handle* h, sim_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_create_error = buf;
+  return s;
+}
+
+sim_status cuda_fail(sim_handle* h, cudaError_t e, const char* what) {
+  sim_status s = (e == cudaErrorMemoryAllocation) ? SIM_E_OOM : SIM_E_CUDA;
+  return fail(h, s, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                              \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+void free_events(sim_handle* h) {
+  cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
+  h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
+  h->sched_order.clear(); h->sched_level.clear(); h->day_lvl.clear();
+  h->events_loaded = false;
+}
+
+void free_all(sim_handle* h) {
+  free_events(h);
+  cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
+  cudaFree(h->d_prev_n); cudaFree(h->d_ctr); cudaFree(h->d_err); cudaFree(h->d_score);
+  cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0);
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+size_t n_counts(const sim_handle* h) { return (size_t)h->cfg.n_replicates * h->nc * h->cfg.n_nodes; }
+size_t n_phi(const sim_handle* h) { return (size_t)h->cfg.n_replicates * h->cfg.n_nodes; }
+
+// Initial state for every replicate and cleared accumulators (synchronous).
+sim_status reset_state(sim_handle* h) {
+  const size_t cbytes = (size_t)h->nc * h->cfg.n_nodes * sizeof(int32_t);
+  const size_t pbytes = (size_t)h->cfg.n_nodes * sizeof(double);
+  CK(h, launch_broadcast(h->d_counts, h->d_u0, cbytes, h->cfg.n_replicates, 0), "initial counts");
+  CK(h, launch_broadcast(h->d_phi, h->d_phi0, pbytes, h->cfg.n_replicates, 0), "initial phi");
+  const size_t stats = (size_t)h->cfg.n_replicates * (h->cfg.max_days > 0 ? h->cfg.max_days : 1);
+  CK(h, cudaMemset(h->d_prev_i, 0, stats * 8), "clear stats");
+  CK(h, cudaMemset(h->d_prev_n, 0, stats * 8), "clear stats");
+  CK(h, cudaMemset(h->d_ctr, 0, (size_t)h->cfg.n_replicates * 4 * 8), "clear counters");
+  CK(h, cudaMemset(h->d_err, 0, sizeof(int32_t)), "clear error");
+  if (h->d_score) {
+    CK(h, cudaMemset(h->d_score, 0, n_phi(h) * kScoreTerms * sizeof(double)), "clear score");
+    CK(h, cudaMemset(h->d_tang, 0, n_phi(h) * 2 * sizeof(double)), "clear tangents");
+  }
+  CK(h, cudaDeviceSynchronize(), "reset");
+  h->day = 0;
+  return SIM_OK;
+}
+
+sim_status check_latched(sim_handle* h) {
+  int32_t e = 0;
+  CK(h, cudaMemcpy(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost), "read device error word");
+  if (e) {
+    CK(h, cudaMemset(h->d_err, 0, sizeof(int32_t)), "clear device error word");
+    return fail(h, SIM_E_UNDERFLOW, "an event asked for more animals than present (ERROR policy)");
+  }
+  return SIM_OK;
+}
+
+SsaArgs ssa_args(sim_handle* h) {
+  SsaArgs a{};
+  a.counts = h->d_counts; a.phi = h->d_phi; a.params = h->d_params;
+  a.prev_i = h->d_prev_i; a.prev_n = h->d_prev_n; a.ctr = h->d_ctr;
+  a.score = h->d_score; a.tang = h->d_tang; a.seed = h->cfg.seed;
+  a.N = h->cfg.n_nodes; a.R = h->cfg.n_replicates; a.Nc = h->nc; a.max_days = h->cfg.max_days;
+  a.pre_event = (h->cfg.flags & SIM_FLAG_PHI_PRE_EVENT) ? 1 : 0;
+  return a;
+}
+
+
+struct Schedule {
+  std::vector<int4> rec;          // execution order
+  std::vector<int32_t> lvl_start; // [levels + 1]
+  std::vector<int32_t> day_lvl;   // [max_days + 1]
+  std::vector<int64_t> order;     // day-stable position of each record
+  std::vector<int32_t> level;
+};
+
+// Validates the events and builds the execution schedule: stable sort by day,
+// then per day a dependency level for each event.  A sampling event on node v
+// (exit, aging, transfer source) gets 1 + the highest level of any earlier event
+// of the day touching v; an add to w (enter, transfer destination) gets 1 + the
+// highest level of an earlier sampling of w; adds to one node commute and may
+// share a level.  Within a level events keep their day-stable order.  Applying
+// the levels in order, each level in any order, equals applying the events in
+// input order.  O(n + max_days) time.
+sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, const int32_t* day,
+                          const int32_t* kind, const int32_t* node, const int32_t* dest,
+                          const int32_t* count, const int32_t* cls, Schedule& S) {
+  if (n < 0 || n >= ((int64_t)1 << 31)) return fail(h, SIM_E_INVALID_ARG, "event count out of range");
+  if (n > 0 && (!day || !kind || !node || !dest || !count || !cls))
+    return fail(h, SIM_E_INVALID_ARG, "null event array");
+  int32_t dmax = T;
+  for (int64_t e = 0; e < n; ++e) {
+    const int k = kind[e];
+    if (day[e] < 0) return fail(h, SIM_E_INVALID_ARG, "event %lld: day < 0", (long long)e);
+    if (k < SIM_EXIT || k > SIM_EXTERNAL) return fail(h, SIM_E_INVALID_ARG, "event %lld: unknown kind %d", (long long)e, k);
+    if (node[e] < 0 || node[e] >= N) return fail(h, SIM_E_INVALID_ARG, "event %lld: node %d out of range", (long long)e, node[e]);
+    if (count[e] < 0 || count[e] >= (1 << 28)) return fail(h, SIM_E_INVALID_ARG, "event %lld: count %d out of range [0, 2^28)", (long long)e, count[e]);
+    if (cls[e] < -1 || cls[e] >= na) return fail(h, SIM_E_INVALID_ARG, "event %lld: class %d out of range", (long long)e, cls[e]);
+    if (k == SIM_INTERNAL && (cls[e] < 0 || cls[e] >= na - 1))
+      return fail(h, SIM_E_INVALID_ARG, "event %lld: aging needs a class with a next class", (long long)e);
+    if (k == SIM_EXTERNAL && (dest[e] < 0 || dest[e] >= N || dest[e] == node[e]))
+      return fail(h, SIM_E_INVALID_ARG, "event %lld: bad destination %d", (long long)e, dest[e]);
+    if (day[e] + 1 > dmax) dmax = day[e] + 1;
+  }
+  std::vector<int64_t> first, by_pos;
+  std::vector<int32_t> last_s, last_a, stamp, lvl_of;
+  std::vector<int64_t> bucket;
+  try {
+    first.assign((size_t)dmax + 1, 0);
+    by_pos.resize((size_t)n);
+    last_s.assign(N, 0); last_a.assign(N, 0); stamp.assign(N, -1);
+    S.day_lvl.assign((size_t)T + 1, 0);
+  } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  for (int64_t e = 0; e < n; ++e) first[(size_t)day[e] + 1]++;
+  for (int32_t d = 0; d < dmax; ++d) first[(size_t)d + 1] += first[(size_t)d];
+  {
+    std::vector<int64_t> fill(first.begin(), first.end() - 1);
+    for (int64_t e = 0; e < n; ++e) by_pos[(size_t)fill[(size_t)day[e]]++] = e;
+  }
+  const int64_t n_run = first[(size_t)T];          // events on days < max_days
+  try {
+    lvl_of.resize((size_t)n_run);
+    S.rec.resize((size_t)n_run);
+    S.order.resize((size_t)n_run);
+    S.level.resize((size_t)n_run);
+  } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  for (int32_t d = 0; d < T; ++d) {
+    S.day_lvl[d] = (int32_t)S.lvl_start.size();
+    const int64_t s0 = first[(size_t)d], s1 = first[(size_t)d + 1];
+    int32_t max_lvl = 0;
+    auto touch = [&](int v) { if (stamp[v] != d) { stamp[v] = d; last_s[v] = 0; last_a[v] = 0; } };
+    for (int64_t s = s0; s < s1; ++s) {
+      const int64_t e = by_pos[(size_t)s];
+      const int k = kind[e], v = node[e];
+      touch(v);
+      int32_t L;
+      if (k == SIM_ENTER) {
+        L = last_s[v] + 1;
+        if (L > last_a[v]) last_a[v] = L;
+      } else {
+        L = (last_s[v] > last_a[v] ? last_s[v] : last_a[v]) + 1;
+        if (k == SIM_EXTERNAL) {
+          const int w = dest[e];
+          touch(w);
+          if (last_s[w] + 1 > L) L = last_s[w] + 1;
+          if (L > last_a[w]) last_a[w] = L;
+        }
+        last_s[v] = L;
+      }
+      lvl_of[(size_t)s] = L;
+      if (L > max_lvl) max_lvl = L;
+    }
+    bucket.assign((size_t)max_lvl + 2, 0);
+    for (int64_t s = s0; s < s1; ++s) bucket[(size_t)lvl_of[(size_t)s] + 1]++;
+    for (int32_t L = 0; L <= max_lvl; ++L) bucket[(size_t)L + 1] += bucket[(size_t)L];
+    for (int32_t L = 1; L <= max_lvl; ++L) S.lvl_start.push_back((int32_t)(s0 + bucket[(size_t)L]));
+    for (int64_t s = s0; s < s1; ++s) {
+      const int64_t e = by_pos[(size_t)s];
+      const size_t slot = (size_t)(s0 + bucket[(size_t)lvl_of[(size_t)s]]++);
+      const uint32_t packed = (uint32_t)kind[e] | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
+      S.rec[slot] = make_int4(node[e], kind[e] == SIM_EXTERNAL ? dest[e] : -1, (int32_t)s, (int32_t)packed);
+      S.order[slot] = s;
+      S.level[slot] = lvl_of[(size_t)s];
+    }
+  }
+  S.day_lvl[T] = (int32_t)S.lvl_start.size();
+  S.lvl_start.push_back((int32_t)n_run);
+  return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,
+                      const sim_params* p, sim_handle** out) {
+  if (!cfg || !u0 || !phi0 || !p || !out) return fail(nullptr, SIM_E_INVALID_ARG, "null argument");
+  if (cfg->model != SIM_SISE && cfg->model != SIM_SISE3)
+    return fail(nullptr, SIM_E_INVALID_ARG, "model must be SIM_SISE (1) or SIM_SISE3 (3)");
+  if (cfg->n_nodes < 1 || cfg->n_replicates < 1 || cfg->max_days < 0)
+    return fail(nullptr, SIM_E_INVALID_ARG, "n_nodes, n_replicates must be >= 1 and max_days >= 0");
+  if (cfg->underflow_policy != SIM_UNDERFLOW_CLAMP && cfg->underflow_policy != SIM_UNDERFLOW_ERROR)
+    return fail(nullptr, SIM_E_INVALID_ARG, "unknown underflow policy");
+  if (cfg->flags & ~(SIM_FLAG_PHI_PRE_EVENT | SIM_FLAG_SCORE))
+    return fail(nullptr, SIM_E_INVALID_ARG, "unknown flag bits");
+  if (!p->upsilon || !p->gamma || !p->alpha || !p->beta || !p->epsilon)
+    return fail(nullptr, SIM_E_INVALID_ARG, "null parameter array");
+  sim_handle* h = new (std::nothrow) sim_handle();
+  if (!h) return fail(nullptr, SIM_E_OOM, "host allocation");
+  h->cfg = *cfg;
+  h->n_age = cfg->model == SIM_SISE3 ? 3 : 1;
+  h->nc = 2 * h->n_age;
+  const int N = cfg->n_nodes, R = cfg->n_replicates;
+  try {
+    h->u0.assign(u0, u0 + (size_t)h->nc * N);
+    h->phi0.assign(phi0, phi0 + N);
+    h->params.resize(R);
+  } catch (...) {
+    delete h;
+    return fail(nullptr, SIM_E_OOM, "host allocation");
+  }
+  for (size_t i = 0; i < h->u0.size(); ++i)
+    if (h->u0[i] < 0) { delete h; return fail(nullptr, SIM_E_INVALID_ARG, "u0[%zu] < 0", i); }
+  for (int v = 0; v < N; ++v) {
+    int64_t tot = 0;
+    for (int c = 0; c < h->nc; ++c) tot += h->u0[(size_t)c * N + v];
+    if (tot > (1 << 30)) { delete h; return fail(nullptr, SIM_E_INVALID_ARG, "node %d holds more than 2^30 animals", v); }
+    if (!finite_nonneg(phi0[v])) { delete h; return fail(nullptr, SIM_E_INVALID_ARG, "phi0[%d] must be finite and >= 0", v); }
+  }
+  for (int r = 0; r < R; ++r) {
+    DevParams& d = h->params[r];
+    std::memset(&d, 0, sizeof d);
+    for (int j = 0; j < 3; ++j) {
+      d.ups[j] = p->upsilon[(size_t)r * 3 + j];
+      d.gam[j] = p->gamma[(size_t)r * 3 + j];
+    }
+    d.alpha = p->alpha[r];
+    for (int s = 0; s < 4; ++s) d.beta[s] = p->beta[(size_t)r * 4 + s];
+    d.eps = p->epsilon[r];
+    bool ok = finite_nonneg(d.alpha) && finite_nonneg(d.eps);
+    for (int j = 0; j < 3; ++j) ok = ok && finite_nonneg(d.ups[j]) && finite_nonneg(d.gam[j]);
+    for (int s = 0; s < 4; ++s) ok = ok && finite_nonneg(d.beta[s]) && d.beta[s] <= 1.0;
+    if (!ok) {
+      delete h;
+      return fail(nullptr, SIM_E_INVALID_ARG,
+                  "replicate %d: parameters must be finite, >= 0, and beta <= 1", r);
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  const size_t stats = (size_t)R * (cfg->max_days > 0 ? cfg->max_days : 1);
+  if (e == cudaSuccess) e = dalloc(&h->d_counts, n_counts(h));
+  if (e == cudaSuccess) e = dalloc(&h->d_phi, n_phi(h));
+  if (e == cudaSuccess) e = dalloc(&h->d_params, (size_t)R);
+  if (e == cudaSuccess) e = dalloc(&h->d_prev_i, stats);
+  if (e == cudaSuccess) e = dalloc(&h->d_prev_n, stats);
+  if (e == cudaSuccess) e = dalloc(&h->d_ctr, (size_t)R * 4);
+  if (e == cudaSuccess) e = dalloc(&h->d_err, 1);
+  if (e == cudaSuccess) e = dalloc(&h->d_u0, h->u0.size());
+  if (e == cudaSuccess) e = dalloc(&h->d_phi0, h->phi0.size());
+  if (e == cudaSuccess && (cfg->flags & SIM_FLAG_SCORE)) {
+    e = dalloc(&h->d_score, n_phi(h) * kScoreTerms);
+    if (e == cudaSuccess) e = dalloc(&h->d_tang, n_phi(h) * 2);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_params, h->params.data(), R * sizeof(DevParams), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_u0, h->u0.data(), h->u0.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_phi0, h->phi0.data(), h->phi0.size() * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    sim_status s = cuda_fail(nullptr, e, "device allocation / upload");
+    free_all(h);
+    delete h;
+    return s;
+  }
+  sim_status s = reset_state(h);
+  if (s != SIM_OK) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const int32_t* kind,
+                           const int32_t* node, const int32_t* dest, const int32_t* count,
+                           const int32_t* cls) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (h->events_loaded) return fail(h, SIM_E_STATE, "events already loaded (sim_reset(h, 1) drops them)");
+  if (h->day != 0) return fail(h, SIM_E_STATE, "events must be loaded at day 0");
+  Schedule S;
+  sim_status st = build_schedule(h, h->cfg.n_nodes, h->n_age, h->cfg.max_days, n, day, kind, node, dest,
+                                 count, cls, S);
+  if (st != SIM_OK) return st;
+  free_events(h);
+  const int32_t T = h->cfg.max_days;
+  cudaError_t err = cudaSuccess;
+  if (err == cudaSuccess) err = dalloc(&h->d_rec, S.rec.size());
+  if (err == cudaSuccess) err = dalloc(&h->d_lvl_start, S.lvl_start.size());
+  if (err == cudaSuccess) err = dalloc(&h->d_day_lvl, (size_t)T + 1);
+  if (err == cudaSuccess && !S.rec.empty()) err = cudaMemcpy(h->d_rec, S.rec.data(), S.rec.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(h->d_lvl_start, S.lvl_start.data(), S.lvl_start.size() * 4, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(h->d_day_lvl, S.day_lvl.data(), S.day_lvl.size() * 4, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
+  h->sched_order.swap(S.order);
+  h->sched_level.swap(S.level);
+  h->day_lvl.swap(S.day_lvl);
+  h->events_loaded = true;
+  return SIM_OK;
+}
+
+sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days, int64_t n,
+                               const int32_t* day, const int32_t* kind, const int32_t* node,
+                               const int32_t* dest, const int32_t* count, const int32_t* cls,
+                               int64_t* order, int32_t* level, int64_t* n_scheduled) {
+  if (n_nodes < 1 || max_days < 0 || (model != SIM_SISE && model != SIM_SISE3))
+    return fail(nullptr, SIM_E_INVALID_ARG, "bad n_nodes / model / max_days");
+  Schedule S;
+  sim_status st = build_schedule(nullptr, n_nodes, model == SIM_SISE3 ? 3 : 1, max_days, n, day, kind,
+                                 node, dest, count, cls, S);
+  if (st != SIM_OK) return st;
+  if (order) std::memcpy(order, S.order.data(), S.order.size() * 8);
+  if (level) std::memcpy(level, S.level.data(), S.level.size() * 4);
+  if (n_scheduled) *n_scheduled = (int64_t)S.order.size();
+  return SIM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (ndays < 0 || (int64_t)h->day + ndays > h->cfg.max_days)
+    return fail(h, SIM_E_INVALID_ARG, "ndays %d from day %d passes max_days %d", ndays, h->day, h->cfg.max_days);
+  if (ndays == 0) return SIM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool score = (h->cfg.flags & SIM_FLAG_SCORE) != 0;
+  SsaArgs a = ssa_args(h);
+  EvArgs ev{};
+  ev.counts = h->d_counts; ev.rec = h->d_rec; ev.lvl_start = h->d_lvl_start; ev.day_lvl = h->d_day_lvl;
+  ev.ctr = h->d_ctr; ev.err = h->d_err; ev.seed = h->cfg.seed;
+  ev.N = h->cfg.n_nodes; ev.R = h->cfg.n_replicates; ev.Nc = h->nc;
+  ev.underflow_error = h->cfg.underflow_policy == SIM_UNDERFLOW_ERROR;
+  const int32_t d0 = h->day;
+  for (int32_t d = d0; d < d0 + ndays; ++d) {
+    a.day = d;
+    a.prologue = d > d0;
+    CK(h, launch_ssa_day(a, h->n_age, score, st), "stochastic step launch");
+    if (h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]) {
+      ev.day = d;
+      CK(h, launch_events_day(ev, h->n_age, st), "event step launch");
+    }
+  }
+  a.day = d0 + ndays - 1;
+  CK(h, launch_finalize(a, h->n_age, score, st), "phi update launch");
+  h->day = d0 + ndays;
+  return SIM_OK;
+}
+
+sim_status sim_sync(sim_handle* h, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  CK(h, cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+  return check_latched(h);
+}
+
+sim_status sim_state(sim_handle* h, int32_t* counts, double* phi, int32_t* day, int32_t where,
+                     void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (where != SIM_HOST && where != SIM_DEVICE) return fail(h, SIM_E_INVALID_ARG, "where must be SIM_HOST or SIM_DEVICE");
+  cudaStream_t st = (cudaStream_t)stream;
+  const cudaMemcpyKind k = where == SIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (counts) CK(h, cudaMemcpyAsync(counts, h->d_counts, n_counts(h) * 4, k, st), "copy counts");
+  if (phi) CK(h, cudaMemcpyAsync(phi, h->d_phi, n_phi(h) * 8, k, st), "copy phi");
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  if (day) *day = h->day;
+  return check_latched(h);
+}
+
+sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi, int32_t day,
+                         int32_t where, void* stream) {
+  if (!h || !counts || !phi) return SIM_E_INVALID_ARG;
+  if (where != SIM_HOST && where != SIM_DEVICE) return fail(h, SIM_E_INVALID_ARG, "where must be SIM_HOST or SIM_DEVICE");
+  if (day < 0 || day > h->cfg.max_days) return fail(h, SIM_E_INVALID_ARG, "day %d out of range", day);
+  if (where == SIM_HOST) {
+    for (size_t i = 0; i < n_counts(h); ++i)
+      if (counts[i] < 0) return fail(h, SIM_E_INVALID_ARG, "counts[%zu] < 0", i);
+    for (size_t i = 0; i < n_phi(h); ++i)
+      if (!finite_nonneg(phi[i])) return fail(h, SIM_E_INVALID_ARG, "phi[%zu] must be finite and >= 0", i);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const cudaMemcpyKind k = where == SIM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(h, cudaMemcpyAsync(h->d_counts, counts, n_counts(h) * 4, k, st), "copy counts");
+  CK(h, cudaMemcpyAsync(h->d_phi, phi, n_phi(h) * 8, k, st), "copy phi");
+  const int T = h->cfg.max_days;
+  if (T > day) {
+    const size_t w = (size_t)(T - day) * 8, pitch = (size_t)T * 8;
+    CK(h, cudaMemset2DAsync(h->d_prev_i + day, pitch, 0, w, h->cfg.n_replicates, st), "clear stats");
+    CK(h, cudaMemset2DAsync(h->d_prev_n + day, pitch, 0, w, h->cfg.n_replicates, st), "clear stats");
+  }
+  if (h->d_score) {
+    CK(h, cudaMemsetAsync(h->d_score, 0, n_phi(h) * kScoreTerms * 8, st), "clear score");
+    CK(h, cudaMemsetAsync(h->d_tang, 0, n_phi(h) * 2 * 8, st), "clear tangents");
+  }
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  h->day = day;
+  return SIM_OK;
+}
+
+sim_status sim_stats(sim_handle* h, int64_t* infected, int64_t* animals, int64_t* counters, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t stats = (size_t)h->cfg.n_replicates * h->cfg.max_days;
+  if (infected && stats) CK(h, cudaMemcpyAsync(infected, h->d_prev_i, stats * 8, cudaMemcpyDeviceToHost, st), "copy stats");
+  if (animals && stats) CK(h, cudaMemcpyAsync(animals, h->d_prev_n, stats * 8, cudaMemcpyDeviceToHost, st), "copy stats");
+  if (counters) CK(h, cudaMemcpyAsync(counters, h->d_ctr, (size_t)h->cfg.n_replicates * 32, cudaMemcpyDeviceToHost, st), "copy counters");
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  return check_latched(h);
+}
+
+sim_status sim_score(sim_handle* h, double* score, void* stream) {
+  if (!h || !score) return SIM_E_INVALID_ARG;
+  if (!h->d_score) return fail(h, SIM_E_STATE, "created without SIM_FLAG_SCORE");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(score, h->d_score, n_phi(h) * kScoreTerms * 8, cudaMemcpyDeviceToHost, st), "copy score");
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  return check_latched(h);
+}
+
+sim_status sim_reset(sim_handle* h, int32_t clear_events) {
+  if (!h) return SIM_E_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  if (clear_events) free_events(h);
+  return reset_state(h);
+}
+
+void sim_destroy(sim_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+const char* sim_last_error(const sim_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n) {
+  if (n < 0 || (n > 0 && (!j_dev || !out_dev))) return SIM_E_INVALID_ARG;
+  cudaError_t e = launch_debug_neglog(j_dev, out_dev, n, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+}
+
+sim_status sim_debug_schedule(const sim_handle* h, int64_t* order, int32_t* level) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (order) std::memcpy(order, h->sched_order.data(), h->sched_order.size() * 8);
+  if (level) std::memcpy(level, h->sched_level.data(), h->sched_level.size() * 4);
+  return SIM_OK;
+}
+
+int64_t sim_debug_schedule_size(const sim_handle* h) { return h ? (int64_t)h->sched_order.size() : -1; }
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal interfaces between the host side of libepisim (host.cpp) and its
+// CUDA kernels.  Not part of the public ABI (include/episim.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace episim {
+
+constexpr int kMaxAge = 3;
+constexpr int kMaxComp = 2 * kMaxAge;
+
+// Per-replicate constants, 128 bytes.
+struct DevParams {
+  double ups[3];
+  double gam[3];
+  double alpha;
+  double beta[4];
+  double eps;
+  double pad[4];
+};
+static_assert(sizeof(DevParams) == 128, "DevParams layout");
+
+// Score-function accumulators per node: [upsilon_1..3, gamma_1..3, beta, alpha].
+constexpr int kScoreTerms = 8;
+
+struct SsaArgs {
+  int32_t* counts;            // [R][Nc][N]
+  double* phi;                // [R][N]
+  const DevParams* params;    // [R]
+  unsigned long long* prev_i; // [R][max_days]
+  unsigned long long* prev_n; // [R][max_days]
+  unsigned long long* ctr;    // [R][4]
+  double* score;              // [R][8][N] (score mode)
+  double* tang;               // [R][2][N]: d phi/d beta, d phi/d alpha (score mode)
+  uint64_t seed;
+  int32_t N, R, Nc, max_days;
+  int32_t day;                // day simulated by this launch
+  int32_t prologue;           // 1: first record stats of day-1 and (post-event mode) update phi
+  int32_t pre_event;          // 1: phi update from post-SSA counts in the epilogue
+};
+
+// One scheduled event, 16 bytes: node, dest, position in the day-stable order,
+// and kind (bits 0-1) | (cls + 1) (bits 2-3) | count (bits 4-31).
+struct EvArgs {
+  int32_t* counts;
+  const int4* rec;            // records sorted by (day, level, position)
+  const int32_t* lvl_start;   // [n_levels + 1] record offsets
+  const int32_t* day_lvl;     // [max_days + 1] level offsets of each day
+  unsigned long long* ctr;    // [R][4]
+  int32_t* err;               // bit 0: underflow under the ERROR policy
+  uint64_t seed;
+  int32_t N, R, Nc;
+  int32_t day;
+  int32_t underflow_error;
+};
+
+struct FinalizeArgs {
+  SsaArgs s;                  // day = last simulated day; prologue semantics for day+1
+};
+
+cudaError_t launch_ssa_day(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
+cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
+// After the last day of a call: phi update (post-event mode) and statistics of day a.day.
+cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
+cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st);
+
+}  // namespace episim
+
+namespace episim {
+// dst holds `copies` back-to-back copies of the `bytes` bytes at src (device pointers).
+cudaError_t launch_broadcast(void* dst, const void* src, size_t bytes, int copies, cudaStream_t st);
+}  // namespace episim

@@ -1,0 +1,256 @@
+// Stochastic step (Eq. (numstep3)): Gillespie's direct method per node on
+// [d, d+1) with phi frozen (Sec. 3.3, Eqs. (sampling) and (sampling2); Alg. 1
+// lines 3-10), one thread per (replicate, node).  The continuous-state update of
+// the previous day (Eq. (numstep5) with Eq. (siminfpressure); Alg. 1 line 14)
+// is fused into the prologue, as Alg. 2 line 5 places it at the start of the
+// next stochastic task; the day's infected/total statistics are reduced there too.
+//
+// Arithmetic (identical, by specification, to the CPU oracle): per class j,
+//   a_inf = (upsilon_j * phi) * S_j, a_rec = gamma_j * I_j, A_j = a_inf + a_rec,
+//   a0 = A_1 or (A_1 + A_2) + A_3;  tau = E / a0;  stop when t + tau >= 1;
+//   r = a0 * u2 selects inf_1, rec_1, inf_2, ... by left-to-right thresholds.
+// IEEE binary64 operations are explicit intrinsics (never contracted).
+#include "internal.h"
+#include "devmath.cuh"
+
+namespace episim {
+
+template <int NA>
+struct NodeState {
+  int32_t x[2 * NA];
+};
+
+template <int NA>
+__device__ __forceinline__ void load_counts(const SsaArgs& a, int r, int v, NodeState<NA>& s) {
+  const int32_t* base = a.counts + (size_t)r * a.Nc * a.N + v;
+#pragma unroll
+  for (int c = 0; c < 2 * NA; ++c) s.x[c] = base[(size_t)c * a.N];
+}
+
+template <int NA>
+__device__ __forceinline__ void store_counts(const SsaArgs& a, int r, int v, const NodeState<NA>& s) {
+  int32_t* base = a.counts + (size_t)r * a.Nc * a.N + v;
+#pragma unroll
+  for (int c = 0; c < 2 * NA; ++c) base[(size_t)c * a.N] = s.x[c];
+}
+
+// phi_{d+1} = ((phi_d (1 - beta(d))) + (alpha I) / N) + eps; tangents d phi/d beta,
+// d phi/d alpha carried alongside in score mode.
+template <int NA, bool SCORE>
+__device__ __forceinline__ double phi_step(const SsaArgs& a, const DevParams& p, int r, int v, int day,
+                                           const NodeState<NA>& s, double phi) {
+  int32_t I = 0, tot = 0;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) { I += s.x[2 * j + 1]; tot += s.x[2 * j] + s.x[2 * j + 1]; }
+  double omb = __dadd_rn(1.0, -p.beta[season_of(day)]);
+  double q = 0.0;
+  double dI = i2d_exact(I), dN = i2d_exact(tot);
+  if (tot > 0) q = __ddiv_rn(__dmul_rn(p.alpha, dI), dN);
+  double next = __dadd_rn(__dadd_rn(__dmul_rn(phi, omb), q), p.eps);
+  if (SCORE) {
+    double* tb = a.tang + ((size_t)r * 2 + 0) * a.N + v;
+    double* ta = a.tang + ((size_t)r * 2 + 1) * a.N + v;
+    double ion = tot > 0 ? __ddiv_rn(dI, dN) : 0.0;
+    *tb = __dsub_rn(__dmul_rn(*tb, omb), phi);
+    *ta = __dadd_rn(__dmul_rn(*ta, omb), ion);
+  }
+  return next;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+struct DayTerms {
+  double n_inf, n_rec, int_s, int_i, tlast;
+};
+
+// The direct method for one node-day; returns the number of transitions fired.
+template <int NA, bool SCORE>
+__device__ __forceinline__ uint32_t ssa_node_day(const DevParams& p, uint64_t seed, int r, int v, int day,
+                                                 double phi, NodeState<NA>& s, DayTerms (&T)[NA]) {
+  double cinf[NA], ainf[NA], arec[NA], A[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    cinf[j] = __dmul_rn(p.ups[j], phi);
+    ainf[j] = __dmul_rn(cinf[j], i2d_exact(s.x[2 * j]));
+    arec[j] = __dmul_rn(p.gam[j], i2d_exact(s.x[2 * j + 1]));
+    A[j] = __dadd_rn(ainf[j], arec[j]);
+    if (SCORE) { T[j].n_inf = T[j].n_rec = T[j].int_s = T[j].int_i = 0.0; T[j].tlast = 0.0; }
+  }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  double t = 0.0;
+  uint32_t fired = 0;
+  for (uint32_t k = 0;; ++k) {
+    double P[NA];
+    P[0] = A[0];
+#pragma unroll
+    for (int j = 1; j < NA; ++j) P[j] = __dadd_rn(P[j - 1], A[j]);
+    const double a0 = P[NA - 1];
+    if (!pos(a0)) break;
+    uint4 w = philox10(make_uint4((uint32_t)v, (uint32_t)day, k, (uint32_t)r), k0, k1);
+    double E = neglog_u(((((uint64_t)w.y) << 32) | w.x) >> 12);
+    double u2 = uniform_open(w.z, w.w);
+    double tn = __dadd_rn(t, __ddiv_rn(E, a0));
+    if (le_nonneg(1.0, tn)) break;
+    t = tn;
+    double rr = __dmul_rn(a0, u2);
+    // class: first with A_j > 0 and r <= P_j, else the last positive one
+    int cls = -1, last = -1;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      if (cls < 0 && pos(A[j])) {
+        last = j;
+        if (le_nonneg(rr, P[j])) cls = j;
+      }
+    }
+    if (cls < 0) cls = last;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      if (j != cls) continue;
+      double thr = (j == 0) ? ainf[0] : __dadd_rn(P[j > 0 ? j - 1 : 0], ainf[j]);
+      bool infect = pos(ainf[j]) && (le_nonneg(rr, thr) || !pos(arec[j]));
+      if (SCORE) {
+        double dt = __dsub_rn(t, T[j].tlast);
+        T[j].int_s = __dadd_rn(T[j].int_s, __dmul_rn(i2d_exact(s.x[2 * j]), dt));
+        T[j].int_i = __dadd_rn(T[j].int_i, __dmul_rn(i2d_exact(s.x[2 * j + 1]), dt));
+        T[j].tlast = t;
+        if (infect) T[j].n_inf = __dadd_rn(T[j].n_inf, 1.0); else T[j].n_rec = __dadd_rn(T[j].n_rec, 1.0);
+      }
+      if (infect) { s.x[2 * j] -= 1; s.x[2 * j + 1] += 1; }
+      else        { s.x[2 * j + 1] -= 1; s.x[2 * j] += 1; }
+      ainf[j] = __dmul_rn(cinf[j], i2d_exact(s.x[2 * j]));
+      arec[j] = __dmul_rn(p.gam[j], i2d_exact(s.x[2 * j + 1]));
+      A[j] = __dadd_rn(ainf[j], arec[j]);
+    }
+    ++fired;
+  }
+  if (SCORE) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      double dt = __dsub_rn(1.0, T[j].tlast);
+      T[j].int_s = __dadd_rn(T[j].int_s, __dmul_rn(i2d_exact(s.x[2 * j]), dt));
+      T[j].int_i = __dadd_rn(T[j].int_i, __dmul_rn(i2d_exact(s.x[2 * j + 1]), dt));
+    }
+  }
+  return fired;
+}
+
+// Adds one node-day's score terms to the node's accumulators (same op order as
+// the oracle).
+template <int NA>
+__device__ __forceinline__ void accumulate_score(const SsaArgs& a, const DevParams& p, int r, int v,
+                                                 double phi, const DayTerms (&T)[NA]) {
+  double* sc = a.score + (size_t)r * kScoreTerms * a.N + v;
+  double ups_int = 0.0;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    double gu = pos(p.ups[j]) ? __ddiv_rn(T[j].n_inf, p.ups[j]) : 0.0;
+    sc[(size_t)j * a.N] = __dadd_rn(sc[(size_t)j * a.N], __dsub_rn(gu, __dmul_rn(phi, T[j].int_s)));
+    double gg = pos(p.gam[j]) ? __ddiv_rn(T[j].n_rec, p.gam[j]) : 0.0;
+    sc[(size_t)(3 + j) * a.N] = __dadd_rn(sc[(size_t)(3 + j) * a.N], __dsub_rn(gg, T[j].int_i));
+    ups_int = __dadd_rn(ups_int, __dmul_rn(p.ups[j], T[j].int_s));
+  }
+  double ninf = 0.0;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) ninf = __dadd_rn(ninf, T[j].n_inf);
+  double cd = __dsub_rn(pos(phi) ? __ddiv_rn(ninf, phi) : 0.0, ups_int);
+  const double* tb = a.tang + ((size_t)r * 2 + 0) * a.N + v;
+  const double* ta = a.tang + ((size_t)r * 2 + 1) * a.N + v;
+  sc[(size_t)6 * a.N] = __dadd_rn(sc[(size_t)6 * a.N], __dmul_rn(cd, *tb));
+  sc[(size_t)7 * a.N] = __dadd_rn(sc[(size_t)7 * a.N], __dmul_rn(cd, *ta));
+}
+
+// MODE 0: day a.day (prologue for a.day - 1 when a.prologue); MODE 1: finalize
+// after the last day a.day (statistics of a.day; phi update in post-event mode).
+template <int NA, bool SCORE, int MODE>
+__global__ void __launch_bounds__(256) k_node_day(SsaArgs a) {
+  const int r = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long sI = 0, sN = 0, fired = 0;
+  const bool do_prologue = (MODE == 1) || a.prologue;
+  const int dprev = (MODE == 1) ? a.day : a.day - 1;
+  if (v < a.N) {
+    const DevParams& p = a.params[r];
+    NodeState<NA> s;
+    load_counts<NA>(a, r, v, s);
+    double* phip = a.phi + (size_t)r * a.N + v;
+    double phi = *phip;
+    if (do_prologue) {
+#pragma unroll
+      for (int j = 0; j < NA; ++j) { sI += (unsigned)s.x[2 * j + 1]; sN += (unsigned)(s.x[2 * j] + s.x[2 * j + 1]); }
+      if (!a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, dprev, s, phi);
+    }
+    if (MODE == 0) {
+      DayTerms T[NA];
+      fired = ssa_node_day<NA, SCORE>(p, a.seed, r, v, a.day, phi, s, T);
+      if (SCORE) accumulate_score<NA>(a, p, r, v, phi, T);
+      if (a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, a.day, s, phi);
+      store_counts<NA>(a, r, v, s);
+    }
+    *phip = phi;
+  }
+  fired = warp_sum(fired);
+  sI = warp_sum(sI);
+  sN = warp_sum(sN);
+  if ((threadIdx.x & 31) == 0) {
+    if (MODE == 0 && fired) atomicAdd(a.ctr + (size_t)r * 4 + 0, fired);
+    if (do_prologue) {
+      atomicAdd(a.prev_i + (size_t)r * a.max_days + dprev, sI);
+      atomicAdd(a.prev_n + (size_t)r * a.max_days + dprev, sN);
+    }
+  }
+}
+
+template <int MODE>
+static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
+  dim3 block(256), grid((a.N + 255) / 256, a.R);
+  if (n_age == 1) {
+    if (score) k_node_day<1, true, MODE><<<grid, block, 0, st>>>(a);
+    else k_node_day<1, false, MODE><<<grid, block, 0, st>>>(a);
+  } else {
+    if (score) k_node_day<3, true, MODE><<<grid, block, 0, st>>>(a);
+    else k_node_day<3, false, MODE><<<grid, block, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ssa_day(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
+  return launch_impl<0>(a, n_age, score, st);
+}
+
+cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
+  return launch_impl<1>(a, n_age, score, st);
+}
+
+__global__ void k_debug_neglog(const uint64_t* j, double* out, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = neglog_u(j[i]);
+}
+
+cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_debug_neglog<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(j, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace episim
+
+namespace episim {
+
+__global__ void k_broadcast_bytes(unsigned char* dst, const unsigned char* src, size_t bytes, int copies) {
+  // dst[c * bytes + i] = src[i] for c in [0, copies); 16-byte granules when aligned
+  size_t total = bytes * (size_t)copies;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i % bytes];
+}
+
+cudaError_t launch_broadcast(void* dst, const void* src, size_t bytes, int copies, cudaStream_t st) {
+  if (bytes == 0 || copies <= 0) return cudaSuccess;
+  k_broadcast_bytes<<<152 * 8, 256, 0, st>>>((unsigned char*)dst, (const unsigned char*)src, bytes, copies);
+  return cudaGetLastError();
+}
+
+}  // namespace episim

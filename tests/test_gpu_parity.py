@@ -1,0 +1,165 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same
+seeded inputs.  Counts, statistics and counters must be bit-identical; phi must
+agree to 1e-12 relative (the kernels follow the oracle's IEEE operation order, so
+it is expected to be identical too); per-node score terms to 1e-12 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02908_gb300 import binding as B
+from paper_1502_02908_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PHI_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load_library()
+
+
+def _assert_phi(got, ref):
+    np.testing.assert_allclose(got, ref, rtol=PHI_RTOL, atol=0)
+
+
+def _run_gpu(w, ndays=None, **kw):
+    s = B.Sim.from_workload(w, **kw)
+    s.run(w.T if ndays is None else ndays)
+    counts, phi, day = s.state()
+    pi, pn, ctr = s.stats()
+    sc = s.score() if kw.get("score") else None
+    s.close()
+    return counts, phi, pi, pn, ctr, sc
+
+
+def _compare(w, ndays=None, replicates=None, **kw):
+    nd = w.T if ndays is None else ndays
+    counts, phi, pi, pn, ctr, sc = _run_gpu(w, ndays=nd, **kw)
+    reps = list(range(w.R)) if replicates is None else replicates
+    ref = oracle.run(w, ndays=nd, replicates=reps, **kw)
+    assert np.array_equal(counts[reps], ref.counts)
+    _assert_phi(phi[reps], ref.phi)
+    assert np.array_equal(pi[reps][:, :nd], ref.prev_i)
+    assert np.array_equal(pn[reps][:, :nd], ref.prev_n)
+    assert np.array_equal(ctr[reps], ref.counters)
+    if kw.get("score"):
+        np.testing.assert_allclose(sc[reps], ref.score, rtol=PHI_RTOL, atol=1e-300)
+    return ref
+
+
+def test_neglog_kernel_bitexact():
+    import torch
+    rng = np.random.default_rng(11)
+    js = rng.integers(0, 1 << 52, size=1 << 20, dtype=np.uint64)
+    js[:6] = [0, 1, (1 << 52) - 1, (1 << 51), (1 << 51) - 1, 12345]
+    jd = torch.from_numpy(js.view(np.int64)).cuda()
+    out = torch.empty(js.size, dtype=torch.float64, device="cuda")
+    B.debug_neglog(jd.data_ptr(), out.data_ptr(), js.size)
+    got = out.cpu().numpy()
+    L = oracle.lib()
+    ref = np.array([L.orc_neglog(int(j)) for j in js[:20000]])
+    assert np.array_equal(got[:20000], ref)
+    # the rest against the float64 library log within the oracle's bound
+    u = (2 * js.astype(np.float64) + 1) / 2.0 ** 53
+    assert np.all(np.abs(got - (-np.log(u))) <= np.spacing(got) + 2.0 ** -55 + 4e-16 * np.abs(got))
+
+
+def test_sise_plain_full_horizon_bitexact():
+    _compare(W.sise_plain())
+
+
+def test_sise_plain_phi_pre_event_bitexact():
+    _compare(W.sise_plain(T=120), phi_pre_event=True)
+
+
+def test_sise3_national_bitexact_120_days():
+    w = W.sise3_national()
+    w.T = 120
+    _compare(w)
+
+
+@pytest.mark.slow
+def test_sise3_national_full_horizon_bitexact():
+    _compare(W.sise3_national())
+
+
+def test_replicates_with_own_parameters_bitexact():
+    base = W.sise3_national(N=3000, T=60, n_events=150_000)
+    w = W.sise3_batched(R=6, T=60, base=base)
+    _compare(w)
+
+
+def test_resume_equals_uninterrupted():
+    w = W.sise_plain()
+    full = B.Sim.from_workload(w)
+    full.run(w.T)
+    c_full, p_full, _ = full.state()
+    a = B.Sim.from_workload(w)
+    a.run(100)
+    c, p, day = a.state()
+    assert day == 100
+    b = B.Sim.from_workload(w)
+    b.set_state(c, p, day)
+    b.run(w.T - 100)
+    c2, p2, day2 = b.state()
+    assert day2 == w.T
+    assert np.array_equal(c2, c_full) and np.array_equal(p2, p_full)
+    # and splitting one handle's run into several calls changes nothing
+    a.run(50); a.run(w.T - 150)
+    c3, p3, _ = a.state()
+    assert np.array_equal(c3, c_full) and np.array_equal(p3, p_full)
+    for s in (full, a, b):
+        s.close()
+
+
+def test_score_terms_match_oracle():
+    w = W.sise_plain(N=300, T=60, n_events=3000, R=3)
+    w.params.upsilon[:, 0] = [0.02, 0.03, 0.04]
+    _compare(w, score=True)
+
+
+def test_score_terms_sise3_match_oracle():
+    base = W.sise3_national(N=500, T=40, n_events=20_000)
+    _compare(base, score=True)
+
+
+def test_underflow_error_policy_latches_and_skips():
+    w = W.sise_plain(N=50, T=30, n_events=3000)
+    ref = oracle.run(w, underflow_error=True)
+    assert ref.counters[0, 3] > 0
+    s = B.Sim.from_workload(w, underflow_error=True)
+    s.run(w.T)
+    with pytest.raises(B.SimError) as ei:
+        s.sync()
+    assert ei.value.status == B.SIM_E_UNDERFLOW
+    counts, phi, _ = s.state()                      # latch was cleared by sync
+    assert np.array_equal(counts, ref.counts)
+    _, _, ctr = s.stats()
+    assert np.array_equal(ctr, ref.counters)
+    s.close()
+
+
+def test_edge_cases_single_node_no_events_zero_days():
+    w = W.tiny_node(model=W.SISE, herd=40, infected=3, T=20,
+                    params=dict(upsilon=0.05, gamma=0.1, alpha=1.0, beta=0.1, epsilon=1e-3))
+    _compare(w)
+    s = B.Sim.from_workload(w)
+    s.run(0)
+    c, p, day = s.state()
+    assert day == 0 and np.array_equal(c[0], w.u0)
+    with pytest.raises(B.SimError) as ei:
+        s.run(w.T + 1)
+    assert ei.value.status == B.SIM_E_INVALID_ARG
+    s.close()
+
+
+def test_empty_herds_and_zero_rates():
+    u0 = np.array([[0, 5, 0], [0, 0, 4]], np.int32)       # empty node, all-S node, all-I node
+    w = W.tiny_node(model=W.SISE, herd=1, infected=0, copies=3, T=10,
+                    params=dict(upsilon=0.2, gamma=0.3, alpha=0.5, beta=0.2, epsilon=0.0))
+    w.u0 = u0
+    _compare(w)

@@ -1,0 +1,117 @@
+"""CPU tests of the C-ABI library (no GPU): it loads, exports every function
+include/episim.h declares, validates events, and its host-side event schedule
+(per-day dependency levels) reproduces sequential input order."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02908_gb300 import binding as B
+from paper_1502_02908_gb300 import workloads as W
+
+
+def test_library_exports_every_header_symbol():
+    L = B.load_library()
+    names = B.header_symbols()
+    assert "sim_create" in names and "sim_run_days" in names and "sim_schedule_events" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def _random_events(rng, N, T, n, model, hub=True):
+    na = 3 if model == W.SISE3 else 1
+    kinds = [W.EXIT, W.ENTER, W.EXTERNAL] + ([W.INTERNAL] if na > 1 else [])
+    kind = rng.choice(kinds, size=n)
+    # a few hub nodes make deep dependency chains
+    node = np.where(rng.random(n) < (0.3 if hub else 0.0), rng.integers(0, 3, size=n), rng.integers(0, N, size=n))
+    dest = (node + rng.integers(1, N, size=n)) % N
+    cls = np.where(kind == W.INTERNAL, rng.integers(0, max(na - 1, 1), size=n),
+                   np.where(kind == W.ENTER, rng.integers(-1, na, size=n), rng.integers(-1, na, size=n)))
+    return W.Events(rng.integers(0, T, size=n).astype(np.int32), kind.astype(np.int32), node.astype(np.int32),
+                    np.where(kind == W.EXTERNAL, dest, -1).astype(np.int32),
+                    rng.integers(0, 7, size=n).astype(np.int32), cls.astype(np.int32))
+
+
+@pytest.mark.parametrize("model", [W.SISE, W.SISE3])
+def test_schedule_levels_reproduce_input_order(model):
+    rng = np.random.default_rng(3)
+    N, T = 40, 12
+    ev = _random_events(rng, N, T, 4000, model)
+    order, level = B.schedule_events(ev, N, model, T)
+    assert order.size == len(ev)
+    stable = np.argsort(ev.day, kind="stable")              # input index of each position
+    day_of = ev.day[stable]
+    # execution order is by (day, level, position)
+    key = np.stack([day_of[order], level, order])
+    assert (np.diff(day_of[order]) >= 0).all()
+    same_day = np.diff(day_of[order]) == 0
+    assert ((np.diff(level)[same_day] > 0) | ((np.diff(level)[same_day] == 0) & (np.diff(order)[same_day] > 0))).all()
+    # the dependency rules hold within every level
+    for d in range(T):
+        sel = day_of[order] == d
+        for L in np.unique(level[sel]):
+            idx = stable[order[sel][level[sel] == L]]
+            sampled = ev.node[idx][ev.kind[idx] != W.ENTER]
+            added = np.concatenate([ev.node[idx][ev.kind[idx] == W.ENTER], ev.dest[idx][ev.kind[idx] == W.EXTERNAL]])
+            assert len(np.unique(sampled)) == len(sampled)
+            assert not set(sampled.tolist()) & set(added.tolist())
+    # applying the schedule equals applying the input order (oracle event processor)
+    nc = 6 if model == W.SISE3 else 2
+    u0 = rng.integers(0, 30, size=(nc, N)).astype(np.int32)
+    w = W.tiny_node(model=model, herd=1, infected=0, copies=N, T=T,
+                    params=dict(upsilon=0.0, gamma=0.0, alpha=0.0, beta=0.0, epsilon=0.0), seed=9)
+    w.u0 = u0
+    seq = oracle.run(w, events=ev)
+    c = u0.copy()
+    ctr = oracle.apply_events(w, c, order, ev.select(stable[order]))
+    assert np.array_equal(c, seq.counts[0])
+    assert ctr[1] == seq.counters[0, 1] and ctr[2] == seq.counters[0, 2]
+    # a shuffled order inside each level gives the same result too
+    perm = np.arange(order.size)
+    for d in range(T):
+        for L in np.unique(level):
+            m = np.nonzero((day_of[order] == d) & (level == L))[0]
+            perm[m] = rng.permutation(m)
+    c2 = u0.copy()
+    oracle.apply_events(w, c2, order[perm], ev.select(stable[order[perm]]))
+    assert np.array_equal(c2, seq.counts[0])
+
+
+def test_schedule_level_depth_of_a_hub_chain():
+    # five exits on one node in one day form a chain of five levels; enters on
+    # another node share one level
+    z = np.zeros(10, np.int32)
+    kind = np.array([W.EXIT] * 5 + [W.ENTER] * 5, np.int32)
+    node = np.array([0] * 5 + [1] * 5, np.int32)
+    ev = W.Events(z, kind, node, z - 1, z + 1, z - 1)
+    order, level = B.schedule_events(ev, 4, W.SISE, 1)
+    assert sorted(level.tolist()) == [1, 1, 1, 1, 1, 1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("bad,field,msg", [
+    (-1, "day", "day < 0"), (7, "kind", "unknown kind"), (99, "node", "out of range"),
+    (-2, "count", "out of range"), (5, "cls", "out of range"),
+])
+def test_schedule_rejects_bad_events(bad, field, msg):
+    one = dict(day=0, kind=W.EXIT, node=0, dest=-1, count=1, cls=-1)
+    one[field] = bad
+    ev = W.Events(*(np.array([one[k]], np.int32) for k in ("day", "kind", "node", "dest", "count", "cls")))
+    with pytest.raises(B.SimError) as ei:
+        B.schedule_events(ev, 4, W.SISE, 5)
+    assert ei.value.status == B.SIM_E_INVALID_ARG and msg in str(ei.value)
+
+
+def test_schedule_rejects_self_transfer_and_bad_aging():
+    ev = W.Events(*(np.array([x], np.int32) for x in (0, W.EXTERNAL, 1, 1, 1, -1)))
+    with pytest.raises(B.SimError):
+        B.schedule_events(ev, 4, W.SISE, 5)
+    ev = W.Events(*(np.array([x], np.int32) for x in (0, W.INTERNAL, 1, -1, 1, 2)))
+    with pytest.raises(B.SimError):
+        B.schedule_events(ev, 4, W.SISE3, 5)       # class 3 has no next class
+
+
+def test_schedule_drops_days_past_horizon():
+    ev = W.Events(*(np.array(x, np.int32) for x in ([0, 5, 9], [W.ENTER] * 3, [0, 0, 0], [-1] * 3, [1] * 3, [0] * 3)))
+    order, level = B.schedule_events(ev, 2, W.SISE, 6)
+    assert order.tolist() == [0, 1]
