@@ -1,0 +1,284 @@
+#!/usr/bin/env python3
+"""Benchmark of the event-based SISe3 simulation on one GB300 (or N, as replicas).
+
+Workload (one "step"): the national-scale SISe3 instance, 37,000 herds x 1,460 days,
+3,000,000 scheduled events (exit / enter / aging / external transfer), one replicate
+per GPU; the whole horizon is the step (stochastic step, events and phi update of
+every day).  Inputs are resident in HBM when the timed region starts; the L2 cache
+(129 MB; the state and event schedule fit in it) is flushed between timed steps by
+writing a 512 MB buffer.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+specification the CUDA path matches bit for bit) on a bounded sample instead.
+Multi-GPU (torchrun): replicas only; rank k runs replicate k (its own Philox
+stream), no collective on the data path; value = all ranks' node-days / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "node-days/sec and SSA events/sec (batched vs plain, bit-exact to oracle)"
+# FP64 pipe peak for the roofline: the nominal 1.25 TFLOP/s FP64 of GB300 counts an FMA
+# as two flops, so the pipe retires 6.25e11 FP64 instruction-lanes per second.
+FP64_PEAK_LANE_OPS = 6.25e11
+# FP64 instruction-lanes the specification costs on the FP64 pipe (IEEE add / mul = 1,
+# IEEE divide = 7: its measured throughput is 1/7 of DFMA's on GB300), SISe3:
+#   per fired transition: 2 (P sums) + 7 (tau) + 1 (t + tau) + 1 (r) + 1 (threshold)
+#                         + 2 (two rates) + 1 (A_j) = 15
+#   per node-day: closing draw 2 + 7 + 1 = 10; rates 3 x 4 = 12; phi update 12  = 34
+FP64_PER_TRANSITION = {3: 15, 1: 12}
+FP64_PER_NODE_DAY = {3: 34, 1: 24}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--days", type=int, default=1460)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(w, days, note):
+    """Times the CPU oracle (single thread) on the first `days` days of `w`."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.run(w, ndays=days, replicates=[0])
+    dt = time.perf_counter() - t0
+    nd = w.N * days
+    ev = int(r.counters[0, 0] + r.counters[0, 1])
+    return {"value": nd / dt, "unit": "node-days/s", "cores": 1, "kind": "oracle",
+            "sample": f"{note}: first {days} of {w.T} days, 1 replicate, single thread",
+            "seconds": dt, "events_per_s": ev / dt}, r
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def run_reference(args, dist, rank, ws):
+    from paper_1502_02908_gb300 import workloads as W
+    if rank != 0:
+        return
+    w = W.sise3_national()
+    days = 73                                   # bounded sample per step
+    times = []
+    for i in range(args.warmup + args.steps):
+        base, _ = oracle_baseline(w, days, "national SISe3")
+        if i >= args.warmup:
+            times.append(base["seconds"])
+    total = sum(times)
+    value = w.N * days * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-days/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
+            "config": {"workload": "SISe3 national, 37,000 herds, 3M events; each step the first 73 of 1,460 days",
+                       "replicates": 1},
+            "cpu_baseline": {"value": value, "unit": "node-days/s", "cores": 1, "kind": "oracle",
+                             "sample": "first 73 of 1,460 days of the national SISe3 workload per step"},
+            "e2e": {"value": value, "unit": "node-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist, rank, ws = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, dist, rank, ws)
+        if dist:
+            dist.destroy_process_group()
+        return
+    import torch
+    from paper_1502_02908_gb300 import binding as B
+    from paper_1502_02908_gb300 import workloads as W
+    from paper_1502_02908_gb300.build import build
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build()
+    w = W.sise3_national()
+    w.T = min(args.days, w.T)        # a shorter horizon of the same instance
+    sim = B.Sim(w.model, w.u0, w.phi0, w.params, w.T, seed=w.seed, replicate_base=rank)
+    t0 = time.perf_counter()
+    sim.load_events(w.events)
+    preprocess_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    R, N, T = 1, w.N, w.T
+    u0_all = np.repeat(w.u0[None], R, 0)
+    phi0_all = np.repeat(w.phi0[None], R, 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def reset():
+        sim.set_state(u0_all, phi0_all, 0)
+
+    def step():
+        sim.run(T)
+
+    for _ in range(args.warmup):
+        reset(); step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    _, _, ctr0 = sim.stats()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            reset()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream); step(); e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
+    total_ms = sum(times)
+    pi, pn, ctr1 = sim.stats()
+    # counters accumulate over every run of the handle: the timed steps' share
+    transitions = int(ctr1[0, 0] - ctr0[0, 0]) // args.steps
+    events = int(ctr1[0, 1] - ctr0[0, 1]) // args.steps
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    node_days = N * T * R * ws
+    value = node_days * args.steps / (total_ms / 1000)
+    ev_rate = (transitions + events) * ws * args.steps / (total_ms / 1000)
+
+    # end to end through the C ABI with host buffers: set state from host, run, read
+    # the final state and the daily statistics back to host
+    e2e_times = []
+    for _ in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_state(u0_all, phi0_all, 0)
+        sim.run(T)
+        c, p, _ = sim.state()
+        pi, pn, ctr2 = sim.stats()
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = u0_all.nbytes + phi0_all.nbytes
+    d2h = c.nbytes + p.nbytes + pi.nbytes + pn.nbytes + ctr2.nbytes
+    e2e = {"value": node_days / statistics.median(e2e_times), "unit": "node-days/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # per-kernel device time over one traced (untimed) step
+    reset()
+    sim.profile(True)
+    step()
+    prof = sim.profile_read()
+    sim.profile(False)
+    ssa_ms, ssa_n = prof["ssa"]
+    ev_ms, ev_n = prof["events"]
+    fin_ms, fin_n = prof["finalize"]
+    tot_k = ssa_ms + ev_ms + fin_ms
+    fp64_ops = FP64_PER_TRANSITION[w.model] * transitions + FP64_PER_NODE_DAY[w.model] * N * T
+    ssa_avg_s = ssa_ms / 1000 / max(ssa_n, 1)
+    achieved = fp64_ops / ssa_n / ssa_avg_s if ssa_n else 0.0
+    roofline = {"kernel": "k_node_day (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
+                "peak": FP64_PEAK_LANE_OPS / 1e9, "unit": "G FP64 lane-ops/s",
+                "frac": achieved / FP64_PEAK_LANE_OPS, "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (derived; see DESIGN.md)",
+                "kernel_share": {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k},
+                "avg_launch_us": {"ssa": 1000 * ssa_ms / max(ssa_n, 1), "events": 1000 * ev_ms / max(ev_n, 1)}}
+
+    line = {"metric": METRIC, "value": value, "unit": "node-days/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
+            "config": {"workload": f"SISe3 national: {N} herds x {T} days, {len(w.events)} events, "
+                                   "1 replicate per GPU (plain)",
+                       "replicates_per_gpu": R, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "events_per_s": ev_rate, "ssa_transitions_per_step": transitions, "events_per_step": events,
+            "preprocess_s": preprocess_s, "e2e": e2e, "roofline": roofline,
+            "gpu_launches": (ssa_n + ev_n + fin_n) * args.steps, "clocks": clk.summary()}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        days = min(365, T)
+        base, ref = oracle_baseline(w, days, "national SISe3")
+        line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # bit-exactness of this configuration at the sampled horizon
+        chk = B.Sim(w.model, w.u0, w.phi0, w.params, w.T, seed=w.seed)
+        chk.load_events(w.events)
+        chk.run(days)
+        c, p, _ = chk.state()
+        chk.close()
+        line["bitexact_vs_oracle"] = {"days": days, "counts_equal": bool(np.array_equal(c[0], ref.counts[0])),
+                                      "phi_max_rel": float(np.max(np.abs(p[0] - ref.phi[0]) /
+                                                                  np.maximum(np.abs(ref.phi[0]), 1e-300)))}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -66,6 +66,10 @@ typedef struct sim_config {
     int32_t underflow_policy; /* SIM_UNDERFLOW_CLAMP (default) or SIM_UNDERFLOW_ERROR */
     int32_t flags;            /* SIM_FLAG_* */
     uint64_t seed;            /* Philox key */
+    int32_t replicate_base;   /* replicate r of this handle draws as replicate
+                                 replicate_base + r (disjoint streams when
+                                 replicates are split across handles or GPUs) */
+    int32_t reserved;         /* must be 0 */
 } sim_config;
 
 /* Per-replicate model constants, host arrays with a leading replicate axis:
@@ -165,16 +169,48 @@ sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days,
                                const int32_t* dest, const int32_t* count, const int32_t* cls,
                                int64_t* order, int32_t* level, int64_t* n_scheduled);
 
+/* Launch shape of the stochastic step.  Nodes whose initial herd has at least
+ * warp_herd_threshold animals are simulated one per warp (the 32 lanes draw
+ * and time 32 steps at once; suited to herds with many transitions per day);
+ * the others one per thread.  -1 = automatic (warps for herds of >= 400 animals
+ * while node-replicates number fewer than 152 x 1024, else none); a very large
+ * value disables the warp path.  Results do not depend on this setting.  Score
+ * mode always uses one thread per node.  Synchronises the device. */
+sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold);
+/* Number of nodes currently simulated one per warp (-1 for a NULL handle). */
+int32_t sim_warp_nodes(const sim_handle* h);
+
+/* Kernel timing (tracing).  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events on its stream.  sim_profile_read synchronises and
+ * returns, per kernel kind (0 = stochastic step, 1 = events, 2 = phi/statistics
+ * finalisation), the summed device time in ms and the number of launches since
+ * the last enable; host arrays of 3 entries. */
+sim_status sim_profile(sim_handle* h, int32_t enable);
+sim_status sim_profile_read(sim_handle* h, double* ms, int64_t* launches);
+
 /* Test hook (not part of the simulation path): evaluates the library's
  * -log(u) for u = (2 j + 1) 2^-53 on the GPU, for n device inputs j (uint64)
  * into n device doubles.  Synchronous. */
 sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n);
+
+/* Test hook: the library's integer-pipe IEEE division x / y for positive
+ * operands, and the reference IEEE division, on n inputs: where = SIM_HOST runs
+ * the same routine on the CPU (host pointers), SIM_DEVICE on the GPU (device
+ * pointers; ref then comes from the hardware divide).  Synchronous. */
+sim_status sim_debug_div(const double* x, const double* y, double* out, double* ref, int64_t n,
+                         int32_t where);
 
 /* Test hook: the event schedule built by sim_load_events, host int64 [n]:
  * the event's position in the day-stable order, listed in execution order
  * (day, then dependency level, then position), and the level of each listed
  * event (int32 [n]).  Either output may be NULL. */
 sim_status sim_debug_schedule(const sim_handle* h, int64_t* order, int32_t* level);
+/* Test hook: global_only = 1 makes the handle apply events with the
+ * global-memory event kernel on every day (call before sim_load_events);
+ * 0 (default) uses the shared-memory staged kernel on days whose working set
+ * fits in shared memory.  Both give identical results. */
+sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only);
+
 /* Number of entries sim_debug_schedule writes (-1 for a NULL handle). */
 int64_t sim_debug_schedule_size(const sim_handle* h);
 

@@ -35,7 +35,8 @@ class SimConfig(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
                 ("n_replicates", ctypes.c_int32), ("max_days", ctypes.c_int32),
                 ("underflow_policy", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("replicate_base", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SimParams(ctypes.Structure):
@@ -76,7 +77,12 @@ def load_library(build_if_missing: bool = True):
             "sim_reset": [vp, i32],
             "sim_schedule_events": [i32, i32, i32, i64, pi32, pi32, pi32, pi32, pi32, pi32, pi64, pi32, pi64],
             "sim_debug_neglog": [vp, vp, i64],
+            "sim_debug_div": [vp, vp, vp, vp, i64, i32],
             "sim_debug_schedule": [vp, pi64, pi32],
+            "sim_profile": [vp, i32],
+            "sim_debug_event_variant": [vp, i32],
+            "sim_tune": [vp, i32],
+            "sim_profile_read": [vp, pd, pi64],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -86,6 +92,8 @@ def load_library(build_if_missing: bool = True):
         L.sim_destroy.restype = None
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = ctypes.c_char_p
+        L.sim_warp_nodes.argtypes = [vp]
+        L.sim_warp_nodes.restype = ctypes.c_int32
         L.sim_debug_schedule_size.argtypes = [vp]
         L.sim_debug_schedule_size.restype = ctypes.c_int64
         _LIB = L
@@ -133,7 +141,7 @@ class Sim:
     """One simulation handle: R replicates of one model on N nodes."""
 
     def __init__(self, model, u0, phi0, params: W.Params, max_days, seed=1,
-                 underflow_error=False, phi_pre_event=False, score=False):
+                 underflow_error=False, phi_pre_event=False, score=False, replicate_base=0):
         self.L = load_library()
         u0 = np.ascontiguousarray(u0, np.int32)
         self.nc, self.N = u0.shape
@@ -141,7 +149,8 @@ class Sim:
         self.R = params.upsilon.shape[0]
         self.max_days = max_days
         cfg = SimConfig(model, self.N, self.R, max_days, 1 if underflow_error else 0,
-                        (FLAG_PHI_PRE_EVENT if phi_pre_event else 0) | (FLAG_SCORE if score else 0), seed)
+                        (FLAG_PHI_PRE_EVENT if phi_pre_event else 0) | (FLAG_SCORE if score else 0), seed,
+                        int(replicate_base), 0)
         self._keep = [np.ascontiguousarray(x, np.float64) for x in
                       (params.upsilon, params.gamma, params.alpha, params.beta, params.epsilon)]
         sp = SimParams(*[_p(a, ctypes.c_double) for a in self._keep])
@@ -152,8 +161,10 @@ class Sim:
         self.h = h
 
     @classmethod
-    def from_workload(cls, w: W.Workload, events=True, max_days=None, **kw):
+    def from_workload(cls, w: W.Workload, events=True, max_days=None, global_events=False, **kw):
         s = cls(w.model, w.u0, w.phi0, w.params, w.T if max_days is None else max_days, seed=w.seed, **kw)
+        if global_events:
+            _check(s.L, s.h, s.L.sim_debug_event_variant(s.h, 1))
         if events and len(w.events):
             s.load_events(w.events)
         return s
@@ -219,6 +230,20 @@ class Sim:
         _check(self.L, self.h, self.L.sim_debug_schedule(self.h, _p(order, ctypes.c_int64), _p(level, ctypes.c_int32)))
         return order[:n], level[:n]
 
+    def tune(self, warp_herd_threshold=-1):
+        _check(self.L, self.h, self.L.sim_tune(self.h, int(warp_herd_threshold)))
+        return self.L.sim_warp_nodes(self.h)
+
+    def profile(self, enable=True):
+        _check(self.L, self.h, self.L.sim_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms = np.zeros(3, np.float64)
+        n = np.zeros(3, np.int64)
+        _check(self.L, self.h, self.L.sim_profile_read(self.h, _p(ms, ctypes.c_double), _p(n, ctypes.c_int64)))
+        return {"ssa": (float(ms[0]), int(n[0])), "events": (float(ms[1]), int(n[1])),
+                "finalize": (float(ms[2]), int(n[2]))}
+
     def close(self):
         if getattr(self, "h", None):
             self.L.sim_destroy(self.h)
@@ -229,6 +254,14 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def debug_div(x, y, out, ref, n, device):
+    """x, y, out, ref: pointers (ints) to n doubles, host or device."""
+    L = load_library()
+    st = L.sim_debug_div(ctypes.c_void_p(x), ctypes.c_void_p(y), ctypes.c_void_p(out), ctypes.c_void_p(ref),
+                         int(n), SIM_DEVICE if device else SIM_HOST)
+    _check(L, None, st)
 
 
 def debug_neglog(j_dev_ptr, out_dev_ptr, n):

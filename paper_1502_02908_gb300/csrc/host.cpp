@@ -4,7 +4,9 @@
 // per-day launch sequence (Alg. 1: stochastic step, events, phi update).
 #include "../../include/episim.h"
 #include "internal.h"
+#include "softdiv.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,17 +34,30 @@ struct sim_handle {
   double* d_score = nullptr;
   double* d_tang = nullptr;
   int32_t* d_u0 = nullptr;          // [Nc][N] master copy for resets
+  int32_t* d_order = nullptr;       // node order of the stochastic step
+  int32_t n_big = 0;                // leading nodes of the order simulated one per warp
+  int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
   double* d_phi0 = nullptr;
   // event schedule
   bool events_loaded = false;
   int4* d_rec = nullptr;
+  int4* d_rec_slot = nullptr;
   int32_t* d_lvl_start = nullptr;
   int32_t* d_day_lvl = nullptr;
+  int32_t* d_touched = nullptr;
+  int32_t* d_day_touch = nullptr;
+  std::vector<int32_t> day_smem;     // shared-memory bytes of the staged event step per day (0: global variant)
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
   std::vector<int32_t> sched_level;
   std::vector<int32_t> day_lvl;      // [max_days + 1]
   int32_t day = 0;
   std::string err;
+  // tracing
+  bool profiling = false;
+  bool force_global_events = false;  // test switch: always use the global-memory event step
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;        // kind of each recorded pair
+  size_t ev_used = 0;
 };
 
 namespace {
@@ -79,16 +94,24 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
+  cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch);
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
-  h->sched_order.clear(); h->sched_level.clear(); h->day_lvl.clear();
+  h->d_rec_slot = nullptr; h->d_touched = nullptr; h->d_day_touch = nullptr;
+  h->sched_order.clear(); h->sched_level.clear(); h->day_lvl.clear(); h->day_smem.clear();
   h->events_loaded = false;
 }
 
+void free_profile(sim_handle* h) {
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear(); h->ev_kind.clear(); h->ev_used = 0;
+}
+
 void free_all(sim_handle* h) {
+  free_profile(h);
   free_events(h);
   cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
   cudaFree(h->d_prev_n); cudaFree(h->d_ctr); cudaFree(h->d_err); cudaFree(h->d_score);
-  cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0);
+  cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0); cudaFree(h->d_order);
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -130,15 +153,49 @@ SsaArgs ssa_args(sim_handle* h) {
   SsaArgs a{};
   a.counts = h->d_counts; a.phi = h->d_phi; a.params = h->d_params;
   a.prev_i = h->d_prev_i; a.prev_n = h->d_prev_n; a.ctr = h->d_ctr;
-  a.score = h->d_score; a.tang = h->d_tang; a.seed = h->cfg.seed;
+  a.score = h->d_score; a.tang = h->d_tang; a.seed = h->cfg.seed; a.rep_base = h->cfg.replicate_base;
   a.N = h->cfg.n_nodes; a.R = h->cfg.n_replicates; a.Nc = h->nc; a.max_days = h->cfg.max_days;
   a.pre_event = (h->cfg.flags & SIM_FLAG_PHI_PRE_EVENT) ? 1 : 0;
+  a.order = h->d_order;
+  a.n_big = h->n_big;
+  a.warp_blocks = (h->n_big + 7) / 8;
   return a;
+}
+
+// Node order of the stochastic step: nodes with at least `threshold` animals
+// (initial herd) first, one warp each, largest first; then the others, largest
+// first, one thread each (similar work per warp).  threshold < 0: automatic --
+// warps only while the per-thread work leaves the GPU under-occupied (fewer than
+// 152 x 1024 node-replicates), for herds of 400 animals or more.
+sim_status set_order(sim_handle* h, int32_t threshold) {
+  const int N = h->cfg.n_nodes;
+  std::vector<int64_t> herd(N, 0);
+  for (int c = 0; c < h->nc; ++c)
+    for (int v = 0; v < N; ++v) herd[v] += h->u0[(size_t)c * N + v];
+  std::vector<int32_t> order(N);
+  for (int v = 0; v < N; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return herd[a] > herd[b]; });
+  int32_t thr = threshold;
+  if (thr < 0) {
+    const int64_t work = (int64_t)N * h->cfg.n_replicates;
+    thr = (work < 152 * 1024) ? 400 : (1 << 30);
+  }
+  int32_t nb = 0;
+  if (!(h->cfg.flags & SIM_FLAG_SCORE))
+    while (nb < N && herd[order[nb]] >= thr) ++nb;
+  if (!h->d_order) CK(h, dalloc(&h->d_order, (size_t)N), "node order allocation");
+  CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
+  h->n_big = nb;
+  h->warp_threshold = threshold;
+  return SIM_OK;
 }
 
 
 struct Schedule {
   std::vector<int4> rec;          // execution order
+  std::vector<int4> rec_slot;     // same, with node slots of the day's touched list
+  std::vector<int32_t> touched;   // node ids per day slot
+  std::vector<int32_t> day_touch; // [max_days + 1]
   std::vector<int32_t> lvl_start; // [levels + 1]
   std::vector<int32_t> day_lvl;   // [max_days + 1]
   std::vector<int64_t> order;     // day-stable position of each record
@@ -194,9 +251,18 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     S.rec.resize((size_t)n_run);
     S.order.resize((size_t)n_run);
     S.level.resize((size_t)n_run);
+    S.rec_slot.resize((size_t)n_run);
+    S.day_touch.assign((size_t)T + 1, 0);
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  std::vector<int32_t> slot_of(N, -1), slot_day(N, -1);
   for (int32_t d = 0; d < T; ++d) {
     S.day_lvl[d] = (int32_t)S.lvl_start.size();
+    S.day_touch[d] = (int32_t)S.touched.size();
+    const int32_t touch0 = S.day_touch[d];
+    auto slot = [&](int v) {
+      if (slot_day[v] != d) { slot_day[v] = d; slot_of[v] = (int32_t)S.touched.size() - touch0; S.touched.push_back(v); }
+      return slot_of[v];
+    };
     const int64_t s0 = first[(size_t)d], s1 = first[(size_t)d + 1];
     int32_t max_lvl = 0;
     auto touch = [&](int v) { if (stamp[v] != d) { stamp[v] = d; last_s[v] = 0; last_a[v] = 0; } };
@@ -233,10 +299,39 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
       S.order[slot] = s;
       S.level[slot] = lvl_of[(size_t)s];
     }
+    for (int64_t k = s0; k < s1; ++k) {          // slots in execution order
+      const int4 rc = S.rec[(size_t)k];
+      const int32_t a = slot(rc.x);
+      const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
+      S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
+    }
   }
   S.day_lvl[T] = (int32_t)S.lvl_start.size();
+  S.day_touch[T] = (int32_t)S.touched.size();
   S.lvl_start.push_back((int32_t)n_run);
   return SIM_OK;
+}
+
+// Launches `fn` on `st`, bracketed by a pair of pooled CUDA events when tracing.
+template <class F>
+cudaError_t traced(sim_handle* h, int kind, cudaStream_t st, F&& fn) {
+  if (!h->profiling) return fn();
+  if (h->ev_used + 2 > h->ev_pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      h->ev_pool.push_back(e);
+    }
+  }
+  cudaError_t err = cudaEventRecord(h->ev_pool[h->ev_used], st);
+  if (err != cudaSuccess) return err;
+  err = fn();
+  if (err != cudaSuccess) return err;
+  err = cudaEventRecord(h->ev_pool[h->ev_used + 1], st);
+  h->ev_used += 2;
+  h->ev_kind.push_back(kind);
+  return err;
 }
 
 }  // namespace
@@ -254,6 +349,9 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     return fail(nullptr, SIM_E_INVALID_ARG, "unknown underflow policy");
   if (cfg->flags & ~(SIM_FLAG_PHI_PRE_EVENT | SIM_FLAG_SCORE))
     return fail(nullptr, SIM_E_INVALID_ARG, "unknown flag bits");
+  if (cfg->replicate_base < 0 || (int64_t)cfg->replicate_base + cfg->n_replicates > ((int64_t)1 << 32) ||
+      cfg->reserved != 0)
+    return fail(nullptr, SIM_E_INVALID_ARG, "replicate_base out of range or reserved field set");
   if (!p->upsilon || !p->gamma || !p->alpha || !p->beta || !p->epsilon)
     return fail(nullptr, SIM_E_INVALID_ARG, "null parameter array");
   sim_handle* h = new (std::nothrow) sim_handle();
@@ -322,6 +420,7 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     return s;
   }
   sim_status s = reset_state(h);
+  if (s == SIM_OK) s = set_order(h, -1);
   if (s != SIM_OK) {
     g_create_error = h->err;
     free_all(h);
@@ -351,7 +450,21 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   if (err == cudaSuccess && !S.rec.empty()) err = cudaMemcpy(h->d_rec, S.rec.data(), S.rec.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(h->d_lvl_start, S.lvl_start.data(), S.lvl_start.size() * 4, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(h->d_day_lvl, S.day_lvl.data(), S.day_lvl.size() * 4, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = dalloc(&h->d_rec_slot, S.rec_slot.size());
+  if (err == cudaSuccess) err = dalloc(&h->d_touched, S.touched.size());
+  if (err == cudaSuccess) err = dalloc(&h->d_day_touch, S.day_touch.size());
+  if (err == cudaSuccess && !S.rec_slot.empty()) err = cudaMemcpy(h->d_rec_slot, S.rec_slot.data(), S.rec_slot.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && !S.touched.empty()) err = cudaMemcpy(h->d_touched, S.touched.data(), S.touched.size() * 4, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(h->d_day_touch, S.day_touch.data(), S.day_touch.size() * 4, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
+  h->day_smem.assign((size_t)T, 0);
+  for (int32_t d = 0; d < T; ++d) {
+    const int64_t nl = S.day_lvl[(size_t)d + 1] - S.day_lvl[(size_t)d];
+    const int64_t ne = S.lvl_start[(size_t)S.day_lvl[(size_t)d + 1]] - S.lvl_start[(size_t)S.day_lvl[(size_t)d]];
+    const int64_t nt = S.day_touch[(size_t)d + 1] - S.day_touch[(size_t)d];
+    const size_t b = events_smem_bytes(ne, nl, nt, h->nc);
+    h->day_smem[(size_t)d] = (b <= kEventsSmemLimit && !h->force_global_events) ? (int32_t)b : 0;
+  }
   h->sched_order.swap(S.order);
   h->sched_level.swap(S.level);
   h->day_lvl.swap(S.day_lvl);
@@ -389,21 +502,32 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   SsaArgs a = ssa_args(h);
   EvArgs ev{};
   ev.counts = h->d_counts; ev.rec = h->d_rec; ev.lvl_start = h->d_lvl_start; ev.day_lvl = h->d_day_lvl;
-  ev.ctr = h->d_ctr; ev.err = h->d_err; ev.seed = h->cfg.seed;
+  ev.ctr = h->d_ctr; ev.err = h->d_err; ev.seed = h->cfg.seed; ev.rep_base = h->cfg.replicate_base;
   ev.N = h->cfg.n_nodes; ev.R = h->cfg.n_replicates; ev.Nc = h->nc;
   ev.underflow_error = h->cfg.underflow_policy == SIM_UNDERFLOW_ERROR;
+  EvSmemArgs es{};
+  es.counts = h->d_counts; es.rec = h->d_rec_slot; es.lvl_start = h->d_lvl_start; es.day_lvl = h->d_day_lvl;
+  es.touched = h->d_touched; es.day_touch = h->d_day_touch; es.ctr = h->d_ctr; es.err = h->d_err;
+  es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
+  es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
   const int32_t d0 = h->day;
   for (int32_t d = d0; d < d0 + ndays; ++d) {
     a.day = d;
     a.prologue = d > d0;
-    CK(h, launch_ssa_day(a, h->n_age, score, st), "stochastic step launch");
+    CK(h, traced(h, 0, st, [&] { return launch_ssa_day(a, h->n_age, score, st); }), "stochastic step launch");
     if (h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]) {
-      ev.day = d;
-      CK(h, launch_events_day(ev, h->n_age, st), "event step launch");
+      if (h->day_smem[(size_t)d] > 0) {
+        es.day = d;
+        es.smem_bytes = h->day_smem[(size_t)d];
+        CK(h, traced(h, 1, st, [&] { return launch_events_day_smem(es, h->n_age, st); }), "event step launch");
+      } else {
+        ev.day = d;
+        CK(h, traced(h, 1, st, [&] { return launch_events_day(ev, h->n_age, st); }), "event step launch");
+      }
     }
   }
   a.day = d0 + ndays - 1;
-  CK(h, launch_finalize(a, h->n_age, score, st), "phi update launch");
+  CK(h, traced(h, 2, st, [&] { return launch_finalize(a, h->n_age, score, st); }), "phi update launch");
   h->day = d0 + ndays;
   return SIM_OK;
 }
@@ -491,6 +615,49 @@ void sim_destroy(sim_handle* h) {
   delete h;
 }
 
+sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only) {
+  if (!h) return SIM_E_INVALID_ARG;
+  h->force_global_events = global_only != 0;
+  for (size_t d = 0; d < h->day_smem.size(); ++d)
+    if (h->force_global_events) h->day_smem[d] = 0;
+  return SIM_OK;
+}
+
+sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold) {
+  if (!h) return SIM_E_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  return set_order(h, warp_herd_threshold);
+}
+
+int32_t sim_warp_nodes(const sim_handle* h) { return h ? h->n_big : -1; }
+
+sim_status sim_profile(sim_handle* h, int32_t enable) {
+  if (!h) return SIM_E_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  h->ev_kind.clear();
+  return SIM_OK;
+}
+
+sim_status sim_profile_read(sim_handle* h, double* ms, int64_t* launches) {
+  if (!h) return SIM_E_INVALID_ARG;
+  double acc[3] = {0, 0, 0};
+  int64_t cnt[3] = {0, 0, 0};
+  for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+    CK(h, cudaEventSynchronize(h->ev_pool[2 * i + 1]), "event synchronize");
+    float t = 0.f;
+    CK(h, cudaEventElapsedTime(&t, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]), "event elapsed time");
+    acc[h->ev_kind[i]] += t;
+    cnt[h->ev_kind[i]] += 1;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return SIM_OK;
+}
+
 const char* sim_last_error(const sim_handle* h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }
@@ -498,6 +665,17 @@ const char* sim_last_error(const sim_handle* h) {
 sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n) {
   if (n < 0 || (n > 0 && (!j_dev || !out_dev))) return SIM_E_INVALID_ARG;
   cudaError_t e = launch_debug_neglog(j_dev, out_dev, n, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+}
+
+sim_status sim_debug_div(const double* x, const double* y, double* out, double* ref, int64_t n, int32_t where) {
+  if (n < 0 || (n > 0 && (!x || !y || !out || !ref))) return SIM_E_INVALID_ARG;
+  if (where == SIM_HOST) {
+    for (int64_t i = 0; i < n; ++i) { out[i] = episim::div_pos(x[i], y[i]); ref[i] = x[i] / y[i]; }
+    return SIM_OK;
+  }
+  cudaError_t e = launch_debug_div(x, y, out, ref, n, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e == cudaSuccess ? SIM_OK : SIM_E_CUDA;
 }

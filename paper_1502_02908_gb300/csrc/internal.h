@@ -33,10 +33,14 @@ struct SsaArgs {
   double* score;              // [R][8][N] (score mode)
   double* tang;               // [R][2][N]: d phi/d beta, d phi/d alpha (score mode)
   uint64_t seed;
+  int32_t rep_base;           // Philox replicate word = rep_base + r
   int32_t N, R, Nc, max_days;
   int32_t day;                // day simulated by this launch
   int32_t prologue;           // 1: first record stats of day-1 and (post-event mode) update phi
   int32_t pre_event;          // 1: phi update from post-SSA counts in the epilogue
+  const int32_t* order;       // node order: first n_big nodes warp-cooperative, the rest per thread (NULL: identity)
+  int32_t n_big;              // nodes simulated one per warp
+  int32_t warp_blocks;        // blocks (of 8 warps) given to them
 };
 
 // One scheduled event, 16 bytes: node, dest, position in the day-stable order,
@@ -49,10 +53,36 @@ struct EvArgs {
   unsigned long long* ctr;    // [R][4]
   int32_t* err;               // bit 0: underflow under the ERROR policy
   uint64_t seed;
+  int32_t rep_base;
   int32_t N, R, Nc;
   int32_t day;
   int32_t underflow_error;
 };
+
+// Shared-memory event step: the day's records refer to node slots of the day's
+// touched-node list; counts of those nodes, the records, the first Philox block
+// of every event and the level offsets are staged in shared memory.
+struct EvSmemArgs {
+  int32_t* counts;
+  const int4* rec;            // {slot_src, slot_dst or -1, position, packed}, execution order
+  const int32_t* lvl_start;   // global level offsets (records)
+  const int32_t* day_lvl;     // [max_days + 1]
+  const int32_t* touched;     // node ids of the day's slots
+  const int32_t* day_touch;   // [max_days + 1] offsets into touched
+  unsigned long long* ctr;
+  int32_t* err;
+  uint64_t seed;
+  int32_t rep_base;
+  int32_t N, R, Nc;
+  int32_t day;
+  int32_t underflow_error;
+  int32_t smem_bytes;
+};
+
+cudaError_t launch_events_day_smem(const EvSmemArgs& a, int n_age, cudaStream_t st);
+// Shared memory the staged event step needs for a day (0 if the day has no events).
+size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc);
+constexpr size_t kEventsSmemLimit = 220 * 1024;
 
 struct FinalizeArgs {
   SsaArgs s;                  // day = last simulated day; prologue semantics for day+1
@@ -63,6 +93,7 @@ cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
 // After the last day of a call: phi update (post-event mode) and statistics of day a.day.
 cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
 cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_debug_div(const double* x, const double* y, double* out, double* ref, int64_t n, cudaStream_t st);
 
 }  // namespace episim
 

@@ -36,9 +36,9 @@ def _run_gpu(w, ndays=None, **kw):
     return counts, phi, pi, pn, ctr, sc
 
 
-def _compare(w, ndays=None, replicates=None, **kw):
+def _compare(w, ndays=None, replicates=None, global_events=False, **kw):
     nd = w.T if ndays is None else ndays
-    counts, phi, pi, pn, ctr, sc = _run_gpu(w, ndays=nd, **kw)
+    counts, phi, pi, pn, ctr, sc = _run_gpu(w, ndays=nd, global_events=global_events, **kw)
     reps = list(range(w.R)) if replicates is None else replicates
     ref = oracle.run(w, ndays=nd, replicates=reps, **kw)
     assert np.array_equal(counts[reps], ref.counts)
@@ -163,3 +163,63 @@ def test_empty_herds_and_zero_rates():
                     params=dict(upsilon=0.2, gamma=0.3, alpha=0.5, beta=0.2, epsilon=0.0))
     w.u0 = u0
     _compare(w)
+
+
+def test_global_event_variant_bitexact():
+    w = W.sise3_national()
+    w.T = 60
+    _compare(w, global_events=True)
+
+
+def test_day_too_large_for_shared_memory_falls_back():
+    # 30,000 events on three days: ~10,000 per day needs more than 220 KB staged
+    w = W.sise_plain(N=2000, T=3, n_events=30_000)
+    _compare(w)
+
+
+def test_integer_pipe_division_matches_hardware_divide():
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(3)
+    n = 1 << 22
+    ex = torch.randint(1023 - 60, 1023 + 60, (n,), generator=g, dtype=torch.int64)
+    ey = torch.randint(1023 - 60, 1023 + 60, (n,), generator=g, dtype=torch.int64)
+    mx = torch.randint(0, 1 << 52, (n,), generator=g, dtype=torch.int64)
+    my = torch.randint(0, 1 << 52, (n,), generator=g, dtype=torch.int64)
+    my[::5] &= 0xF
+    x = ((ex << 52) | mx).view(torch.float64).cuda()
+    y = ((ey << 52) | my).view(torch.float64).cuda()
+    out = torch.empty_like(x); ref = torch.empty_like(x)
+    B.debug_div(x.data_ptr(), y.data_ptr(), out.data_ptr(), ref.data_ptr(), n, device=True)
+    assert torch.equal(out.view(torch.int64), ref.view(torch.int64))
+    assert torch.equal(out.view(torch.int64), (x / y).view(torch.int64))
+
+
+@pytest.mark.parametrize("threshold", [0, 60])
+def test_warp_per_node_path_bitexact_sise3(threshold):
+    w = W.sise3_national(N=4000, T=90, n_events=80_000)
+    s = B.Sim.from_workload(w)
+    nwarp = s.tune(threshold)
+    assert nwarp == (4000 if threshold == 0 else int((w.u0.sum(0) >= threshold).sum()))
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    pi, pn, ctr = s.stats()
+    s.close()
+    ref = oracle.run(w)
+    assert np.array_equal(counts, ref.counts)
+    _assert_phi(phi, ref.phi)
+    assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
+
+
+def test_warp_per_node_path_bitexact_sise_many_transitions():
+    # prevalence near 1: ~19 transitions per node-day, long warp chains
+    w = W.sise_plain(N=600, T=200, n_events=12_000)
+    s = B.Sim.from_workload(w)
+    assert s.tune(0) == 600
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    _, _, ctr = s.stats()
+    s.close()
+    ref = oracle.run(w)
+    assert np.array_equal(counts, ref.counts)
+    _assert_phi(phi, ref.phi)
+    assert np.array_equal(ctr, ref.counters)

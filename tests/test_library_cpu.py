@@ -115,3 +115,21 @@ def test_schedule_drops_days_past_horizon():
     ev = W.Events(*(np.array(x, np.int32) for x in ([0, 5, 9], [W.ENTER] * 3, [0, 0, 0], [-1] * 3, [1] * 3, [0] * 3)))
     order, level = B.schedule_events(ev, 2, W.SISE, 6)
     assert order.tolist() == [0, 1]
+
+
+def test_integer_pipe_division_matches_ieee_on_host():
+    rng = np.random.default_rng(5)
+    n = 400_000
+    ex = rng.integers(1023 - 60, 1023 + 60, size=n, dtype=np.uint64)
+    ey = rng.integers(1023 - 60, 1023 + 60, size=n, dtype=np.uint64)
+    mx = rng.integers(0, 1 << 52, size=n, dtype=np.uint64)
+    my = rng.integers(0, 1 << 52, size=n, dtype=np.uint64)
+    my[::5] &= np.uint64(0xF)                 # divisors at and near powers of two
+    mx[::7] = np.uint64((1 << 52) - 1) - (mx[::7] & np.uint64(0xF))
+    x = ((ex << np.uint64(52)) | mx).view(np.float64).copy()
+    y = ((ey << np.uint64(52)) | my).view(np.float64).copy()
+    x[:4] = [1.0, 3.0, np.nextafter(2.0, 0), 1e-300]
+    y[:4] = [3.0, 3.0, np.nextafter(1.0, 2), 1e300]      # last: subnormal quotient path
+    out = np.empty(n); ref = np.empty(n)
+    B.debug_div(x.ctypes.data, y.ctypes.data, out.ctypes.data, ref.ctypes.data, n, device=False)
+    assert np.array_equal(out.view(np.uint64), (x / y).view(np.uint64))
