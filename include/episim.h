@@ -55,7 +55,11 @@ enum { SIM_HOST = 0, SIM_DEVICE = 1 };
 /* sim_config.flags */
 enum {
     SIM_FLAG_PHI_PRE_EVENT = 1,  /* phi from post-SSA, pre-event counts (Eq. (numstep5) as printed) */
-    SIM_FLAG_SCORE = 2           /* accumulate score-function terms (sim_score) */
+    SIM_FLAG_SCORE = 2,          /* accumulate score-function terms (sim_score); the beta and
+                                    alpha terms through forward tangents of phi */
+    SIM_FLAG_SCORE_REVERSE = 4   /* score terms with the beta and alpha terms left to a reverse
+                                    sweep (sim_score_backward) over a stored per-day trajectory
+                                    of 24 bytes per node-day-replicate; implies SIM_FLAG_SCORE */
 };
 
 typedef struct sim_config {
@@ -143,6 +147,25 @@ sim_status sim_stats(sim_handle* h, int64_t* infected, int64_t* animals, int64_t
  * sampling law; phi's dependence on beta and alpha is carried through Eq.
  * (numstep5).  Synchronises `stream`. */
 sim_status sim_score(sim_handle* h, double* score, void* stream);
+
+/* Reverse sweep of the phi recursion (needs SIM_FLAG_SCORE_REVERSE), on the
+ * device: for every node and replicate, over the days simulated since the score
+ * was last cleared, lambda_d = c_d + (1 - beta_d) lambda_{d+1} with c_d the
+ * node-day's d log p / d phi_d; adds sum_d -lambda_{d+1} phi_d to the beta term
+ * and sum_d lambda_{d+1} (I_d / N_d) to the alpha term of the node's score
+ * (Eq. (numstep5) with Eq. (siminfpressure) differentiated in reverse).  Call
+ * once per run, after the last sim_run_days.  Asynchronous on `stream`. */
+sim_status sim_score_backward(sim_handle* h, void* stream);
+
+/* Moments for the score-function gradient estimate, on the device: for each
+ * replicate, f = infected / animals after day days[i] (i < n_days) and s = its
+ * score summed over nodes; writes per_rep [R][8] (may be NULL) and out
+ * [n_days][34] = sum f, sum f^2, then for each of the 8 score terms k:
+ * sum s_k, sum s_k^2, sum f s_k, sum (f s_k)^2 (replicates added in index
+ * order).  d E[f] / d theta_k is estimated by the covariance of f and s_k.
+ * Host outputs; synchronises `stream`. */
+sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_days, double* per_rep,
+                                double* out, void* stream);
 
 /* Back to day 0 with the initial counts and phi; statistics and score cleared.
  * clear_events = 1 also drops the loaded events. */

@@ -20,7 +20,7 @@ HEADER = pathlib.Path(__file__).resolve().parent.parent / "include" / "episim.h"
 
 SIM_OK, SIM_E_INVALID_ARG, SIM_E_OOM, SIM_E_CUDA, SIM_E_UNDERFLOW, SIM_E_TIMEOUT, SIM_E_STATE = range(7)
 SIM_HOST, SIM_DEVICE = 0, 1
-FLAG_PHI_PRE_EVENT, FLAG_SCORE = 1, 2
+FLAG_PHI_PRE_EVENT, FLAG_SCORE, FLAG_SCORE_REVERSE = 1, 2, 4
 STATUS_NAMES = {0: "SIM_OK", 1: "SIM_E_INVALID_ARG", 2: "SIM_E_OOM", 3: "SIM_E_CUDA",
                 4: "SIM_E_UNDERFLOW", 5: "SIM_E_TIMEOUT", 6: "SIM_E_STATE"}
 
@@ -82,6 +82,8 @@ def load_library(build_if_missing: bool = True):
             "sim_profile": [vp, i32],
             "sim_debug_event_variant": [vp, i32],
             "sim_tune": [vp, i32],
+            "sim_score_backward": [vp, vp],
+            "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
             "sim_profile_read": [vp, pd, pi64],
         }
         for name, args in sigs.items():
@@ -141,7 +143,8 @@ class Sim:
     """One simulation handle: R replicates of one model on N nodes."""
 
     def __init__(self, model, u0, phi0, params: W.Params, max_days, seed=1,
-                 underflow_error=False, phi_pre_event=False, score=False, replicate_base=0):
+                 underflow_error=False, phi_pre_event=False, score=False, replicate_base=0,
+                 score_reverse=False):
         self.L = load_library()
         u0 = np.ascontiguousarray(u0, np.int32)
         self.nc, self.N = u0.shape
@@ -149,7 +152,8 @@ class Sim:
         self.R = params.upsilon.shape[0]
         self.max_days = max_days
         cfg = SimConfig(model, self.N, self.R, max_days, 1 if underflow_error else 0,
-                        (FLAG_PHI_PRE_EVENT if phi_pre_event else 0) | (FLAG_SCORE if score else 0), seed,
+                        (FLAG_PHI_PRE_EVENT if phi_pre_event else 0) | (FLAG_SCORE if score else 0)
+                        | (FLAG_SCORE_REVERSE if score_reverse else 0), seed,
                         int(replicate_base), 0)
         self._keep = [np.ascontiguousarray(x, np.float64) for x in
                       (params.upsilon, params.gamma, params.alpha, params.beta, params.epsilon)]
@@ -219,6 +223,19 @@ class Sim:
         out = np.zeros((self.R, 8, self.N), np.float64)
         _check(self.L, self.h, self.L.sim_score(self.h, _p(out, ctypes.c_double), self._stream(stream)))
         return out
+
+    def score_backward(self, stream=None):
+        _check(self.L, self.h, self.L.sim_score_backward(self.h, self._stream(stream)))
+
+    def gradient_moments(self, days, stream=None):
+        """Returns (moments [n_days, 34], per-replicate scores [R, 8])."""
+        d = np.ascontiguousarray(days, np.int32)
+        out = np.zeros((d.size, 34), np.float64)
+        per = np.zeros((self.R, 8), np.float64)
+        _check(self.L, self.h, self.L.sim_gradient_moments(self.h, _p(d, ctypes.c_int32), d.size,
+                                                           _p(per, ctypes.c_double), _p(out, ctypes.c_double),
+                                                           self._stream(stream)))
+        return out, per
 
     def reset(self, clear_events=False):
         _check(self.L, self.h, self.L.sim_reset(self.h, 1 if clear_events else 0))

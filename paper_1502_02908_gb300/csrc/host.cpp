@@ -33,6 +33,12 @@ struct sim_handle {
   int32_t* d_err = nullptr;
   double* d_score = nullptr;
   double* d_tang = nullptr;
+  double* d_traj = nullptr;         // reverse-mode score trajectory [3][max_days][R][N]
+  int32_t score_day0 = 0;           // day since which score terms accumulate
+  double* d_per_rep = nullptr;      // [R][8]
+  double* d_moments = nullptr;      // scratch for sim_gradient_moments
+  int32_t* d_days = nullptr;
+  int32_t moments_cap = 0;
   int32_t* d_u0 = nullptr;          // [Nc][N] master copy for resets
   int32_t* d_order = nullptr;       // node order of the stochastic step
   int32_t n_big = 0;                // leading nodes of the order simulated one per warp
@@ -112,6 +118,7 @@ void free_all(sim_handle* h) {
   cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
   cudaFree(h->d_prev_n); cudaFree(h->d_ctr); cudaFree(h->d_err); cudaFree(h->d_score);
   cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0); cudaFree(h->d_order);
+  cudaFree(h->d_traj); cudaFree(h->d_per_rep); cudaFree(h->d_moments); cudaFree(h->d_days);
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -136,6 +143,7 @@ sim_status reset_state(sim_handle* h) {
   }
   CK(h, cudaDeviceSynchronize(), "reset");
   h->day = 0;
+  h->score_day0 = 0;
   return SIM_OK;
 }
 
@@ -156,6 +164,7 @@ SsaArgs ssa_args(sim_handle* h) {
   a.score = h->d_score; a.tang = h->d_tang; a.seed = h->cfg.seed; a.rep_base = h->cfg.replicate_base;
   a.N = h->cfg.n_nodes; a.R = h->cfg.n_replicates; a.Nc = h->nc; a.max_days = h->cfg.max_days;
   a.pre_event = (h->cfg.flags & SIM_FLAG_PHI_PRE_EVENT) ? 1 : 0;
+  a.traj = h->d_traj;
   a.order = h->d_order;
   a.n_big = h->n_big;
   a.warp_blocks = (h->n_big + 7) / 8;
@@ -347,7 +356,7 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     return fail(nullptr, SIM_E_INVALID_ARG, "n_nodes, n_replicates must be >= 1 and max_days >= 0");
   if (cfg->underflow_policy != SIM_UNDERFLOW_CLAMP && cfg->underflow_policy != SIM_UNDERFLOW_ERROR)
     return fail(nullptr, SIM_E_INVALID_ARG, "unknown underflow policy");
-  if (cfg->flags & ~(SIM_FLAG_PHI_PRE_EVENT | SIM_FLAG_SCORE))
+  if (cfg->flags & ~(SIM_FLAG_PHI_PRE_EVENT | SIM_FLAG_SCORE | SIM_FLAG_SCORE_REVERSE))
     return fail(nullptr, SIM_E_INVALID_ARG, "unknown flag bits");
   if (cfg->replicate_base < 0 || (int64_t)cfg->replicate_base + cfg->n_replicates > ((int64_t)1 << 32) ||
       cfg->reserved != 0)
@@ -357,6 +366,7 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
   sim_handle* h = new (std::nothrow) sim_handle();
   if (!h) return fail(nullptr, SIM_E_OOM, "host allocation");
   h->cfg = *cfg;
+  if (h->cfg.flags & SIM_FLAG_SCORE_REVERSE) h->cfg.flags |= SIM_FLAG_SCORE;
   h->n_age = cfg->model == SIM_SISE3 ? 3 : 1;
   h->nc = 2 * h->n_age;
   const int N = cfg->n_nodes, R = cfg->n_replicates;
@@ -406,10 +416,13 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
   if (e == cudaSuccess) e = dalloc(&h->d_err, 1);
   if (e == cudaSuccess) e = dalloc(&h->d_u0, h->u0.size());
   if (e == cudaSuccess) e = dalloc(&h->d_phi0, h->phi0.size());
-  if (e == cudaSuccess && (cfg->flags & SIM_FLAG_SCORE)) {
+  if (e == cudaSuccess && (h->cfg.flags & SIM_FLAG_SCORE)) {
     e = dalloc(&h->d_score, n_phi(h) * kScoreTerms);
     if (e == cudaSuccess) e = dalloc(&h->d_tang, n_phi(h) * 2);
+    if (e == cudaSuccess) e = dalloc(&h->d_per_rep, (size_t)R * kScoreTerms);
   }
+  if (e == cudaSuccess && (h->cfg.flags & SIM_FLAG_SCORE_REVERSE))
+    e = dalloc(&h->d_traj, (size_t)3 * (cfg->max_days > 0 ? cfg->max_days : 1) * n_phi(h));
   if (e == cudaSuccess) e = cudaMemcpy(h->d_params, h->params.data(), R * sizeof(DevParams), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_u0, h->u0.data(), h->u0.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_phi0, h->phi0.data(), h->phi0.size() * 8, cudaMemcpyHostToDevice);
@@ -578,6 +591,7 @@ sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi
   }
   CK(h, cudaStreamSynchronize(st), "stream synchronize");
   h->day = day;
+  h->score_day0 = day;
   return SIM_OK;
 }
 
@@ -597,6 +611,42 @@ sim_status sim_score(sim_handle* h, double* score, void* stream) {
   if (!h->d_score) return fail(h, SIM_E_STATE, "created without SIM_FLAG_SCORE");
   cudaStream_t st = (cudaStream_t)stream;
   CK(h, cudaMemcpyAsync(score, h->d_score, n_phi(h) * kScoreTerms * 8, cudaMemcpyDeviceToHost, st), "copy score");
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  return check_latched(h);
+}
+
+sim_status sim_score_backward(sim_handle* h, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (!h->d_traj) return fail(h, SIM_E_STATE, "created without SIM_FLAG_SCORE_REVERSE");
+  // the sweep covers [score_day0, day); days before score_day0 hold no trajectory
+  const int32_t nd = h->day - h->score_day0;
+  if (nd <= 0) return SIM_OK;
+  CK(h, launch_phi_backward(h->d_traj + (size_t)h->score_day0 * n_phi(h),
+                            h->d_params, h->d_score, h->cfg.n_nodes, h->cfg.n_replicates,
+                            h->cfg.max_days, nd, (cudaStream_t)stream), "phi backward launch");
+  return SIM_OK;
+}
+
+sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_days, double* per_rep,
+                                double* out, void* stream) {
+  if (!h || n_days < 0 || (n_days > 0 && (!days || !out))) return SIM_E_INVALID_ARG;
+  if (!h->d_score) return fail(h, SIM_E_STATE, "created without SIM_FLAG_SCORE");
+  for (int i = 0; i < n_days; ++i)
+    if (days[i] < 0 || days[i] >= h->cfg.max_days) return fail(h, SIM_E_INVALID_ARG, "days[%d] out of range", i);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_days > h->moments_cap) {
+    cudaFree(h->d_moments); cudaFree(h->d_days);
+    h->d_moments = nullptr; h->d_days = nullptr; h->moments_cap = 0;
+    CK(h, dalloc(&h->d_moments, (size_t)n_days * 34), "moments allocation");
+    CK(h, dalloc(&h->d_days, (size_t)n_days), "moments allocation");
+    h->moments_cap = n_days;
+  }
+  if (n_days > 0) CK(h, cudaMemcpyAsync(h->d_days, days, (size_t)n_days * 4, cudaMemcpyHostToDevice, st), "copy days");
+  CK(h, launch_gradient_moments(h->d_score, h->d_prev_i, h->d_prev_n, h->d_days, n_days, h->cfg.n_nodes,
+                                h->cfg.n_replicates, h->cfg.max_days, h->d_per_rep, h->d_moments, st),
+     "gradient moments launch");
+  if (per_rep) CK(h, cudaMemcpyAsync(per_rep, h->d_per_rep, (size_t)h->cfg.n_replicates * kScoreTerms * 8, cudaMemcpyDeviceToHost, st), "copy scores");
+  if (n_days > 0) CK(h, cudaMemcpyAsync(out, h->d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st), "copy moments");
   CK(h, cudaStreamSynchronize(st), "stream synchronize");
   return check_latched(h);
 }

@@ -38,6 +38,7 @@ struct SsaArgs {
   int32_t day;                // day simulated by this launch
   int32_t prologue;           // 1: first record stats of day-1 and (post-event mode) update phi
   int32_t pre_event;          // 1: phi update from post-SSA counts in the epilogue
+  double* traj;               // reverse-mode score: [3][max_days][R][N] = c_d, phi_d, I_d/N_d (NULL otherwise)
   const int32_t* order;       // node order: first n_big nodes warp-cooperative, the rest per thread (NULL: identity)
   int32_t n_big;              // nodes simulated one per warp
   int32_t warp_blocks;        // blocks (of 8 warps) given to them
@@ -93,6 +94,18 @@ cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
 // After the last day of a call: phi update (post-event mode) and statistics of day a.day.
 cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
 cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st);
+
+// Reverse sweep of the phi recursion over days [0, ndays) for every (r, v):
+// lambda_d = c_d + (1 - beta_d) lambda_{d+1}; adds -lambda_{d+1} phi_d to the
+// beta score and lambda_{d+1} q_d to the alpha score of the node.
+cudaError_t launch_phi_backward(const double* traj, const DevParams* params, double* score, int N, int R,
+                                int max_days, int ndays, cudaStream_t st);
+// Per replicate: f = infected/animals after each listed day, s = score summed over
+// nodes; moments per listed day [n_days][34]: sum f, sum f^2, then per score term
+// k: sum s_k, sum s_k^2, sum f s_k, sum (f s_k)^2.
+cudaError_t launch_gradient_moments(const double* score, const unsigned long long* prev_i,
+                                    const unsigned long long* prev_n, const int32_t* days, int n_days, int N,
+                                    int R, int max_days, double* per_rep /*[R][8]*/, double* out, cudaStream_t st);
 cudaError_t launch_debug_div(const double* x, const double* y, double* out, double* ref, int64_t n, cudaStream_t st);
 
 }  // namespace episim

@@ -48,7 +48,10 @@ __device__ __forceinline__ double phi_step(const SsaArgs& a, const DevParams& p,
   double dI = i2d_exact(I), dN = i2d_exact(tot);
   if (tot > 0) { const double aI = __dmul_rn(p.alpha, dI); q = pos(aI) ? div_pos(aI, dN) : 0.0; }
   double next = __dadd_rn(__dadd_rn(__dmul_rn(phi, omb), q), p.eps);
-  if (SCORE) {
+  if (SCORE && a.traj) {
+    const double ion = (tot > 0 && I > 0) ? div_pos(dI, dN) : 0.0;
+    a.traj[((size_t)2 * a.max_days + day) * a.R * a.N + (size_t)r * a.N + v] = ion;
+  } else if (SCORE) {
     double* tb = a.tang + ((size_t)r * 2 + 0) * a.N + v;
     double* ta = a.tang + ((size_t)r * 2 + 1) * a.N + v;
     double ion = (tot > 0 && I > 0) ? div_pos(dI, dN) : 0.0;
@@ -363,6 +366,12 @@ __device__ __forceinline__ void accumulate_score(const SsaArgs& a, const DevPara
 #pragma unroll
   for (int j = 0; j < NA; ++j) ninf = __dadd_rn(ninf, T[j].n_inf);
   double cd = __dsub_rn((pos(phi) && pos(ninf)) ? div_pos(ninf, phi) : 0.0, ups_int);
+  if (a.traj) {
+    const size_t plane = (size_t)a.max_days * a.R * a.N, at = (size_t)a.day * a.R * a.N + (size_t)r * a.N + v;
+    a.traj[at] = cd;
+    a.traj[plane + at] = phi;
+    return;
+  }
   const double* tb = a.tang + ((size_t)r * 2 + 0) * a.N + v;
   const double* ta = a.tang + ((size_t)r * 2 + 1) * a.N + v;
   sc[(size_t)6 * a.N] = __dadd_rn(sc[(size_t)6 * a.N], __dmul_rn(cd, *tb));
@@ -375,18 +384,20 @@ __device__ __forceinline__ void accumulate_score(const SsaArgs& a, const DevPara
 // first a.n_big nodes of the order (warp-cooperative method); the other blocks
 // give each thread one of the remaining nodes.
 template <int NA, bool SCORE, int MODE>
-__global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a) {
-  const int r = blockIdx.y;
+__global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_rep) {
+  // 1-D grid: replicate r owns blocks [r * blocks_per_rep, (r + 1) * blocks_per_rep)
+  const int r = (int)(blockIdx.x / (unsigned)blocks_per_rep);
+  const int bx = (int)(blockIdx.x - (unsigned)r * (unsigned)blocks_per_rep);
   const int lane = threadIdx.x & 31;
-  const bool warp_role = (MODE == 0) && !SCORE && (int)blockIdx.x < a.warp_blocks;
+  const bool warp_role = (MODE == 0) && !SCORE && bx < a.warp_blocks;
   int v;
   bool active;
   if (warp_role) {
-    const int wi = (int)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int wi = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     active = wi < a.n_big;
     v = active ? a.order[wi] : 0;
   } else {
-    const int i = ((int)blockIdx.x - ((MODE == 0 && !SCORE) ? a.warp_blocks : 0)) * blockDim.x + threadIdx.x;
+    const int i = (bx - ((MODE == 0 && !SCORE) ? a.warp_blocks : 0)) * blockDim.x + threadIdx.x;
     const int base = (MODE == 0 && !SCORE && a.order) ? a.n_big : 0;
     active = i + base < a.N;
     v = active ? (a.order && MODE == 0 && !SCORE ? a.order[base + i] : i + base) : 0;
@@ -438,13 +449,14 @@ template <int MODE>
 static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
   const int warp_blocks = (MODE == 0 && !score) ? a.warp_blocks : 0;
   const int n_thread = a.N - ((MODE == 0 && !score && a.order) ? a.n_big : 0);
-  dim3 block(256), grid(warp_blocks + (n_thread + 255) / 256, a.R);
+  const int bpr = warp_blocks + (n_thread + 255) / 256;
+  dim3 block(256), grid((unsigned)((int64_t)bpr * a.R));
   if (n_age == 1) {
-    if (score) k_node_day<1, true, MODE><<<grid, block, 0, st>>>(a);
-    else k_node_day<1, false, MODE><<<grid, block, 0, st>>>(a);
+    if (score) k_node_day<1, true, MODE><<<grid, block, 0, st>>>(a, bpr);
+    else k_node_day<1, false, MODE><<<grid, block, 0, st>>>(a, bpr);
   } else {
-    if (score) k_node_day<3, true, MODE><<<grid, block, 0, st>>>(a);
-    else k_node_day<3, false, MODE><<<grid, block, 0, st>>>(a);
+    if (score) k_node_day<3, true, MODE><<<grid, block, 0, st>>>(a, bpr);
+    else k_node_day<3, false, MODE><<<grid, block, 0, st>>>(a, bpr);
   }
   return cudaGetLastError();
 }
@@ -493,6 +505,95 @@ __global__ void k_broadcast_bytes(unsigned char* dst, const unsigned char* src, 
 cudaError_t launch_broadcast(void* dst, const void* src, size_t bytes, int copies, cudaStream_t st) {
   if (bytes == 0 || copies <= 0) return cudaSuccess;
   k_broadcast_bytes<<<152 * 8, 256, 0, st>>>((unsigned char*)dst, (const unsigned char*)src, bytes, copies);
+  return cudaGetLastError();
+}
+
+}  // namespace episim
+
+namespace episim {
+
+// Reverse sweep, one thread per (replicate, node); day-major storage makes
+// every day's read coalesced.  Streams 24 bytes per node-day from HBM.
+__global__ void __launch_bounds__(256) k_phi_backward(const double* __restrict__ traj, const DevParams* params,
+                                                      double* score, int N, int R, int max_days, int ndays) {
+  const int bpr = (N + 255) / 256;
+  const int r = (int)(blockIdx.x / (unsigned)bpr);
+  const int v = (int)(blockIdx.x - (unsigned)r * (unsigned)bpr) * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const size_t plane = (size_t)max_days * R * N, stride = (size_t)R * N;
+  const DevParams& p = params[r];
+  double lam = 0.0, sb = 0.0, sa = 0.0;           // lambda_{d+1}
+  const double* c = traj + (size_t)r * N + v;
+  for (int d = ndays - 1; d >= 0; --d) {
+    const size_t at = (size_t)d * stride;
+    const double cd = __ldcs(c + at);
+    const double ph = __ldcs(c + plane + at);
+    const double q = __ldcs(c + 2 * plane + at);
+    sb = __dsub_rn(sb, __dmul_rn(lam, ph));
+    sa = __dadd_rn(sa, __dmul_rn(lam, q));
+    lam = __dadd_rn(cd, __dmul_rn(__dadd_rn(1.0, -p.beta[season_of(d)]), lam));
+  }
+  double* sc = score + (size_t)r * kScoreTerms * N + v;
+  sc[(size_t)6 * N] = __dadd_rn(sc[(size_t)6 * N], sb);
+  sc[(size_t)7 * N] = __dadd_rn(sc[(size_t)7 * N], sa);
+}
+
+cudaError_t launch_phi_backward(const double* traj, const DevParams* params, double* score, int N, int R,
+                                int max_days, int ndays, cudaStream_t st) {
+  if (ndays <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((int64_t)((N + 255) / 256) * R));
+  k_phi_backward<<<grid, 256, 0, st>>>(traj, params, score, N, R, max_days, ndays);
+  return cudaGetLastError();
+}
+
+// Per-replicate score sums over nodes, fixed order: 256-thread block partials in
+// a fixed tree, blocks added in index order by one thread.
+__global__ void __launch_bounds__(256) k_score_sum(const double* score, int N, double* per_rep) {
+  const int r = blockIdx.x / kScoreTerms, k = blockIdx.x % kScoreTerms;
+  __shared__ double sh[256];
+  const double* row = score + ((size_t)r * kScoreTerms + k) * N;
+  double acc = 0.0;
+  for (int v = threadIdx.x; v < N; v += 256) acc = __dadd_rn(acc, row[v]);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = __dadd_rn(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) per_rep[(size_t)r * kScoreTerms + k] = sh[0];
+}
+
+__global__ void k_gradient_moments(const double* per_rep, const unsigned long long* prev_i,
+                                   const unsigned long long* prev_n, const int32_t* days, int n_days, int R,
+                                   int max_days, double* out) {
+  const int di = blockIdx.x;
+  if (di >= n_days || threadIdx.x != 0) return;
+  const int d = days[di];
+  double m[34];
+  for (int i = 0; i < 34; ++i) m[i] = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const unsigned long long I = prev_i[(size_t)r * max_days + d], T = prev_n[(size_t)r * max_days + d];
+    const double f = T ? __ddiv_rn((double)I, (double)T) : 0.0;
+    m[0] = __dadd_rn(m[0], f);
+    m[1] = __dadd_rn(m[1], __dmul_rn(f, f));
+    for (int k = 0; k < kScoreTerms; ++k) {
+      const double sk = per_rep[(size_t)r * kScoreTerms + k], fs = __dmul_rn(f, sk);
+      m[2 + 4 * k] = __dadd_rn(m[2 + 4 * k], sk);
+      m[3 + 4 * k] = __dadd_rn(m[3 + 4 * k], __dmul_rn(sk, sk));
+      m[4 + 4 * k] = __dadd_rn(m[4 + 4 * k], fs);
+      m[5 + 4 * k] = __dadd_rn(m[5 + 4 * k], __dmul_rn(fs, fs));
+    }
+  }
+  for (int i = 0; i < 34; ++i) out[(size_t)di * 34 + i] = m[i];
+}
+
+cudaError_t launch_gradient_moments(const double* score, const unsigned long long* prev_i,
+                                    const unsigned long long* prev_n, const int32_t* days, int n_days, int N,
+                                    int R, int max_days, double* per_rep, double* out, cudaStream_t st) {
+  k_score_sum<<<R * kScoreTerms, 256, 0, st>>>(score, N, per_rep);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_days <= 0) return e;
+  k_gradient_moments<<<n_days, 32, 0, st>>>(per_rep, prev_i, prev_n, days, n_days, R, max_days, out);
   return cudaGetLastError();
 }
 

@@ -223,3 +223,19 @@ def test_warp_per_node_path_bitexact_sise_many_transitions():
     assert np.array_equal(counts, ref.counts)
     _assert_phi(phi, ref.phi)
     assert np.array_equal(ctr, ref.counters)
+
+
+def test_reverse_score_sweep_matches_oracle_tangents():
+    w = W.sise_plain(N=300, T=60, n_events=3000, R=3)
+    s = B.Sim.from_workload(w, score_reverse=True)
+    s.run(w.T)
+    s.score_backward()
+    sc = s.score()
+    s.close()
+    ref = oracle.run(w, score=True)
+    # upsilon / gamma terms: same operation order, identical
+    np.testing.assert_allclose(sc[:, :6], ref.score[:, :6], rtol=PHI_RTOL, atol=1e-300)
+    # beta / alpha: reverse sweep vs forward tangents, a different summation order
+    for k in (6, 7):
+        scale = np.abs(ref.score[:, k]).max()
+        assert np.max(np.abs(sc[:, k] - ref.score[:, k])) <= 1e-9 * scale
