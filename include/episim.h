@@ -167,6 +167,22 @@ sim_status sim_score_backward(sim_handle* h, void* stream);
 sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_days, double* per_rep,
                                 double* out, void* stream);
 
+/* The same result as sim_gradient_moments, from a call that allocates no
+ * memory.  The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc -- code whose device memory belongs to another allocator (a
+ * framework's caching pool, an application with a fixed memory budget) or that
+ * must avoid the device synchronisation and fragmentation an allocation can
+ * cause.  Its scratch is one fixed array in the library's device image (about
+ * 650 KiB on every GPU that loads the library, kept until exit), which limits a
+ * call to at most 8192 replicates and 512 days; larger requests return
+ * SIM_E_INVALID_ARG.  The first call on each device looks the array's device
+ * address up once (make it before any stream capture).  Every call shares the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  Nothing needs clearing between calls.  Host outputs; synchronises
+ * `stream`. */
+sim_status sim_gradient_moments_noalloc(sim_handle* h, const int32_t* days, int32_t n_days,
+                                        double* per_rep, double* out, void* stream);
+
 /* Back to day 0 with the initial counts and phi; statistics and score cleared.
  * clear_events = 1 also drops the loaded events. */
 sim_status sim_reset(sim_handle* h, int32_t clear_events);

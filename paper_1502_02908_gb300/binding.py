@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
             "sim_tune": [vp, i32],
             "sim_score_backward": [vp, vp],
             "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
+            "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
             "sim_profile_read": [vp, pd, pi64],
         }
         for name, args in sigs.items():

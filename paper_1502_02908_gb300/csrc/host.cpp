@@ -345,6 +345,17 @@ cudaError_t traced(sim_handle* h, int kind, cudaStream_t st, F&& fn) {
 
 }  // namespace
 
+namespace episim {
+sim_status handle_score_view(sim_handle* h, HandleScoreView* out) {
+  if (!h->d_score) return fail(h, SIM_E_STATE, "created without SIM_FLAG_SCORE");
+  out->score = h->d_score; out->prev_i = h->d_prev_i; out->prev_n = h->d_prev_n;
+  out->N = h->cfg.n_nodes; out->R = h->cfg.n_replicates; out->max_days = h->cfg.max_days;
+  return SIM_OK;
+}
+sim_status handle_fail(sim_handle* h, sim_status s, const char* msg) { return fail(h, s, "%s", msg); }
+sim_status handle_cuda_fail(sim_handle* h, cudaError_t e, const char* what) { return cuda_fail(h, e, what); }
+}  // namespace episim
+
 extern "C" {
 
 sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "../../include/episim.h"
 
 namespace episim {
 
@@ -113,4 +114,18 @@ cudaError_t launch_debug_div(const double* x, const double* y, double* out, doub
 namespace episim {
 // dst holds `copies` back-to-back copies of the `bytes` bytes at src (device pointers).
 cudaError_t launch_broadcast(void* dst, const void* src, size_t bytes, int copies, cudaStream_t st);
+}  // namespace episim
+
+struct sim_handle;
+namespace episim {
+// Read-only view of a handle's score state for entry points outside host.cpp.
+struct HandleScoreView {
+  const double* score;
+  const unsigned long long* prev_i;
+  const unsigned long long* prev_n;
+  int N, R, max_days;
+};
+sim_status handle_score_view(sim_handle* h, HandleScoreView* out);
+sim_status handle_fail(sim_handle* h, sim_status s, const char* msg);
+sim_status handle_cuda_fail(sim_handle* h, cudaError_t e, const char* what);
 }  // namespace episim
