@@ -219,6 +219,27 @@ sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold);
 /* Number of nodes currently simulated one per warp (-1 for a NULL handle). */
 int32_t sim_warp_nodes(const sim_handle* h);
 
+/* Batched and uneven runs: advances every listed handle (all on the current
+ * device; any mix of models, node and replicate counts, horizons, events and
+ * parameters) to day until[i] (NULL: each handle's max_days) in ONE persistent
+ * work-stealing kernel launch.  Blocks fetch work items -- stochastic-step
+ * chunks of an (instance, replicate, day), event steps of an (instance,
+ * replicate, day), finalisation chunks -- from one atomic counter in a
+ * dependency-respecting order and wait for their inputs with bounded spins.
+ * Results are identical to running each handle alone with sim_run_days.
+ * Synchronous on `stream`.  A wait that runs out aborts the launch and returns
+ * SIM_E_TIMEOUT (the batch's state is then undefined); device errors of a
+ * handle are latched in it as for sim_run_days. */
+sim_status sim_run_batch(sim_handle** handles, int32_t n, const int32_t* until, void* stream);
+
+/* Test hooks for the batch kernel's failure path: sets the number of polls a
+ * dependency wait makes before giving up (default ~2 s worth); runs h (whose
+ * day must be >= 1) in a batch whose first dependency is never met, so that the
+ * wait runs out and the call returns SIM_E_TIMEOUT with the device usable.  The
+ * handle's state is undefined afterwards (sim_reset or sim_set_state it). */
+sim_status sim_debug_batch_spin_limit(int64_t limit);
+sim_status sim_debug_batch_stall(sim_handle* h, int32_t until, int64_t spin_limit);
+
 /* Kernel timing (tracing).  While enabled, every kernel the handle launches is
  * bracketed by CUDA events on its stream.  sim_profile_read synchronises and
  * returns, per kernel kind (0 = stochastic step, 1 = events, 2 = phi/statistics

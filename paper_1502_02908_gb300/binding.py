@@ -85,6 +85,9 @@ def load_library(build_if_missing: bool = True):
             "sim_score_backward": [vp, vp],
             "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
+            "sim_run_batch": [P(vp), i32, pi32, vp],
+            "sim_debug_batch_spin_limit": [i64],
+            "sim_debug_batch_stall": [vp, i32, i64],
             "sim_profile_read": [vp, pd, pi64],
         }
         for name, args in sigs.items():
@@ -272,6 +275,16 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def run_batch(sims, until=None, stream=None):
+    """Advances several Sim handles together in one persistent kernel launch."""
+    L = load_library()
+    arr = (ctypes.c_void_p * len(sims))(*[s.h for s in sims])
+    u = None if until is None else np.ascontiguousarray(until, np.int32)
+    st = current_stream() if stream is None else ctypes.c_void_p(stream)
+    status = L.sim_run_batch(arr, len(sims), _p(u, ctypes.c_int32), st)
+    _check(L, None, status)
 
 
 def debug_div(x, y, out, ref, n, device):

@@ -1,0 +1,42 @@
+// Descriptors of the persistent batch kernel (batch.cu), filled by host.cpp.
+#pragma once
+#include "internal.h"
+
+namespace episim {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchTimeout = 2;      // error bit: a bounded wait ran out
+
+struct BatchInst {
+  SsaArgs ssa;            // node order / warp split set for kBatchThreads-thread chunks
+  EvSmemArgs evs;
+  EvArgs evg;
+  const int32_t* day_smem;  // [max_days] shared memory of the staged event step (0: global variant)
+  int32_t na, score, has_events;
+  int32_t bpr;            // stochastic-step chunks per replicate
+  int32_t tbpr;           // finalisation chunks per replicate
+  int32_t day0, ndays;
+  unsigned* ssa_done;     // [R] chunks completed in this run
+  unsigned* ev_done;      // [R] 1 + last day whose events are applied (starts at day0)
+};
+
+struct BatchCtl {
+  const BatchInst* inst;  // [n_inst], longest horizon first
+  const long long* cumA;  // [n_inst + 1] prefix sums of R * bpr
+  const long long* cumB;  // [n_inst + 1] prefix sums of R
+  const long long* cumF;  // [n_inst + 1] prefix sums of R * tbpr
+  const long long* step_off;  // [n_steps + 1] first item of each step
+  const int32_t* active;  // [n_steps] instances still running at each step (a prefix)
+  unsigned long long* next;
+  int* abort;
+  int* err;
+  long long total_main, total;
+  long long spin_limit;
+  int n_inst, n_steps;
+  int smem_cap;
+};
+
+cudaError_t launch_batch(const BatchCtl& c, int grid, cudaStream_t st);
+cudaError_t batch_occupancy(int smem_bytes, int* blocks_per_sm);
+
+}  // namespace episim

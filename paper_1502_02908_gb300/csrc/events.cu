@@ -1,147 +1,6 @@
-// Deterministic step (Eq. (numstep4); Sec. 3.3 "read and incorporate"; Alg. 1
-// line 13): the day's scheduled events (Sec. 3.2, Eq. (event)) applied level by
-// level.  The host assigns levels so that, within a level, no two events sample
-// the same node and no node is both sampled and added to; adds that share a node
-// commute and use integer atomics.  The result equals applying the events one
-// by one in their input order (scheduling rule 2(b) of Sec. 3.6 applied per node).
-//
-// One block per replicate; its threads take a level's events in parallel, with a
-// block barrier between levels.  Removed animals are drawn without replacement,
-// uniformly over the selected compartments, one at a time (Lemire's bounded
-// integers on the event's own Philox word stream).
-#include "internal.h"
-#include "devmath.cuh"
+// Kernels of the deterministic step; the device code is in events_device.cuh.
+#include "events_device.cuh"
 
-namespace episim {
-
-namespace {
-
-struct WordStream {
-  uint4 ctr;
-  uint32_t k0, k1;
-  uint4 buf;
-  uint32_t q;
-  __device__ uint32_t operator()() {
-    if ((q & 3u) == 0u) { ctr.z = q >> 2; buf = philox10(ctr, k0, k1); }
-    uint32_t sel = q & 3u;
-    ++q;
-    return sel == 0 ? buf.x : sel == 1 ? buf.y : sel == 2 ? buf.z : buf.w;
-  }
-};
-
-template <int NA>
-__device__ __forceinline__ void apply_event(const EvArgs& a, int32_t* X, int r, int4 rec,
-                                            unsigned& applied, unsigned& clamped, unsigned& skipped) {
-  const int N = a.N;
-  const int node = rec.x, dest = rec.y, e = rec.z;
-  const int kind = rec.w & 3;
-  const int cls = ((rec.w >> 2) & 3) - 1;
-  const int32_t n = (int32_t)((uint32_t)rec.w >> 4);
-  if (kind == 1) {  // enter: susceptible animals of class cls (class 0 for -1)
-    const int j = cls < 0 ? 0 : cls;
-    atomicAdd(&X[(size_t)(2 * j) * N + node], n);
-    ++applied;
-    return;
-  }
-  // selected compartments: both states of class cls, or every compartment
-  const int c_lo = cls < 0 ? 0 : 2 * cls;
-  const int c_hi = cls < 0 ? 2 * NA : 2 * cls + 2;
-  int32_t have[2 * NA];
-  int32_t took[2 * NA];
-  int64_t avail = 0;
-#pragma unroll
-  for (int c = 0; c < 2 * NA; ++c) {
-    have[c] = (c >= c_lo && c < c_hi) ? X[(size_t)c * N + node] : 0;
-    took[c] = 0;
-    avail += have[c];
-  }
-  int32_t take = n;
-  if ((int64_t)n > avail) {
-    if (a.underflow_error) {
-      ++skipped;
-      atomicOr(a.err, 1);
-      return;
-    }
-    take = (int32_t)avail;
-    ++clamped;
-  }
-  WordStream ws;
-  ws.ctr = make_uint4((uint32_t)e, (uint32_t)a.day | kEventTag, 0u, (uint32_t)(a.rep_base + r));
-  ws.k0 = (uint32_t)a.seed;
-  ws.k1 = (uint32_t)(a.seed >> 32);
-  ws.q = 0;
-  for (int32_t t = 0; t < take; ++t) {
-    uint32_t slot = lemire((uint32_t)(avail - t), ws);
-    bool done = false;
-#pragma unroll
-    for (int c = 0; c < 2 * NA; ++c) {
-      if (!done) {
-        if (slot < (uint32_t)have[c]) { have[c] -= 1; took[c] += 1; done = true; }
-        else slot -= (uint32_t)have[c];
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 2 * NA; ++c) {
-    if (c >= c_lo && c < c_hi) X[(size_t)c * N + node] = have[c];
-  }
-  if (kind == 2) {  // aging: same state, next class of the same node
-#pragma unroll
-    for (int c = 0; c + 2 < 2 * NA; ++c)
-      if (took[c]) X[(size_t)(c + 2) * N + node] += took[c];
-  } else if (kind == 3) {  // external transfer to dest
-#pragma unroll
-    for (int c = 0; c < 2 * NA; ++c)
-      if (took[c]) atomicAdd(&X[(size_t)c * N + dest], took[c]);
-  }
-  ++applied;
-}
-
-template <int NA>
-__global__ void __launch_bounds__(512) k_events_day(EvArgs a) {
-  const int r = blockIdx.x;
-  int32_t* X = a.counts + (size_t)r * a.Nc * a.N;
-  const int l0 = a.day_lvl[a.day], l1 = a.day_lvl[a.day + 1];
-  unsigned applied = 0, clamped = 0, skipped = 0;
-  for (int l = l0; l < l1; ++l) {
-    const int b = a.lvl_start[l], end = a.lvl_start[l + 1];
-    for (int q = b + (int)threadIdx.x; q < end; q += blockDim.x)
-      apply_event<NA>(a, X, r, a.rec[q], applied, clamped, skipped);
-    __syncthreads();
-  }
-  // counters
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    applied += __shfl_down_sync(0xffffffffu, applied, o);
-    clamped += __shfl_down_sync(0xffffffffu, clamped, o);
-    skipped += __shfl_down_sync(0xffffffffu, skipped, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    unsigned long long* c = a.ctr + (size_t)r * 4;
-    if (applied) atomicAdd(c + 1, (unsigned long long)applied);
-    if (clamped) atomicAdd(c + 2, (unsigned long long)clamped);
-    if (skipped) atomicAdd(c + 3, (unsigned long long)skipped);
-  }
-}
-
-}  // namespace
-
-cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st) {
-  if (n_age == 1) k_events_day<1><<<a.R, 512, 0, st>>>(a);
-  else k_events_day<3><<<a.R, 512, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-}  // namespace episim
-
-// ---------------------------------------------------------------------------
-// Staged variant.  Per replicate block: the day's records, the first two
-// Philox blocks of every event, the level offsets and the counts of every node
-// the day touches are loaded into shared memory; levels wider than a warp are
-// processed by the whole block with a block barrier after each, narrower levels
-// by warp 0 alone with a warp barrier (the deep tail of a hub node's chain);
-// counts are written back at the end.  Same results as the global-memory
-// variant, bit for bit.
 namespace episim {
 
 size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc) {
@@ -151,241 +10,24 @@ size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, 
 
 namespace {
 
-struct Words8 {
-  uint4 a, b;
-};
-
-// Word stream of one event: the two precomputed Philox blocks, then further
-// blocks computed on demand (events of more than 8 animals or with rejections).
-struct EventWords {
-  Words8 w;
-  uint4 extra;
-  uint32_t q, e, day, rep, k0, k1;
-  __device__ __forceinline__ uint32_t operator()() {
-    const uint32_t i = q++;
-    if (i < 4u) return i == 0 ? w.a.x : i == 1 ? w.a.y : i == 2 ? w.a.z : w.a.w;
-    if (i < 8u) return i == 4 ? w.b.x : i == 5 ? w.b.y : i == 6 ? w.b.z : w.b.w;
-    if ((i & 3u) == 0u) extra = philox10(make_uint4(e, day | kEventTag, i >> 2, rep), k0, k1);
-    const uint32_t sel = i & 3u;
-    return sel == 0 ? extra.x : sel == 1 ? extra.y : sel == 2 ? extra.z : extra.w;
-  }
-};
-
-template <bool ATOMIC>
-__device__ __forceinline__ void add_count(int32_t* p, int32_t v) {
-  if (ATOMIC) atomicAdd(p, v); else *p += v;
-}
-
-template <int NA, bool ATOMIC>
-__device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* cnt, uint32_t rep, int4 rec,
-                                                 const Words8& w8, unsigned& applied, unsigned& clamped,
-                                                 unsigned& skipped) {
-  constexpr int NC = 2 * NA;
-  const int src = rec.x, dst = rec.y;
-  const int kind = rec.w & 3;
-  const int cls = ((rec.w >> 2) & 3) - 1;
-  const int32_t n = (int32_t)((uint32_t)rec.w >> 4);
-  int32_t* cs = cnt + src * NC;
-  if (kind == 1) {                                   // enter: susceptibles of the class
-    add_count<ATOMIC>(&cs[2 * (cls < 0 ? 0 : cls)], n);
-    ++applied;
-    return;
-  }
-  EventWords ws;
-  ws.w = w8; ws.q = 0; ws.e = (uint32_t)rec.z; ws.day = (uint32_t)a.day; ws.rep = rep;
-  ws.k0 = (uint32_t)a.seed; ws.k1 = (uint32_t)(a.seed >> 32);
-  if (cls >= 0) {
-    // one class: draws pick S or I
-    const int32_t s0 = cs[2 * cls], s1 = cs[2 * cls + 1];
-    const int32_t avail = s0 + s1;
-    int32_t take = n;
-    if (n > avail) {
-      if (a.underflow_error) { ++skipped; atomicOr(a.err, 1); return; }
-      take = avail;
-      ++clamped;
-    }
-    int32_t t0, t1;
-    if (take == avail) { t0 = s0; t1 = s1; }
-    else if (s0 == 0) { t0 = 0; t1 = take; }
-    else if (s1 == 0) { t0 = take; t1 = 0; }
-    else {
-      t0 = 0; t1 = 0;
-      for (int32_t k = 0; k < take; ++k) {
-        const uint32_t slot = lemire((uint32_t)(avail - k), ws);
-        if (slot < (uint32_t)(s0 - t0)) ++t0; else ++t1;
-      }
-    }
-    cs[2 * cls] = s0 - t0;
-    cs[2 * cls + 1] = s1 - t1;
-    if (kind == 2) {                                 // aging: same state, next class
-      cs[2 * cls + 2] += t0;
-      cs[2 * cls + 3] += t1;
-    } else if (kind == 3) {
-      int32_t* cd = cnt + dst * NC;
-      if (t0) add_count<ATOMIC>(&cd[2 * cls], t0);
-      if (t1) add_count<ATOMIC>(&cd[2 * cls + 1], t1);
-    }
-    ++applied;
-    return;
-  }
-  // every class: draws over all compartments in order
-  int32_t have[NC];
-  int32_t avail = 0, nonempty = 0;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    have[c] = cs[c];
-    avail += have[c];
-    nonempty += have[c] > 0 ? 1 : 0;
-  }
-  int32_t take = n;
-  if (n > avail) {
-    if (a.underflow_error) { ++skipped; atomicOr(a.err, 1); return; }
-    take = avail;
-    ++clamped;
-  }
-  int32_t took[NC];
-  if (take == avail || nonempty <= 1) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      took[c] = (take == avail) ? have[c] : (have[c] > 0 ? take : 0);
-      cs[c] = have[c] - took[c];
-    }
-  } else {
-    int32_t cum[NC];
-    int32_t acc = 0;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) { acc += have[c]; cum[c] = acc; took[c] = 0; }
-    for (int32_t k = 0; k < take; ++k) {
-      const uint32_t slot = lemire((uint32_t)(avail - k), ws);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        // compartment c is hit when slot falls in [cum[c-1], cum[c])
-        const bool hit = slot < (uint32_t)cum[c] && (c == 0 || slot >= (uint32_t)cum[c > 0 ? c - 1 : 0]);
-        took[c] += hit ? 1 : 0;
-      }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) cum[c] -= (slot < (uint32_t)cum[c]) ? 1 : 0;
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) cs[c] = have[c] - took[c];
-  }
-  if (kind == 3) {
-    int32_t* cd = cnt + dst * NC;
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (took[c]) add_count<ATOMIC>(&cd[c], took[c]);
-  }
-  ++applied;
+template <int NA>
+__global__ void __launch_bounds__(512) k_events_day(EvArgs a) {
+  events_block_global<NA>(a, blockIdx.x);
 }
 
 template <int NA>
 __global__ void __launch_bounds__(512, 1) k_events_day_smem(EvSmemArgs a) {
-  constexpr int NC = 2 * NA;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int r = blockIdx.x;
-  const uint32_t rep = (uint32_t)(a.rep_base + r);
-  int32_t* X = a.counts + (size_t)r * NC * a.N;
-  const int l0 = a.day_lvl[a.day], l1 = a.day_lvl[a.day + 1];
-  const int e0 = a.lvl_start[l0], e1 = a.lvl_start[l1];
-  const int nev = e1 - e0, nlev = l1 - l0;
-  const int t0 = a.day_touch[a.day], t1 = a.day_touch[a.day + 1];
-  const int nt = t1 - t0;
-  int4* srec = reinterpret_cast<int4*>(smem);
-  Words8* swords = reinterpret_cast<Words8*>(smem + (size_t)nev * 16);
-  int32_t* scnt = reinterpret_cast<int32_t*>(smem + (size_t)nev * 48);
-  int32_t* slvl = scnt + (size_t)nt * NC;
-  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-  // counts of the touched nodes: one node per thread, its compartments in flight together
-  for (int i0 = threadIdx.x; i0 < nt; i0 += 4 * blockDim.x) {
-    int v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * blockDim.x;
-      v[u] = i < nt ? a.touched[t0 + i] : -1;
-    }
-    int32_t x[4][NC];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) x[u][c] = v[u] >= 0 ? X[(size_t)c * a.N + v[u]] : 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < nt) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) scnt[i * NC + c] = x[u][c];
-      }
-    }
-  }
-  for (int i = threadIdx.x; i < nev; i += blockDim.x) {
-    const int4 rc = a.rec[e0 + i];
-    srec[i] = rc;
-    const uint4 c0 = make_uint4((uint32_t)rc.z, (uint32_t)a.day | kEventTag, 0u, rep);
-    Words8 w;
-    w.a = philox10(c0, k0, k1);
-    w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
-    swords[i] = w;
-  }
-  for (int i = threadIdx.x; i <= nlev; i += blockDim.x) slvl[i] = a.lvl_start[l0 + i] - e0;
-  __syncthreads();
-  unsigned applied = 0, clamped = 0, skipped = 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int l = 0;
-  while (l < nlev) {
-    const int b = slvl[l], end = slvl[l + 1];
-    if (end - b > 32) {
-      for (int q = b + (int)threadIdx.x; q < end; q += blockDim.x)
-        apply_event_smem<NA, true>(a, scnt, rep, srec[q], swords[q], applied, clamped, skipped);
-      __syncthreads();
-      ++l;
-      continue;
-    }
-    // a run of narrow levels: warp 0 alone (lane i takes the level's i-th event),
-    // the other warps wait at the barrier after the run
-    int lr = l;
-    while (lr < nlev && slvl[lr + 1] - slvl[lr] <= 32) ++lr;
-    if (warp == 0) {
-      int bb = b, ee = end;
-      int4 rc = (bb + lane < ee) ? srec[bb + lane] : make_int4(0, 0, 0, 0);
-      Words8 wd;
-      if (bb + lane < ee) wd = swords[bb + lane];
-      for (int k = l; k < lr; ++k) {
-        // prefetch the next level's record while this one is applied
-        const int nb = ee, ne = (k + 1 < lr) ? slvl[k + 2] : ee;
-        int4 nrc = make_int4(0, 0, 0, 0);
-        Words8 nwd;
-        if (nb + lane < ne) { nrc = srec[nb + lane]; nwd = swords[nb + lane]; }
-        if (bb + lane < ee) apply_event_smem<NA, true>(a, scnt, rep, rc, wd, applied, clamped, skipped);
-        __syncwarp();
-        bb = nb; ee = ne; rc = nrc; wd = nwd;
-      }
-    }
-    __syncthreads();
-    l = lr;
-  }
-  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-    const int v = a.touched[t0 + i];
-    int32_t x[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) x[c] = scnt[i * NC + c];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) X[(size_t)c * a.N + v] = x[c];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    applied += __shfl_down_sync(0xffffffffu, applied, o);
-    clamped += __shfl_down_sync(0xffffffffu, clamped, o);
-    skipped += __shfl_down_sync(0xffffffffu, skipped, o);
-  }
-  if (lane == 0) {
-    unsigned long long* c = a.ctr + (size_t)r * 4;
-    if (applied) atomicAdd(c + 1, (unsigned long long)applied);
-    if (clamped) atomicAdd(c + 2, (unsigned long long)clamped);
-    if (skipped) atomicAdd(c + 3, (unsigned long long)skipped);
-  }
+  events_block_smem<NA>(a, blockIdx.x, smem);
 }
 
 }  // namespace
+
+cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st) {
+  if (n_age == 1) k_events_day<1><<<a.R, 512, 0, st>>>(a);
+  else k_events_day<3><<<a.R, 512, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_events_day_smem(const EvSmemArgs& a, int n_age, cudaStream_t st) {
   static bool attr_set[2] = {false, false};

@@ -3,6 +3,7 @@
 // the ordering rule 2(b) of Sec. 3.6, applied per node), device memory, and the
 // per-day launch sequence (Alg. 1: stochastic step, events, phi update).
 #include "../../include/episim.h"
+#include "batch.h"
 #include "internal.h"
 #include "softdiv.cuh"
 
@@ -53,6 +54,7 @@ struct sim_handle {
   int32_t* d_touched = nullptr;
   int32_t* d_day_touch = nullptr;
   std::vector<int32_t> day_smem;     // shared-memory bytes of the staged event step per day (0: global variant)
+  int32_t* d_day_smem = nullptr;     // device copy for the persistent batch kernel
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
   std::vector<int32_t> sched_level;
   std::vector<int32_t> day_lvl;      // [max_days + 1]
@@ -100,7 +102,8 @@ cudaError_t dalloc(T** p, size_t n) {
 
 void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
-  cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch);
+  cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
+  h->d_day_smem = nullptr;
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
   h->d_rec_slot = nullptr; h->d_touched = nullptr; h->d_day_touch = nullptr;
   h->sched_order.clear(); h->sched_level.clear(); h->day_lvl.clear(); h->day_smem.clear();
@@ -489,6 +492,11 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
     const size_t b = events_smem_bytes(ne, nl, nt, h->nc);
     h->day_smem[(size_t)d] = (b <= kEventsSmemLimit && !h->force_global_events) ? (int32_t)b : 0;
   }
+  {
+    cudaError_t e2 = dalloc(&h->d_day_smem, (size_t)T);
+    if (e2 == cudaSuccess && T > 0) e2 = cudaMemcpy(h->d_day_smem, h->day_smem.data(), (size_t)T * 4, cudaMemcpyHostToDevice);
+    if (e2 != cudaSuccess) { free_events(h); return cuda_fail(h, e2, "event upload"); }
+  }
   h->sched_order.swap(S.order);
   h->sched_level.swap(S.level);
   h->day_lvl.swap(S.day_lvl);
@@ -681,7 +689,177 @@ sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only) {
   h->force_global_events = global_only != 0;
   for (size_t d = 0; d < h->day_smem.size(); ++d)
     if (h->force_global_events) h->day_smem[d] = 0;
+  if (h->d_day_smem && !h->day_smem.empty())
+    CK(h, cudaMemcpy(h->d_day_smem, h->day_smem.data(), h->day_smem.size() * 4, cudaMemcpyHostToDevice), "upload");
   return SIM_OK;
+}
+
+namespace {
+long long g_batch_spin_limit = 5000000;   // ~2 s of polling per wait
+bool g_batch_stall = false;               // test switch, see sim_debug_batch_stall
+}
+
+sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void* stream) {
+  if (n < 0 || (n > 0 && !hs)) return fail(nullptr, SIM_E_INVALID_ARG, "bad handle list");
+  if (n == 0) return SIM_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(nullptr, SIM_E_INVALID_ARG, "handle %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(nullptr, SIM_E_INVALID_ARG, "handle %d listed twice", i);
+    const int32_t u = until ? until[i] : hs[i]->cfg.max_days;
+    if (u < hs[i]->day || u > hs[i]->cfg.max_days)
+      return fail(hs[i], SIM_E_INVALID_ARG, "until day %d outside [day %d, max_days %d]", u, hs[i]->day, hs[i]->cfg.max_days);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // instances with days to run, longest horizon first
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i) {
+    const int32_t u = until ? until[i] : hs[i]->cfg.max_days;
+    if (u > hs[i]->day) idx.push_back(i);
+  }
+  if (idx.empty()) return SIM_OK;
+  auto nd = [&](int i) { return (until ? until[i] : hs[i]->cfg.max_days) - hs[i]->day; };
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return nd(a) > nd(b); });
+  const int ni = (int)idx.size();
+  std::vector<BatchInst> inst(ni);
+  std::vector<long long> cumA(ni + 1, 0), cumB(ni + 1, 0), cumF(ni + 1, 0);
+  long long n_counters = 0;
+  int smem_cap = 0;
+  const int wpb = kBatchThreads / 32;
+  for (int k = 0; k < ni; ++k) {
+    sim_handle* h = hs[idx[k]];
+    BatchInst& I = inst[k];
+    std::memset(&I, 0, sizeof I);
+    I.ssa = ssa_args(h);
+    I.ssa.warp_blocks = (h->n_big + wpb - 1) / wpb;
+    I.na = h->n_age;
+    I.score = (h->cfg.flags & SIM_FLAG_SCORE) ? 1 : 0;
+    if (I.score) { I.ssa.n_big = 0; I.ssa.warp_blocks = 0; }
+    const int n_thread = h->cfg.n_nodes - I.ssa.n_big;
+    I.bpr = I.ssa.warp_blocks + (n_thread + kBatchThreads - 1) / kBatchThreads;
+    I.tbpr = (h->cfg.n_nodes + kBatchThreads - 1) / kBatchThreads;
+    I.day0 = h->day;
+    I.ndays = nd(idx[k]);
+    I.has_events = h->events_loaded ? 1 : 0;
+    I.day_smem = h->d_day_smem;
+    EvArgs& ev = I.evg;
+    ev.counts = h->d_counts; ev.rec = h->d_rec; ev.lvl_start = h->d_lvl_start; ev.day_lvl = h->d_day_lvl;
+    ev.ctr = h->d_ctr; ev.err = h->d_err; ev.seed = h->cfg.seed; ev.rep_base = h->cfg.replicate_base;
+    ev.N = h->cfg.n_nodes; ev.R = h->cfg.n_replicates; ev.Nc = h->nc;
+    ev.underflow_error = h->cfg.underflow_policy == SIM_UNDERFLOW_ERROR;
+    EvSmemArgs& es = I.evs;
+    es.counts = h->d_counts; es.rec = h->d_rec_slot; es.lvl_start = h->d_lvl_start; es.day_lvl = h->d_day_lvl;
+    es.touched = h->d_touched; es.day_touch = h->d_day_touch; es.ctr = h->d_ctr; es.err = h->d_err;
+    es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
+    es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
+    if (h->events_loaded)
+      for (int32_t d = I.day0; d < I.day0 + I.ndays; ++d) smem_cap = std::max(smem_cap, h->day_smem[(size_t)d]);
+    const long long R = h->cfg.n_replicates;
+    cumA[k + 1] = cumA[k] + R * I.bpr;
+    cumB[k + 1] = cumB[k] + R;
+    cumF[k + 1] = cumF[k] + R * I.tbpr;
+    n_counters += 2 * R;
+  }
+  const int S = inst[0].ndays;
+  std::vector<int32_t> active(S);
+  std::vector<long long> step_off(S + 1, 0);
+  for (int s = 0, a = ni; s < S; ++s) {
+    while (a > 0 && inst[a - 1].ndays <= s) --a;
+    active[s] = a;
+    step_off[s + 1] = step_off[s] + cumA[a] + cumB[a];
+  }
+  // workspace: counters, control words, descriptors and tables (freed below)
+  const size_t bytes_inst = sizeof(BatchInst) * ni;
+  const size_t bytes_tab = sizeof(long long) * (3 * (ni + 1) + S + 1) + sizeof(int32_t) * S;
+  const size_t bytes_ctr = sizeof(unsigned) * n_counters + 64;
+  unsigned char* ws = nullptr;
+  CK(nullptr, cudaMalloc(&ws, bytes_inst + bytes_tab + bytes_ctr + 256), "batch workspace");
+  unsigned char* p = ws;
+  BatchInst* d_inst = (BatchInst*)p; p += (bytes_inst + 15) / 16 * 16;
+  long long* d_cumA = (long long*)p; p += 8 * (ni + 1);
+  long long* d_cumB = (long long*)p; p += 8 * (ni + 1);
+  long long* d_cumF = (long long*)p; p += 8 * (ni + 1);
+  long long* d_step = (long long*)p; p += 8 * (S + 1);
+  int32_t* d_active = (int32_t*)p; p += 4 * S;
+  p = (unsigned char*)(((uintptr_t)p + 15) / 16 * 16);
+  unsigned long long* d_next = (unsigned long long*)p; p += 8;
+  int* d_abort = (int*)p; p += 4;
+  int* d_err = (int*)p; p += 4;
+  unsigned* d_ctr = (unsigned*)p;
+  {
+    unsigned* c = d_ctr;
+    std::vector<unsigned> init((size_t)n_counters);
+    size_t o = 0;
+    for (int k = 0; k < ni; ++k) {
+      const int R = inst[k].ssa.R;
+      inst[k].ssa_done = c + o;
+      for (int r = 0; r < R; ++r) init[o++] = 0;
+      inst[k].ev_done = c + o;
+      for (int r = 0; r < R; ++r) init[o++] = (unsigned)inst[k].day0;
+      if (g_batch_stall && k == 0) init[o - R] = 0;   // replicate 0 waits for a day that never comes
+    }
+    cudaError_t e = cudaMemcpyAsync(d_ctr, init.data(), init.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_inst, inst.data(), bytes_inst, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cumA, cumA.data(), 8 * (ni + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cumB, cumB.data(), 8 * (ni + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cumF, cumF.data(), 8 * (ni + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_step, step_off.data(), 8 * (S + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_active, active.data(), 4 * S, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, 16, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host vectors go out of scope
+    if (e != cudaSuccess) { cudaFree(ws); return cuda_fail(nullptr, e, "batch upload"); }
+  }
+  BatchCtl c{};
+  c.inst = d_inst; c.cumA = d_cumA; c.cumB = d_cumB; c.cumF = d_cumF; c.step_off = d_step; c.active = d_active;
+  c.next = d_next; c.abort = d_abort; c.err = d_err;
+  c.total_main = step_off[S];
+  c.total = c.total_main + cumF[ni];
+  c.spin_limit = g_batch_spin_limit;
+  c.n_inst = ni; c.n_steps = S;
+  c.smem_cap = smem_cap;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaError_t e = batch_occupancy(smem_cap, &per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  const long long want = (long long)sms * per_sm;
+  const int grid = (int)std::max(1LL, std::min(want, c.total));
+  if (e == cudaSuccess) e = launch_batch(c, grid, st);
+  int berr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&berr, d_err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ws);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch kernel");
+  for (int k = 0; k < ni; ++k) hs[idx[k]]->day = inst[k].day0 + inst[k].ndays;
+  if (berr & kBatchTimeout) {
+    for (int k = 0; k < ni; ++k) fail(hs[idx[k]], SIM_E_TIMEOUT, "a batch dependency wait ran out");
+    return fail(nullptr, SIM_E_TIMEOUT, "a batch dependency wait ran out (state of the batch is undefined)");
+  }
+  return SIM_OK;
+}
+
+sim_status sim_debug_batch_spin_limit(int64_t limit) {
+  if (limit < 1) return SIM_E_INVALID_ARG;
+  g_batch_spin_limit = limit;
+  return SIM_OK;
+}
+
+sim_status sim_debug_batch_stall(sim_handle* h, int32_t until, int64_t spin_limit) {
+  // A batch run whose first dependency can never be met: replicate 0's event
+  // counter starts at 0 while the run starts at day >= 1, so its first chunk
+  // waits for event steps that are never scheduled.  The bounded wait must run
+  // out, abort the launch and report SIM_E_TIMEOUT; the device stays usable.
+  if (!h || h->day < 1 || until <= h->day || spin_limit < 1) return SIM_E_INVALID_ARG;
+  const long long saved = g_batch_spin_limit;
+  g_batch_spin_limit = spin_limit;
+  g_batch_stall = true;
+  const int32_t d0 = h->day;
+  sim_handle* one[1] = {h};
+  sim_status s = sim_run_batch(one, 1, &until, nullptr);
+  g_batch_spin_limit = saved;
+  g_batch_stall = false;
+  h->day = d0;
+  return s;
 }
 
 sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold) {

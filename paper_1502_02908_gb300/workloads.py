@@ -272,3 +272,39 @@ def tiny_node(model=SISE, herd=10, infected=1, R=1, copies=1, **kw):
     phi0 = np.full(copies, float(kw.pop("phi0", 0.0)))
     return Workload("tiny", model, copies, kw.pop("T", 1), R, u0, phi0, params,
                     Events.empty(), kw.pop("seed", 1))
+
+
+def latin_hypercube(rng, n, lo, hi):
+    """n points, one per stratum in every dimension, uniform within strata."""
+    lo = np.asarray(lo, float); hi = np.asarray(hi, float)
+    d = lo.size
+    u = (np.stack([rng.permutation(n) for _ in range(d)], 1) + rng.random((n, d))) / n
+    return lo + u * (hi - lo)
+
+
+def uneven_batch(n_inst=512, N_lo=100, N_hi=50_000, T_lo=90, T_hi=1460, events_per_node_year=80,
+                 seed=5, R=1):
+    """Instances mixing SISe and SISe3 (probability 1/2 each), node counts
+    log-uniform in [N_lo, N_hi], horizons uniform in [T_lo, T_hi], events at
+    `events_per_node_year` with the plain SISe type mix (exit/enter/external
+    50/30/20 %, no aging), and parameters from an n_inst-point Latin hypercube over
+    log(upsilon, gamma, beta, alpha) in [0.5, 1.5] x (0.0357, 0.1, 0.005, 1.0).
+    SISe3 instances use one (upsilon, gamma) for the three age classes.  Herds are
+    U{20..200}, 5% infected (SISe3: split 20/20/60 by age)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = np.log([0.0357, 0.1, 0.005, 1.0])
+    lhs = np.exp(latin_hypercube(rng, n_inst, base + np.log(0.5), base + np.log(1.5)))
+    out = []
+    for i in range(n_inst):
+        model = SISE if rng.random() < 0.5 else SISE3
+        N = int(round(math.exp(rng.uniform(math.log(N_lo), math.log(N_hi)))))
+        T = int(rng.integers(T_lo, T_hi + 1))
+        herd = rng.integers(20, 201, size=N)
+        u0 = _initial_counts(model, herd)
+        n_ev = int(round(events_per_node_year * N * T / 365))
+        ev = _uniform_events(rng, N, T, n_ev, (0.5, 0.3, 0.2)) if n_ev else Events.empty()
+        ups, gam, bet, alp = lhs[i]
+        params = Params.broadcast(R, [ups] * (3 if model == SISE3 else 1), [gam] * (3 if model == SISE3 else 1),
+                                  alp, bet, 1e-6)
+        out.append(Workload(f"uneven_{i}", model, N, T, R, u0, np.zeros(N), params, ev, seed=1000 + i))
+    return out

@@ -1,0 +1,86 @@
+"""The persistent work-stealing batch kernel: results identical to running each
+simulation alone (and to the oracle), score mode inside a batch, and the failure
+path of its bounded dependency waits."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02908_gb300 import binding as B
+from paper_1502_02908_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load_library()
+
+
+def _state(s):
+    c, p, d = s.state()
+    pi, pn, ctr = s.stats()
+    return c, p, d, pi, pn, ctr
+
+
+def test_uneven_batch_equals_individual_runs_and_oracle():
+    ws = W.uneven_batch(n_inst=12, N_lo=50, N_hi=3000, T_lo=20, T_hi=120, seed=7)
+    ws[0].R = 3
+    ws[0].params = W.Params.broadcast(3, ws[0].params.upsilon[0, :1], ws[0].params.gamma[0, :1],
+                                      ws[0].params.alpha[0], ws[0].params.beta[0, 0], 1e-6)
+    batch = [B.Sim.from_workload(w) for w in ws]
+    batch[1].tune(0)                               # one instance on the warp-per-node path
+    B.run_batch(batch)
+    for w, s in zip(ws, batch):
+        alone = B.Sim.from_workload(w)
+        alone.run(w.T)
+        a, b = _state(s), _state(alone)
+        assert b[2] == w.T and a[2] == w.T
+        for x, y in zip(a, b):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), w.name
+        alone.close()
+    for i in (0, 1, 5):
+        ref = oracle.run(ws[i])
+        c, p, _, pi, pn, ctr = _state(batch[i])
+        assert np.array_equal(c, ref.counts) and np.array_equal(ctr, ref.counters)
+        np.testing.assert_allclose(p, ref.phi, rtol=1e-12, atol=0)
+    for s in batch:
+        s.close()
+
+
+def test_batch_partial_horizons_and_resume():
+    ws = W.uneven_batch(n_inst=4, N_lo=100, N_hi=800, T_lo=30, T_hi=60, seed=9)
+    sims = [B.Sim.from_workload(w) for w in ws]
+    B.run_batch(sims, until=[10, 0, 17, 5])
+    B.run_batch(sims)                              # the rest of every horizon
+    for w, s in zip(ws, sims):
+        ref = oracle.run(w)
+        c, p, d = s.state()
+        assert d == w.T and np.array_equal(c, ref.counts)
+        s.close()
+
+
+def test_batch_with_score_mode_matches_plain_run():
+    w = W.sise_plain(N=300, T=40, n_events=3000, R=4)
+    a = B.Sim.from_workload(w, score=True)
+    b = B.Sim.from_workload(w, score=True)
+    B.run_batch([a])
+    b.run(w.T)
+    assert np.array_equal(a.score(), b.score())
+    assert np.array_equal(a.state()[0], b.state()[0])
+    a.close(); b.close()
+
+
+def test_batch_wait_runs_out_and_reports_timeout():
+    w = W.sise_plain(N=200, T=20, n_events=1000)
+    s = B.Sim.from_workload(w)
+    s.run(1)
+    st = s.L.sim_debug_batch_stall(s.h, 5, 20_000)
+    assert st == B.SIM_E_TIMEOUT
+    # the context is still usable: a fresh run matches the oracle
+    t = B.Sim.from_workload(w)
+    t.run(w.T)
+    assert np.array_equal(t.state()[0], oracle.run(w).counts)
+    s.close(); t.close()
