@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--days", type=int, default=1460)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -115,6 +117,37 @@ def oracle_baseline(w, days, note):
             "seconds": dt, "events_per_s": ev / dt}, r
 
 
+def batched_leg(args, B, W, torch, plain_value):
+    """The same national network batched: 256 replicates x 365 days, each with its
+    own (upsilon, gamma), in one handle; launch mode chosen by a short autotune."""
+    from paper_1502_02908_gb300 import autotune
+    w = W.sise3_batched(R=256, T=365)
+    best, _ = autotune.autotune(w, days=20, thresholds=(1 << 30,), modes=("stream", "graph", "persistent"),
+                                repeats=1)
+    sim = B.Sim.from_workload(w)
+    sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
+    u0 = np.repeat(w.u0[None], w.R, 0); phi0 = np.repeat(w.phi0[None], w.R, 0)
+    steps, warm = 2, 1
+    times = []
+    for i in range(warm + steps):
+        sim.set_state(u0, phi0, 0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); sim.run(w.T); e1.record()
+        torch.cuda.synchronize()
+        if i >= warm:
+            times.append(e0.elapsed_time(e1))
+    _, _, ctr = sim.stats()
+    sim.close()
+    ms = sum(times) / len(times)
+    value = w.N * w.R * w.T / (ms / 1000)
+    trans = int(ctr[:, 0].sum()) // (warm + steps)
+    evs = int(ctr[:, 1].sum()) // (warm + steps)
+    return {"workload": f"SISe3 national network, {w.R} replicates x {w.T} days, own (upsilon, gamma) each",
+            "value": value, "unit": "node-days/s", "steps": steps, "warmup": warm, "ms_per_step": ms,
+            "events_per_s": (trans + evs) / (ms / 1000), "launch": best, "vs_plain": value / plain_value}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
@@ -166,10 +199,17 @@ def main():
     build()
     w = W.sise3_national()
     w.T = min(args.days, w.T)        # a shorter horizon of the same instance
+    tuned = {"warp_threshold": -1, "launch": "graph"}
+    if not args.no_tune:
+        from paper_1502_02908_gb300 import autotune
+        tuned, _ = autotune.autotune(w, days=max(10, w.T // 10), thresholds=(1 << 30, 800, 400, 200),
+                                     modes=("stream", "graph"), repeats=1)
     sim = B.Sim(w.model, w.u0, w.phi0, w.params, w.T, seed=w.seed, replicate_base=rank)
     t0 = time.perf_counter()
     sim.load_events(w.events)
     preprocess_s = time.perf_counter() - t0
+    sim.tune(tuned["warp_threshold"])
+    sim.set_launch(tuned["launch"])
     stream = torch.cuda.current_stream()
     R, N, T = 1, w.N, w.T
     u0_all = np.repeat(w.u0[None], R, 0)
@@ -260,6 +300,9 @@ def main():
             "preprocess_s": preprocess_s, "e2e": e2e, "roofline": roofline,
             "gpu_launches": (ssa_n + ev_n + fin_n) * args.steps, "clocks": clk.summary()}
 
+    line["config"]["launch"] = tuned
+    if not args.no_batched:
+        line["batched"] = batched_leg(args, B, W, torch, value)
     if rank == 0 and not args.no_cpu_baseline:
         days = min(365, T)
         base, ref = oracle_baseline(w, days, "national SISe3")

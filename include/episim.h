@@ -219,6 +219,17 @@ sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold);
 /* Number of nodes currently simulated one per warp (-1 for a NULL handle). */
 int32_t sim_warp_nodes(const sim_handle* h);
 
+/* Execution options (results never depend on them):
+ *   SIM_OPT_WARP_THRESHOLD: as sim_tune.
+ *   SIM_OPT_LAUNCH: how sim_run_days issues a call's days -- SIM_LAUNCH_STREAM
+ *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
+ *     sequence captured once as a CUDA graph, keyed by start day and day count,
+ *     and replayed), SIM_LAUNCH_PERSISTENT (one persistent batch-kernel launch,
+ *     synchronous).  Tracing (sim_profile) always uses stream launches. */
+enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2 };
+enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
+sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
+
 /* Batched and uneven runs: advances every listed handle (all on the current
  * device; any mix of models, node and replicate counts, horizons, events and
  * parameters) to day until[i] (NULL: each handle's max_days) in ONE persistent

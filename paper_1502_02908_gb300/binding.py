@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
             "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
             "sim_run_batch": [P(vp), i32, pi32, vp],
+            "sim_set_option": [vp, i32, i64],
             "sim_debug_batch_spin_limit": [i64],
             "sim_debug_batch_stall": [vp, i32, i64],
             "sim_profile_read": [vp, pd, pi64],
@@ -254,6 +255,11 @@ class Sim:
     def tune(self, warp_herd_threshold=-1):
         _check(self.L, self.h, self.L.sim_tune(self.h, int(warp_herd_threshold)))
         return self.L.sim_warp_nodes(self.h)
+
+    LAUNCH = {"stream": 0, "graph": 1, "persistent": 2}
+
+    def set_launch(self, mode):
+        _check(self.L, self.h, self.L.sim_set_option(self.h, 2, self.LAUNCH[mode]))
 
     def profile(self, enable=True):
         _check(self.L, self.h, self.L.sim_profile(self.h, 1 if enable else 0))

@@ -60,6 +60,10 @@ struct sim_handle {
   std::vector<int32_t> day_lvl;      // [max_days + 1]
   int32_t day = 0;
   std::string err;
+  // launch mode of sim_run_days: 0 stream, 1 CUDA graph, 2 persistent batch kernel
+  int32_t launch_mode = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  int32_t graph_d0 = -1, graph_nd = -1;
   // tracing
   bool profiling = false;
   bool force_global_events = false;  // test switch: always use the global-memory event step
@@ -115,7 +119,14 @@ void free_profile(sim_handle* h) {
   h->ev_pool.clear(); h->ev_kind.clear(); h->ev_used = 0;
 }
 
+void free_graph(sim_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  h->graph_d0 = h->graph_nd = -1;
+}
+
 void free_all(sim_handle* h) {
+  free_graph(h);
   free_profile(h);
   free_events(h);
   cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
@@ -199,6 +210,7 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_big = nb;
   h->warp_threshold = threshold;
+  free_graph(h);
   return SIM_OK;
 }
 
@@ -501,6 +513,7 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   h->sched_level.swap(S.level);
   h->day_lvl.swap(S.day_lvl);
   h->events_loaded = true;
+  free_graph(h);
   return SIM_OK;
 }
 
@@ -524,12 +537,8 @@ sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days,
 
 extern "C" {
 
-sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
-  if (!h) return SIM_E_INVALID_ARG;
-  if (ndays < 0 || (int64_t)h->day + ndays > h->cfg.max_days)
-    return fail(h, SIM_E_INVALID_ARG, "ndays %d from day %d passes max_days %d", ndays, h->day, h->cfg.max_days);
-  if (ndays == 0) return SIM_OK;
-  cudaStream_t st = (cudaStream_t)stream;
+// Enqueues the launches of days [d0, d0 + ndays) on st (no state change).
+static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStream_t st) {
   const bool score = (h->cfg.flags & SIM_FLAG_SCORE) != 0;
   SsaArgs a = ssa_args(h);
   EvArgs ev{};
@@ -542,7 +551,6 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   es.touched = h->d_touched; es.day_touch = h->d_day_touch; es.ctr = h->d_ctr; es.err = h->d_err;
   es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
   es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
-  const int32_t d0 = h->day;
   for (int32_t d = d0; d < d0 + ndays; ++d) {
     a.day = d;
     a.prologue = d > d0;
@@ -560,6 +568,49 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   }
   a.day = d0 + ndays - 1;
   CK(h, traced(h, 2, st, [&] { return launch_finalize(a, h->n_age, score, st); }), "phi update launch");
+  return SIM_OK;
+}
+
+sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (ndays < 0 || (int64_t)h->day + ndays > h->cfg.max_days)
+    return fail(h, SIM_E_INVALID_ARG, "ndays %d from day %d passes max_days %d", ndays, h->day, h->cfg.max_days);
+  if (ndays == 0) return SIM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t d0 = h->day;
+  if (h->launch_mode == 2 && !h->profiling) {
+    const int32_t until = d0 + ndays;
+    sim_handle* one[1] = {h};
+    sim_status s = sim_run_batch(one, 1, &until, stream);
+    if (s != SIM_OK) return fail(h, s, "%s", sim_last_error(nullptr));
+    return SIM_OK;
+  }
+  if (h->launch_mode == 1 && !h->profiling) {
+    if (!h->graph_exec || h->graph_d0 != d0 || h->graph_nd != ndays) {
+      free_graph(h);
+      // capture on a private stream so that the caller's stream may be the legacy default stream
+      cudaStream_t cs;
+      CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      sim_status s = SIM_OK;
+      if (e == cudaSuccess) s = enqueue_days(h, d0, ndays, cs);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess && s == SIM_OK) e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (s != SIM_OK) return s;
+      if (e != cudaSuccess) { h->graph_exec = nullptr; return cuda_fail(h, e, "daily-loop graph capture"); }
+      h->graph_d0 = d0;
+      h->graph_nd = ndays;
+    }
+    CK(h, cudaGraphLaunch(h->graph_exec, st), "daily-loop graph launch");
+    h->day = d0 + ndays;
+    return SIM_OK;
+  }
+  sim_status s = enqueue_days(h, d0, ndays, st);
+  if (s != SIM_OK) return s;
   h->day = d0 + ndays;
   return SIM_OK;
 }
@@ -673,7 +724,7 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
 sim_status sim_reset(sim_handle* h, int32_t clear_events) {
   if (!h) return SIM_E_INVALID_ARG;
   CK(h, cudaDeviceSynchronize(), "synchronize");
-  if (clear_events) free_events(h);
+  if (clear_events) { free_events(h); free_graph(h); }
   return reset_state(h);
 }
 
@@ -869,6 +920,23 @@ sim_status sim_tune(sim_handle* h, int32_t warp_herd_threshold) {
 }
 
 int32_t sim_warp_nodes(const sim_handle* h) { return h ? h->n_big : -1; }
+
+sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
+  if (!h) return SIM_E_INVALID_ARG;
+  switch (option) {
+    case SIM_OPT_WARP_THRESHOLD:
+      return sim_tune(h, (int32_t)std::max<int64_t>(-1, std::min<int64_t>(value, 1 << 30)));
+    case SIM_OPT_LAUNCH:
+      if (value < SIM_LAUNCH_STREAM || value > SIM_LAUNCH_PERSISTENT)
+        return fail(h, SIM_E_INVALID_ARG, "unknown launch mode %lld", (long long)value);
+      CK(h, cudaDeviceSynchronize(), "synchronize");
+      free_graph(h);
+      h->launch_mode = (int32_t)value;
+      return SIM_OK;
+    default:
+      return fail(h, SIM_E_INVALID_ARG, "unknown option %d", option);
+  }
+}
 
 sim_status sim_profile(sim_handle* h, int32_t enable) {
   if (!h) return SIM_E_INVALID_ARG;

@@ -84,3 +84,29 @@ def test_batch_wait_runs_out_and_reports_timeout():
     t.run(w.T)
     assert np.array_equal(t.state()[0], oracle.run(w).counts)
     s.close(); t.close()
+
+
+def test_graph_and_persistent_launch_modes_match_stream_launches():
+    w = W.sise3_national(N=3000, T=40, n_events=60_000)
+    out = {}
+    for mode in ("stream", "graph", "persistent"):
+        s = B.Sim.from_workload(w)
+        s.set_launch(mode)
+        s.run(15); s.run(25)                       # two calls: two graphs / two batch launches
+        out[mode] = _state(s)
+        s.reset()                                  # replaying a cached graph after a reset
+        s.run(15); s.run(25)
+        again = _state(s)
+        for x, y in zip(out[mode], again):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+        s.close()
+    for mode in ("graph", "persistent"):
+        for x, y in zip(out[mode], out["stream"]):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), mode
+
+
+def test_autotuner_keeps_results_and_picks_a_setting():
+    from paper_1502_02908_gb300 import autotune
+    w = W.sise3_national(N=2000, T=30, n_events=40_000)
+    best, table = autotune.autotune(w, days=20, thresholds=(1 << 30, 200), repeats=1)
+    assert len(table) == 6 and best["launch"] in autotune.LAUNCH_MODES
