@@ -276,11 +276,13 @@ sim_status sim_debug_div(const double* x, const double* y, double* out, double* 
  * (day, then dependency level, then position), and the level of each listed
  * event (int32 [n]).  Either output may be NULL. */
 sim_status sim_debug_schedule(const sim_handle* h, int64_t* order, int32_t* level);
-/* Test hook: global_only = 1 makes the handle apply events with the
- * global-memory event kernel on every day (call before sim_load_events);
- * 0 (default) uses the shared-memory staged kernel on days whose working set
- * fits in shared memory.  Both give identical results. */
-sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only);
+/* Test hook choosing the event-step kernel (call before sim_load_events):
+ * 0 (default) the owner-computes kernel (each node's events applied in input
+ * order by the thread that owns the node, with counter waits for transfers) on
+ * days whose working set fits in shared memory, else the level-staged kernel,
+ * else the global-memory kernel; 1 the global-memory level kernel on every day;
+ * 2 the level kernels only.  All give identical results. */
+sim_status sim_debug_event_variant(sim_handle* h, int32_t variant);
 
 /* Number of entries sim_debug_schedule writes (-1 for a NULL handle). */
 int64_t sim_debug_schedule_size(const sim_handle* h);

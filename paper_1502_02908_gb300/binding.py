@@ -170,10 +170,12 @@ class Sim:
         self.h = h
 
     @classmethod
-    def from_workload(cls, w: W.Workload, events=True, max_days=None, global_events=False, **kw):
+    def from_workload(cls, w: W.Workload, events=True, max_days=None, global_events=False, event_variant=None, **kw):
         s = cls(w.model, w.u0, w.phi0, w.params, w.T if max_days is None else max_days, seed=w.seed, **kw)
         if global_events:
             _check(s.L, s.h, s.L.sim_debug_event_variant(s.h, 1))
+        if event_variant is not None:
+            _check(s.L, s.h, s.L.sim_debug_event_variant(s.h, int(event_variant)))
         if events and len(w.events):
             s.load_events(w.events)
         return s

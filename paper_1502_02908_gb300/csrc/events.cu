@@ -16,12 +16,38 @@ __global__ void __launch_bounds__(512) k_events_day(EvArgs a) {
 }
 
 template <int NA>
+__global__ void __launch_bounds__(kDfThreads, 1) k_events_day_df(EvDfArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  events_block_dataflow<NA>(a, blockIdx.x, smem);
+}
+
+template <int NA>
 __global__ void __launch_bounds__(512, 1) k_events_day_smem(EvSmemArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   events_block_smem<NA>(a, blockIdx.x, smem);
 }
 
 }  // namespace
+
+size_t events_df_smem_bytes(int64_t n_events, int64_t n_touched, int nc) {
+  if (n_events == 0) return 0;
+  return (size_t)n_events * 64 + (size_t)n_touched * (nc + 2) * 4 + (size_t)(kDfThreads + 2) * 4 + 16;
+}
+
+cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st) {
+  static bool attr_set[2] = {false, false};
+  const int which = n_age == 1 ? 0 : 1;
+  if (!attr_set[which]) {
+    cudaError_t e = n_age == 1
+        ? cudaFuncSetAttribute(k_events_day_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEventsSmemLimit)
+        : cudaFuncSetAttribute(k_events_day_df<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEventsSmemLimit);
+    if (e != cudaSuccess) return e;
+    attr_set[which] = true;
+  }
+  if (n_age == 1) k_events_day_df<1><<<a.R, kDfThreads, a.smem_bytes, st>>>(a);
+  else k_events_day_df<3><<<a.R, kDfThreads, a.smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st) {
   if (n_age == 1) k_events_day<1><<<a.R, 512, 0, st>>>(a);

@@ -155,10 +155,40 @@ __device__ __forceinline__ void add_count(int32_t* p, int32_t v) {
   if (ATOMIC) atomicAdd(p, v); else *p += v;
 }
 
+// The k-th 32-bit word of an event's stream when no draw before k was rejected.
+__device__ __forceinline__ uint32_t word_k(const Words8& w, int k) {
+  const uint4 v = k < 4 ? w.a : w.b;
+  const int j = k & 3;
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Draw slots one at a time.  Draw k uses word k and range avail - k while no
+// earlier draw was rejected (one word per draw, so the stream position is k);
+// the first draw that Lemire's method might reject (low product word below the
+// range) and every draw after it go through the exact word stream from position
+// k on, rejections included.  Same slots as the sequential definition.
+struct DrawState {
+  EventWords ws;
+  bool exact;
+};
+
+__device__ __forceinline__ uint32_t draw_slot(DrawState& st, int k, uint32_t range) {
+  if (!st.exact && k < 8) {
+    const uint64_t m = (uint64_t)word_k(st.ws.w, k) * range;
+    if ((uint32_t)m >= range) return (uint32_t)(m >> 32);
+    st.exact = true;
+    st.ws.q = (uint32_t)k;
+  } else if (!st.exact) {
+    st.exact = true;
+    st.ws.q = (uint32_t)k;
+  }
+  return lemire(range, st.ws);
+}
+
 template <int NA, bool ATOMIC>
-__device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* cnt, uint32_t rep, int4 rec,
-                                                 const Words8& w8, unsigned& applied, unsigned& clamped,
-                                                 unsigned& skipped) {
+__device__ __forceinline__ void apply_event_smem(int underflow_error, int32_t* err, int day, uint64_t seed,
+                                                 int32_t* cnt, uint32_t rep, int4 rec, const Words8& w8,
+                                                 unsigned& applied, unsigned& clamped, unsigned& skipped) {
   constexpr int NC = 2 * NA;
   const int src = rec.x, dst = rec.y;
   const int kind = rec.w & 3;
@@ -170,16 +200,17 @@ __device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* c
     ++applied;
     return;
   }
-  EventWords ws;
-  ws.w = w8; ws.q = 0; ws.e = (uint32_t)rec.z; ws.day = (uint32_t)a.day; ws.rep = rep;
-  ws.k0 = (uint32_t)a.seed; ws.k1 = (uint32_t)(a.seed >> 32);
+  DrawState st;
+  st.ws.w = w8; st.ws.q = 0; st.ws.e = (uint32_t)rec.z; st.ws.day = (uint32_t)day; st.ws.rep = rep;
+  st.ws.k0 = (uint32_t)seed; st.ws.k1 = (uint32_t)(seed >> 32);
+  st.exact = false;
   if (cls >= 0) {
     // one class: draws pick S or I
     const int32_t s0 = cs[2 * cls], s1 = cs[2 * cls + 1];
     const int32_t avail = s0 + s1;
     int32_t take = n;
     if (n > avail) {
-      if (a.underflow_error) { ++skipped; atomicOr(a.err, 1); return; }
+      if (underflow_error) { ++skipped; atomicOr(err, 1); return; }
       take = avail;
       ++clamped;
     }
@@ -188,11 +219,12 @@ __device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* c
     else if (s0 == 0) { t0 = 0; t1 = take; }
     else if (s1 == 0) { t0 = take; t1 = 0; }
     else {
-      t0 = 0; t1 = 0;
+      t0 = 0;
       for (int32_t k = 0; k < take; ++k) {
-        const uint32_t slot = lemire((uint32_t)(avail - k), ws);
-        if (slot < (uint32_t)(s0 - t0)) ++t0; else ++t1;
+        const uint32_t sl = draw_slot(st, k, (uint32_t)(avail - k));
+        t0 += (sl < (uint32_t)(s0 - t0)) ? 1 : 0;
       }
+      t1 = take - t0;
     }
     cs[2 * cls] = s0 - t0;
     cs[2 * cls + 1] = s1 - t1;
@@ -218,7 +250,7 @@ __device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* c
   }
   int32_t take = n;
   if (n > avail) {
-    if (a.underflow_error) { ++skipped; atomicOr(a.err, 1); return; }
+    if (underflow_error) { ++skipped; atomicOr(err, 1); return; }
     take = avail;
     ++clamped;
   }
@@ -235,15 +267,15 @@ __device__ __forceinline__ void apply_event_smem(const EvSmemArgs& a, int32_t* c
 #pragma unroll
     for (int c = 0; c < NC; ++c) { acc += have[c]; cum[c] = acc; took[c] = 0; }
     for (int32_t k = 0; k < take; ++k) {
-      const uint32_t slot = lemire((uint32_t)(avail - k), ws);
+      const uint32_t sl = draw_slot(st, k, (uint32_t)(avail - k));
+      bool below[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) below[c] = sl < (uint32_t)cum[c];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        // compartment c is hit when slot falls in [cum[c-1], cum[c])
-        const bool hit = slot < (uint32_t)cum[c] && (c == 0 || slot >= (uint32_t)cum[c > 0 ? c - 1 : 0]);
-        took[c] += hit ? 1 : 0;
+        took[c] += (below[c] && (c == 0 || !below[c > 0 ? c - 1 : 0])) ? 1 : 0;
+        cum[c] -= below[c] ? 1 : 0;
       }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) cum[c] -= (slot < (uint32_t)cum[c]) ? 1 : 0;
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) cs[c] = have[c] - took[c];
@@ -312,7 +344,7 @@ __device__ __forceinline__ void events_block_smem(const EvSmemArgs& a, int r, un
     const int b = slvl[l], end = slvl[l + 1];
     if (end - b > 32) {
       for (int q = b + (int)threadIdx.x; q < end; q += blockDim.x)
-        apply_event_smem<NA, true>(a, scnt, rep, srec[q], swords[q], applied, clamped, skipped);
+        apply_event_smem<NA, true>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, srec[q], swords[q], applied, clamped, skipped);
       __syncthreads();
       ++l;
       continue;
@@ -332,7 +364,7 @@ __device__ __forceinline__ void events_block_smem(const EvSmemArgs& a, int r, un
         int4 nrc = make_int4(0, 0, 0, 0);
         Words8 nwd;
         if (nb + lane < ne) { nrc = srec[nb + lane]; nwd = swords[nb + lane]; }
-        if (bb + lane < ee) apply_event_smem<NA, true>(a, scnt, rep, rc, wd, applied, clamped, skipped);
+        if (bb + lane < ee) apply_event_smem<NA, true>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rc, wd, applied, clamped, skipped);
         __syncwarp();
         bb = nb; ee = ne; rc = nrc; wd = nwd;
       }
@@ -362,5 +394,142 @@ __device__ __forceinline__ void events_block_smem(const EvSmemArgs& a, int r, un
   }
 }
 
+
+// ---- owner-computes variant (no levels): thread t applies, in input order, the
+// events of the nodes it owns.  A sampling of node v first waits until every
+// transfer into v that precedes it in input order has been added (v's add
+// counter); a transfer into w first waits until every sampling of w that precedes
+// it is done (w's sampling counter).  Waits point only to earlier positions and
+// each thread follows input order, so the earliest pending event is always
+// runnable.  Waits are bounded: running out sets an error bit and an abort flag.
+template <int NA>
+__device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, unsigned char* smem) {
+  constexpr int NC = 2 * NA;
+  const uint32_t rep = (uint32_t)(a.rep_base + r);
+  int32_t* X = a.counts + (size_t)r * NC * a.N;
+  const int e0 = a.day_ev[a.day], e1 = a.day_ev[a.day + 1];
+  const int nev = e1 - e0;
+  const int t0 = a.day_touch[a.day], t1 = a.day_touch[a.day + 1];
+  const int nt = t1 - t0;
+  int4* srec = reinterpret_cast<int4*>(smem);
+  Words8* swords = reinterpret_cast<Words8*>(smem + (size_t)nev * 16);
+  int4* swait = reinterpret_cast<int4*>(smem + (size_t)nev * 48);
+  int32_t* scnt = reinterpret_cast<int32_t*>(smem + (size_t)nev * 64);
+  int32_t* sadd = scnt + (size_t)nt * NC;
+  int32_t* ssmp = sadd + nt;
+  int32_t* soff = ssmp + nt;
+  int32_t* sabort = soff + (kDfThreads + 1);
+  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+  for (int i0 = threadIdx.x; i0 < nt; i0 += 4 * blockDim.x) {
+    int v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < nt ? a.touched[t0 + i] : -1;
+    }
+    int32_t x[4][NC];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[u][c] = v[u] >= 0 ? __ldcg(X + (size_t)c * a.N + v[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < nt) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) scnt[i * NC + c] = x[u][c];
+        sadd[i] = 0;
+        ssmp[i] = 0;
+      }
+    }
+  }
+  for (int i0 = threadIdx.x; i0 < nev; i0 += 4 * blockDim.x) {
+    int4 rc[4], wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < nev) { rc[u] = a.rec[e0 + i]; wv[u] = a.wait[e0 + i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < nev) {
+        srec[i] = rc[u];
+        swait[i] = wv[u];
+        const uint4 c0 = make_uint4((uint32_t)rc[u].z, (uint32_t)a.day | kEventTag, 0u, rep);
+        Words8 w;
+        w.a = philox10(c0, k0, k1);
+        w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
+        swords[i] = w;
+      }
+    }
+  }
+  const int32_t* off = a.thr_off + (size_t)a.day * (kDfThreads + 1);
+  for (int i = threadIdx.x; i <= kDfThreads; i += blockDim.x) soff[i] = off[i];
+  if (threadIdx.x == 0) *sabort = 0;
+  __syncthreads();
+  unsigned applied = 0, clamped = 0, skipped = 0;
+  const int q0 = soff[threadIdx.x], q1 = soff[threadIdx.x + 1];
+  int4 rc = make_int4(0, 0, 0, 0), wt = make_int4(0, 0, 0, 0);
+  Words8 wd;
+  if (q0 < q1) { rc = srec[q0]; wt = swait[q0]; wd = swords[q0]; }
+  for (int q = q0; q < q1; ++q) {
+    // next record in flight while this one is applied
+    int4 nrc = rc, nwt = wt;
+    Words8 nwd = wd;
+    if (q + 1 < q1) { nrc = srec[q + 1]; nwt = swait[q + 1]; nwd = swords[q + 1]; }
+    const int kind = rc.w & 3;
+    if (wt.z & kDfAcquire) {
+      bool ok = true;
+      if (wt.x > 0) {                                  // transfers into src before this sampling
+        volatile int32_t* p = sadd + rc.x;
+        for (int it = 0; *p < wt.x; ++it)
+          if (it >= a.spin_limit || *(volatile int32_t*)sabort) { ok = false; break; }
+      }
+      if (ok && wt.y > 0) {                            // samplings of dst before this transfer
+        volatile int32_t* p = ssmp + rc.y;
+        for (int it = 0; *p < wt.y; ++it)
+          if (it >= a.spin_limit || *(volatile int32_t*)sabort) { ok = false; break; }
+      }
+      if (!ok) {
+        if (!*(volatile int32_t*)sabort) atomicOr(a.err, kEventWaitTimeout);
+        *(volatile int32_t*)sabort = 1;
+        break;
+      }
+      __threadfence_block();
+    }
+    apply_event_smem<NA, true>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rc, wd, applied, clamped,
+                               skipped);
+    if (wt.z & (kDfPublishSampling | kDfPublishAdd)) {
+      __threadfence_block();
+      if (wt.z & kDfPublishSampling) *(volatile int32_t*)(ssmp + rc.x) = *(volatile int32_t*)(ssmp + rc.x) + 1;
+      if (wt.z & kDfPublishAdd) atomicAdd(sadd + rc.y, 1);
+    }
+    (void)kind;
+    rc = nrc; wt = nwt; wd = nwd;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    const int v = a.touched[t0 + i];
+    int32_t x[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = scnt[i * NC + c];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) X[(size_t)c * a.N + v] = x[c];
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    applied += __shfl_down_sync(0xffffffffu, applied, o);
+    clamped += __shfl_down_sync(0xffffffffu, clamped, o);
+    skipped += __shfl_down_sync(0xffffffffu, skipped, o);
+  }
+  if (lane == 0) {
+    unsigned long long* c = a.ctr + (size_t)r * 4;
+    if (applied) atomicAdd(c + 1, (unsigned long long)applied);
+    if (clamped) atomicAdd(c + 2, (unsigned long long)clamped);
+    if (skipped) atomicAdd(c + 3, (unsigned long long)skipped);
+  }
+}
 
 }  // namespace episim

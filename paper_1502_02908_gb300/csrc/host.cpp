@@ -54,6 +54,12 @@ struct sim_handle {
   int32_t* d_touched = nullptr;
   int32_t* d_day_touch = nullptr;
   std::vector<int32_t> day_smem;     // shared-memory bytes of the staged event step per day (0: global variant)
+  std::vector<int32_t> day_df;       // shared-memory bytes of the owner-computes step per day (0: not used)
+  int4* d_rec_df = nullptr;
+  int4* d_wait_df = nullptr;
+  int32_t* d_thr_off = nullptr;
+  int32_t* d_day_ev = nullptr;
+  int32_t event_variant = 0;         // 0 auto, 1 global only, 2 levels (no owner-computes)
   int32_t* d_day_smem = nullptr;     // device copy for the persistent batch kernel
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
   std::vector<int32_t> sched_level;
@@ -107,6 +113,9 @@ cudaError_t dalloc(T** p, size_t n) {
 void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
+  cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_day_ev);
+  h->d_rec_df = nullptr; h->d_wait_df = nullptr; h->d_thr_off = nullptr; h->d_day_ev = nullptr;
+  h->day_df.clear();
   h->d_day_smem = nullptr;
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
   h->d_rec_slot = nullptr; h->d_touched = nullptr; h->d_day_touch = nullptr;
@@ -166,6 +175,7 @@ sim_status check_latched(sim_handle* h) {
   CK(h, cudaMemcpy(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost), "read device error word");
   if (e) {
     CK(h, cudaMemset(h->d_err, 0, sizeof(int32_t)), "clear device error word");
+    if (e & kEventWaitTimeout) return fail(h, SIM_E_TIMEOUT, "an event-step dependency wait ran out");
     return fail(h, SIM_E_UNDERFLOW, "an event asked for more animals than present (ERROR policy)");
   }
   return SIM_OK;
@@ -218,6 +228,10 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
 struct Schedule {
   std::vector<int4> rec;          // execution order
   std::vector<int4> rec_slot;     // same, with node slots of the day's touched list
+  // owner-computes form: per day, events grouped by owner thread, input order within
+  std::vector<int4> rec_df;       // {slot_src, slot_dst, position, packed}
+  std::vector<int4> wait_df;      // {transfer-adds into src before it, samplings of dst before it, flags, 0}
+  std::vector<int32_t> thr_off;   // [max_days][kDfThreads + 1] offsets within the day
   std::vector<int32_t> touched;   // node ids per day slot
   std::vector<int32_t> day_touch; // [max_days + 1]
   std::vector<int32_t> lvl_start; // [levels + 1]
@@ -225,6 +239,97 @@ struct Schedule {
   std::vector<int64_t> order;     // day-stable position of each record
   std::vector<int32_t> level;
 };
+
+// Owner-computes form of one day (events at day-stable positions [s0, s1)).
+// Every touched node is owned by one thread, which applies the node's events
+// (enter, exit, aging, transfer out) in input order.  A sampling event waits
+// until every transfer into its node that precedes it has been added; a
+// transfer waits until every sampling of its destination that precedes it is
+// done.  Waits only ever point to earlier input positions, so threads that each
+// follow input order always make progress.  Nodes with many events get a warp of
+// their own (lane 0), so that their chain is not serialised behind other lanes;
+// the others are packed longest-first onto the least-loaded threads.
+void build_owner_form(Schedule& S, int32_t d, int64_t s0, int64_t s1, int32_t touch0,
+                      const std::vector<int64_t>& by_pos, const int32_t* kind, const int32_t* node,
+                      const int32_t* dest, const int32_t* count, const int32_t* cls,
+                      const std::vector<int32_t>& slot_of) {
+  const int nt = (int)S.touched.size() - touch0;
+  const int64_t n = s1 - s0;
+  std::vector<int32_t> evcount(nt, 0), owner(nt, -1);
+  for (int64_t s = s0; s < s1; ++s) evcount[slot_of[node[by_pos[(size_t)s]]]]++;
+  std::vector<int32_t> nodes;
+  for (int i = 0; i < nt; ++i) if (evcount[i] > 0) nodes.push_back(i);
+  std::stable_sort(nodes.begin(), nodes.end(), [&](int a, int b) { return evcount[a] > evcount[b]; });
+  const int warps = kDfThreads / 32;
+  int heavy = 0;
+  const int64_t heavy_min = std::max<int64_t>(32, n / 64);
+  while (heavy < (int)nodes.size() && heavy < warps / 2 && evcount[nodes[heavy]] >= heavy_min) {
+    owner[nodes[heavy]] = heavy * 32;              // lane 0 of its own warp
+    ++heavy;
+  }
+  // least-loaded threads among the warps not taken by heavy nodes
+  std::vector<std::pair<int64_t, int>> heapv;
+  for (int t = heavy * 32; t < kDfThreads; ++t) heapv.push_back({0, t});
+  auto cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+    return a.first > b.first || (a.first == b.first && a.second > b.second);
+  };
+  std::make_heap(heapv.begin(), heapv.end(), cmp);
+  for (size_t k = heavy; k < nodes.size(); ++k) {
+    std::pop_heap(heapv.begin(), heapv.end(), cmp);
+    heapv.back().first += evcount[nodes[k]];
+    owner[nodes[k]] = heapv.back().second;
+    std::push_heap(heapv.begin(), heapv.end(), cmp);
+  }
+  // wait counts in input order, and which events must publish: a sampling of v
+  // when a transfer into v follows it, a transfer into w when a sampling of w
+  // follows it (only those counters are ever waited on)
+  std::vector<int32_t> adds(nt, 0), samps(nt, 0);
+  std::vector<int64_t> last_into(nt, -1), last_samp(nt, -1);
+  std::vector<int4> rec(n);
+  std::vector<int4> wt(n);
+  std::vector<int32_t> own(n);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int64_t e = by_pos[(size_t)s];
+    const int k = kind[e];
+    if (k != SIM_ENTER) last_samp[slot_of[node[e]]] = s;
+    if (k == SIM_EXTERNAL) last_into[slot_of[dest[e]]] = s;
+  }
+  for (int64_t s = s0; s < s1; ++s) {
+    const int64_t e = by_pos[(size_t)s];
+    const int k = kind[e];
+    const int a = slot_of[node[e]];
+    const int b = (k == SIM_EXTERNAL) ? slot_of[dest[e]] : -1;
+    const uint32_t packed = (uint32_t)k | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
+    rec[(size_t)(s - s0)] = make_int4(a, b, (int32_t)s, (int32_t)packed);
+    int4 w = make_int4(0, 0, 0, 0);
+    if (k != SIM_ENTER) {
+      w.x = adds[a]; samps[a]++;
+      if (s < last_into[a]) w.z |= kDfPublishSampling;
+    }
+    if (k == SIM_EXTERNAL) {
+      w.y = samps[b]; adds[b]++;
+      if (s < last_samp[b]) w.z |= kDfPublishAdd;
+    }
+    if (w.x > 0 || w.y > 0) w.z |= kDfAcquire;
+    wt[(size_t)(s - s0)] = w;
+    own[(size_t)(s - s0)] = owner[a];
+  }
+  // group by owner thread, input order within
+  std::vector<int32_t> off(kDfThreads + 1, 0);
+  for (int64_t i = 0; i < n; ++i) off[(size_t)own[(size_t)i] + 1]++;
+  for (int t = 0; t < kDfThreads; ++t) off[(size_t)t + 1] += off[(size_t)t];
+  std::vector<int32_t> fill(off.begin(), off.end() - 1);
+  const size_t base = S.rec_df.size();
+  S.rec_df.resize(base + (size_t)n);
+  S.wait_df.resize(base + (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t at = fill[(size_t)own[(size_t)i]]++;
+    S.rec_df[base + (size_t)at] = rec[(size_t)i];
+    S.wait_df[base + (size_t)at] = wt[(size_t)i];
+  }
+  S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
+  (void)d;
+}
 
 // Validates the events and builds the execution schedule: stable sort by day,
 // then per day a dependency level for each event.  A sampling event on node v
@@ -277,6 +382,9 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     S.level.resize((size_t)n_run);
     S.rec_slot.resize((size_t)n_run);
     S.day_touch.assign((size_t)T + 1, 0);
+    S.rec_df.reserve((size_t)n_run);
+    S.wait_df.reserve((size_t)n_run);
+    S.thr_off.reserve((size_t)T * (kDfThreads + 1));
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
   std::vector<int32_t> slot_of(N, -1), slot_day(N, -1);
   for (int32_t d = 0; d < T; ++d) {
@@ -329,6 +437,7 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
       const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
       S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
     }
+    build_owner_form(S, d, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of);
   }
   S.day_lvl[T] = (int32_t)S.lvl_start.size();
   S.day_touch[T] = (int32_t)S.touched.size();
@@ -496,6 +605,26 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   if (err == cudaSuccess && !S.touched.empty()) err = cudaMemcpy(h->d_touched, S.touched.data(), S.touched.size() * 4, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(h->d_day_touch, S.day_touch.data(), S.day_touch.size() * 4, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
+  {
+    std::vector<int32_t> day_ev((size_t)T + 1);
+    for (int32_t d = 0; d <= T; ++d) day_ev[(size_t)d] = S.lvl_start[(size_t)S.day_lvl[(size_t)d]];
+    if (err == cudaSuccess) err = dalloc(&h->d_rec_df, S.rec_df.size());
+    if (err == cudaSuccess) err = dalloc(&h->d_wait_df, S.wait_df.size());
+    if (err == cudaSuccess) err = dalloc(&h->d_thr_off, S.thr_off.size());
+    if (err == cudaSuccess) err = dalloc(&h->d_day_ev, day_ev.size());
+    if (err == cudaSuccess && !S.rec_df.empty()) err = cudaMemcpy(h->d_rec_df, S.rec_df.data(), S.rec_df.size() * 16, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && !S.wait_df.empty()) err = cudaMemcpy(h->d_wait_df, S.wait_df.data(), S.wait_df.size() * 16, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && !S.thr_off.empty()) err = cudaMemcpy(h->d_thr_off, S.thr_off.data(), S.thr_off.size() * 4, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(h->d_day_ev, day_ev.data(), day_ev.size() * 4, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
+    h->day_df.assign((size_t)T, 0);
+    for (int32_t d = 0; d < T; ++d) {
+      const int64_t ne = day_ev[(size_t)d + 1] - day_ev[(size_t)d];
+      const int64_t nt = S.day_touch[(size_t)d + 1] - S.day_touch[(size_t)d];
+      const size_t b = events_df_smem_bytes(ne, nt, h->nc);
+      h->day_df[(size_t)d] = (b <= kEventsSmemLimit) ? (int32_t)b : 0;
+    }
+  }
   h->day_smem.assign((size_t)T, 0);
   for (int32_t d = 0; d < T; ++d) {
     const int64_t nl = S.day_lvl[(size_t)d + 1] - S.day_lvl[(size_t)d];
@@ -551,12 +680,22 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   es.touched = h->d_touched; es.day_touch = h->d_day_touch; es.ctr = h->d_ctr; es.err = h->d_err;
   es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
   es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
+  EvDfArgs df{};
+  df.counts = h->d_counts; df.rec = h->d_rec_df; df.wait = h->d_wait_df; df.thr_off = h->d_thr_off;
+  df.day_ev = h->d_day_ev; df.touched = h->d_touched; df.day_touch = h->d_day_touch; df.ctr = h->d_ctr;
+  df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
+  df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
+  df.spin_limit = 1 << 24;
   for (int32_t d = d0; d < d0 + ndays; ++d) {
     a.day = d;
     a.prologue = d > d0;
     CK(h, traced(h, 0, st, [&] { return launch_ssa_day(a, h->n_age, score, st); }), "stochastic step launch");
     if (h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]) {
-      if (h->day_smem[(size_t)d] > 0) {
+      if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
+        df.day = d;
+        df.smem_bytes = h->day_df[(size_t)d];
+        CK(h, traced(h, 1, st, [&] { return launch_events_day_df(df, h->n_age, st); }), "event step launch");
+      } else if (h->event_variant != 1 && h->day_smem[(size_t)d] > 0) {
         es.day = d;
         es.smem_bytes = h->day_smem[(size_t)d];
         CK(h, traced(h, 1, st, [&] { return launch_events_day_smem(es, h->n_age, st); }), "event step launch");
@@ -737,6 +876,9 @@ void sim_destroy(sim_handle* h) {
 
 sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only) {
   if (!h) return SIM_E_INVALID_ARG;
+  if (global_only < 0 || global_only > 2) return fail(h, SIM_E_INVALID_ARG, "variant must be 0, 1 or 2");
+  h->event_variant = global_only;
+  if (global_only == 2) return SIM_OK;
   h->force_global_events = global_only != 0;
   for (size_t d = 0; d < h->day_smem.size(); ++d)
     if (h->force_global_events) h->day_smem[d] = 0;

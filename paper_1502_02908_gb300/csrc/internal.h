@@ -82,6 +82,36 @@ struct EvSmemArgs {
 };
 
 cudaError_t launch_events_day_smem(const EvSmemArgs& a, int n_age, cudaStream_t st);
+
+// Owner-computes event step (no levels on the device): thread t applies, in input
+// order, the events of the nodes it owns, waiting on shared-memory counters for
+// the transfers into a node that precede a sampling of it and for the samplings of
+// a destination that precede a transfer into it.
+constexpr int kDfThreads = 512;
+constexpr int kEventWaitTimeout = 4;      // error bit: an event-step wait ran out
+constexpr int kDfAcquire = 1;             // the event waited on another thread's counter
+constexpr int kDfPublishSampling = 2;     // a later transfer into its node waits on it
+constexpr int kDfPublishAdd = 4;          // a later sampling of its destination waits on it
+struct EvDfArgs {
+  int32_t* counts;
+  const int4* rec;            // per day: grouped by owner thread, input order within
+  const int4* wait;           // {adds into src before it, samplings of dst before it, flags, 0}
+  const int32_t* thr_off;     // [max_days][kDfThreads + 1]
+  const int32_t* day_ev;      // [max_days + 1] first record of each day
+  const int32_t* touched;
+  const int32_t* day_touch;
+  unsigned long long* ctr;
+  int32_t* err;
+  uint64_t seed;
+  int32_t rep_base;
+  int32_t N, R, Nc;
+  int32_t day;
+  int32_t underflow_error;
+  int32_t smem_bytes;
+  int32_t spin_limit;
+};
+cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st);
+size_t events_df_smem_bytes(int64_t n_events, int64_t n_touched, int nc);
 // Shared memory the staged event step needs for a day (0 if the day has no events).
 size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc);
 constexpr size_t kEventsSmemLimit = 220 * 1024;

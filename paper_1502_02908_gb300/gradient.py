@@ -61,15 +61,19 @@ def _slice_params(p: W.Params, r0, r1):
                     p.beta[r0:r1].copy(), p.epsilon[r0:r1].copy())
 
 
-def run_moments(spec: GradientSpec, per_replicate=False):
+def run_moments(spec: GradientSpec, per_replicate=False, rank=0, world=1):
     """Runs every replicate (in chunks), returns (moments [F, 34] summed over all
-    replicates, R, optional per-replicate (f [R, F], score [R, 8]))."""
+    replicates, R, optional per-replicate (f [R, F], score [R, 8])).  With
+    world > 1 (torch.distributed initialised, one GPU per rank) each rank runs
+    its contiguous replicate range and the moment sums are combined in rank order."""
+    from . import replicas
     w = spec.w
     days = np.ascontiguousarray(spec.days, np.int32)
     total = np.zeros((days.size, N_MOMENTS))
     fs, ss = [], []
-    for r0 in range(0, w.R, spec.chunk):
-        r1 = min(w.R, r0 + spec.chunk)
+    lo, hi = replicas.shard(w.R, world, rank)
+    for r0 in range(lo, hi, spec.chunk):
+        r1 = min(hi, r0 + spec.chunk)
         s = B.Sim(w.model, w.u0, w.phi0, _slice_params(w.params, r0, r1), w.T, seed=w.seed,
                   score_reverse=True, replicate_base=r0)
         try:
@@ -85,7 +89,9 @@ def run_moments(spec: GradientSpec, per_replicate=False):
                 ss.append(per)
         finally:
             s.close()
-    extra = (np.concatenate(fs), np.concatenate(ss)) if per_replicate else None
+    if world > 1:
+        total = replicas.allreduce_moments(total)
+    extra = (np.concatenate(fs), np.concatenate(ss)) if per_replicate and fs else None
     return total, w.R, extra
 
 

@@ -26,8 +26,8 @@ def _assert_phi(got, ref):
     np.testing.assert_allclose(got, ref, rtol=PHI_RTOL, atol=0)
 
 
-def _run_gpu(w, ndays=None, **kw):
-    s = B.Sim.from_workload(w, **kw)
+def _run_gpu(w, ndays=None, event_variant=None, **kw):
+    s = B.Sim.from_workload(w, event_variant=event_variant, **kw)
     s.run(w.T if ndays is None else ndays)
     counts, phi, day = s.state()
     pi, pn, ctr = s.stats()
@@ -239,3 +239,14 @@ def test_reverse_score_sweep_matches_oracle_tangents():
     for k in (6, 7):
         scale = np.abs(ref.score[:, k]).max()
         assert np.max(np.abs(sc[:, k] - ref.score[:, k])) <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_event_kernel_variants_bitexact(variant):
+    # 0: owner-computes kernel (default), 2: level-scheduled kernels
+    w = W.sise3_national()
+    w.T = 90
+    counts, phi, pi, pn, ctr, _ = _run_gpu(w, event_variant=variant)
+    ref = oracle.run(w)
+    assert np.array_equal(counts, ref.counts) and np.array_equal(ctr, ref.counters)
+    _assert_phi(phi, ref.phi)
