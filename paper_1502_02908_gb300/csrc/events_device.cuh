@@ -395,6 +395,124 @@ __device__ __forceinline__ void events_block_smem(const EvSmemArgs& a, int r, un
 }
 
 
+// One event on a node whose counts live in the owner's registers (x).  Same
+// semantics and draws as apply_event_smem; transfer destinations are added in
+// shared memory.  Each class case is straight-line code with compile-time
+// register indices (a lone thread pays the latency of every instruction).
+template <int NA, int J>
+__device__ __forceinline__ void one_class_reg(int kind, int32_t n, int underflow_error, int32_t* err,
+                                              DrawState& st, int32_t* cd, int32_t (&x)[2 * NA],
+                                              unsigned& applied, unsigned& clamped, unsigned& skipped) {
+  const int32_t s0 = x[2 * J], s1 = x[2 * J + 1];
+  const int32_t avail = s0 + s1;
+  int32_t take = n;
+  if (n > avail) {
+    if (underflow_error) { ++skipped; atomicOr(err, 1); return; }
+    take = avail;
+    ++clamped;
+  }
+  int32_t t0, t1;
+  if (take == avail) { t0 = s0; t1 = s1; }
+  else if (s0 == 0) { t0 = 0; t1 = take; }
+  else if (s1 == 0) { t0 = take; t1 = 0; }
+  else {
+    t0 = 0;
+    for (int32_t k = 0; k < take; ++k) {
+      const uint32_t sl = draw_slot(st, k, (uint32_t)(avail - k));
+      t0 += (sl < (uint32_t)(s0 - t0)) ? 1 : 0;
+    }
+    t1 = take - t0;
+  }
+  x[2 * J] = s0 - t0;
+  x[2 * J + 1] = s1 - t1;
+  if (kind == 2) {
+    if (2 * J + 3 < 2 * NA) { x[2 * J + 2 < 2 * NA ? 2 * J + 2 : 0] += t0; x[2 * J + 3 < 2 * NA ? 2 * J + 3 : 0] += t1; }
+  } else if (kind == 3) {
+    if (t0) atomicAdd(&cd[2 * J], t0);
+    if (t1) atomicAdd(&cd[2 * J + 1], t1);
+  }
+  ++applied;
+}
+
+template <int NA>
+__device__ __forceinline__ void all_classes_reg(int kind, int32_t n, int underflow_error, int32_t* err,
+                                                DrawState& st, int32_t* cd, int32_t (&x)[2 * NA],
+                                                unsigned& applied, unsigned& clamped, unsigned& skipped) {
+  constexpr int NC = 2 * NA;
+  int32_t avail = x[0] + x[1];
+  if (NA == 3) avail += (x[2 < NC ? 2 : 0] + x[3 < NC ? 3 : 0]) + (x[4 < NC ? 4 : 0] + x[5 < NC ? 5 : 0]);
+  int32_t take = n;
+  if (n > avail) {
+    if (underflow_error) { ++skipped; atomicOr(err, 1); return; }
+    take = avail;
+    ++clamped;
+  }
+  if (take == 0) { ++applied; return; }
+  int32_t took[NC];
+  if (take == avail) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { took[c] = x[c]; x[c] = 0; }
+  } else {
+    int nonempty = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) nonempty += x[c] > 0 ? 1 : 0;
+    if (nonempty <= 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { took[c] = x[c] > 0 ? take : 0; x[c] -= took[c]; }
+    } else {
+      int32_t cum[NC];
+      int32_t acc = 0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { acc += x[c]; cum[c] = acc; took[c] = 0; }
+      for (int32_t k = 0; k < take; ++k) {
+        const uint32_t sl = draw_slot(st, k, (uint32_t)(avail - k));
+        bool below[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) below[c] = sl < (uint32_t)cum[c];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          took[c] += (below[c] && (c == 0 || !below[c > 0 ? c - 1 : 0])) ? 1 : 0;
+          cum[c] -= below[c] ? 1 : 0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] -= took[c];
+    }
+  }
+  if (kind == 3) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (took[c]) atomicAdd(&cd[c], took[c]);
+  }
+  ++applied;
+}
+
+template <int NA>
+__device__ __forceinline__ void apply_event_reg(int underflow_error, int32_t* err, int day, uint64_t seed,
+                                                int32_t* cnt, uint32_t rep, int4 rec, const Words8& w8,
+                                                int32_t (&x)[2 * NA], unsigned& applied, unsigned& clamped,
+                                                unsigned& skipped) {
+  const int kind = rec.w & 3;
+  const int cls = ((rec.w >> 2) & 3) - 1;
+  const int32_t n = (int32_t)((uint32_t)rec.w >> 4);
+  if (kind == 1) {
+    if (cls <= 0) x[0] += n;
+    else if (NA == 3 && cls == 1) x[2 < 2 * NA ? 2 : 0] += n;
+    else if (NA == 3) x[4 < 2 * NA ? 4 : 0] += n;
+    ++applied;
+    return;
+  }
+  DrawState st;
+  st.ws.w = w8; st.ws.q = 0; st.ws.e = (uint32_t)rec.z; st.ws.day = (uint32_t)day; st.ws.rep = rep;
+  st.ws.k0 = (uint32_t)seed; st.ws.k1 = (uint32_t)(seed >> 32);
+  st.exact = false;
+  int32_t* cd = cnt + rec.y * 2 * NA;
+  if (cls < 0) all_classes_reg<NA>(kind, n, underflow_error, err, st, cd, x, applied, clamped, skipped);
+  else if (cls == 0) one_class_reg<NA, 0>(kind, n, underflow_error, err, st, cd, x, applied, clamped, skipped);
+  else if (NA == 3 && cls == 1) one_class_reg<NA, (NA == 3 ? 1 : 0)>(kind, n, underflow_error, err, st, cd, x, applied, clamped, skipped);
+  else if (NA == 3) one_class_reg<NA, (NA == 3 ? 2 : 0)>(kind, n, underflow_error, err, st, cd, x, applied, clamped, skipped);
+}
+
 // ---- owner-computes variant (no levels): thread t applies, in input order, the
 // events of the nodes it owns.  A sampling of node v first waits until every
 // transfer into v that precedes it in input order has been added (v's add
@@ -420,18 +538,36 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
   int32_t* soff = ssmp + nt;
   int32_t* sabort = soff + (kDfThreads + 1);
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-  for (int i0 = threadIdx.x; i0 < nt; i0 += 4 * blockDim.x) {
+  // setup: the scattered count loads and the record loads of up to 4 nodes and 4
+  // events per thread are issued first; the Philox blocks are computed while they
+  // are in flight
+  for (int i0 = threadIdx.x; i0 < (nt > nev ? nt : nev); i0 += 4 * blockDim.x) {
     int v[4];
+    int4 rc[4], wv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * blockDim.x;
       v[u] = i < nt ? a.touched[t0 + i] : -1;
+      if (i < nev) { rc[u] = a.rec[e0 + i]; wv[u] = a.wait[e0 + i]; }
     }
     int32_t x[4][NC];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[u][c] = v[u] >= 0 ? __ldcg(X + (size_t)c * a.N + v[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < nev) {
+        const uint4 c0 = make_uint4((uint32_t)rc[u].z, (uint32_t)a.day | kEventTag, 0u, rep);
+        Words8 w;
+        w.a = philox10(c0, k0, k1);
+        w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
+        swords[i] = w;
+        srec[i] = rc[u];
+        swait[i] = wv[u];
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * blockDim.x;
@@ -443,33 +579,23 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
       }
     }
   }
-  for (int i0 = threadIdx.x; i0 < nev; i0 += 4 * blockDim.x) {
-    int4 rc[4], wv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < nev) { rc[u] = a.rec[e0 + i]; wv[u] = a.wait[e0 + i]; }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < nev) {
-        srec[i] = rc[u];
-        swait[i] = wv[u];
-        const uint4 c0 = make_uint4((uint32_t)rc[u].z, (uint32_t)a.day | kEventTag, 0u, rep);
-        Words8 w;
-        w.a = philox10(c0, k0, k1);
-        w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
-        swords[i] = w;
-      }
-    }
-  }
   const int32_t* off = a.thr_off + (size_t)a.day * (kDfThreads + 1);
   for (int i = threadIdx.x; i <= kDfThreads; i += blockDim.x) soff[i] = off[i];
   if (threadIdx.x == 0) *sabort = 0;
   __syncthreads();
   unsigned applied = 0, clamped = 0, skipped = 0;
   const int q0 = soff[threadIdx.x], q1 = soff[threadIdx.x + 1];
+  // a thread owning one heavy node (lane 0 of one of the first day_heavy warps)
+  // keeps the node's counts in registers; the node's shared-memory counts then
+  // act as an inbox for transfers from other threads, drained after each wait
+  const bool heavy = (threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < a.day_heavy[a.day] && q0 < q1;
+  int32_t hx[NC];
+  int hslot = -1;
+  if (heavy) {
+    hslot = srec[q0].x;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { hx[c] = scnt[hslot * NC + c]; scnt[hslot * NC + c] = 0; }
+  }
   int4 rc = make_int4(0, 0, 0, 0), wt = make_int4(0, 0, 0, 0);
   Words8 wd;
   if (q0 < q1) { rc = srec[q0]; wt = swait[q0]; wd = swords[q0]; }
@@ -497,9 +623,15 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
         break;
       }
       __threadfence_block();
+      if (heavy && wt.x > 0) {                        // drain the transfers received so far
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hx[c] += atomicExch(&scnt[hslot * NC + c], 0);
+      }
     }
-    apply_event_smem<NA, true>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rc, wd, applied, clamped,
-                               skipped);
+    if (heavy) apply_event_reg<NA>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rc, wd, hx, applied, clamped,
+                                   skipped);
+    else apply_event_smem<NA, true>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rc, wd, applied, clamped,
+                                    skipped);
     if (wt.z & (kDfPublishSampling | kDfPublishAdd)) {
       __threadfence_block();
       if (wt.z & kDfPublishSampling) *(volatile int32_t*)(ssmp + rc.x) = *(volatile int32_t*)(ssmp + rc.x) + 1;
@@ -507,6 +639,10 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
     }
     (void)kind;
     rc = nrc; wt = nwt; wd = nwd;
+  }
+  if (heavy) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) atomicAdd(&scnt[hslot * NC + c], hx[c]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {

@@ -59,6 +59,7 @@ struct sim_handle {
   int4* d_wait_df = nullptr;
   int32_t* d_thr_off = nullptr;
   int32_t* d_day_ev = nullptr;
+  int32_t* d_day_heavy = nullptr;
   int32_t event_variant = 0;         // 0 auto, 1 global only, 2 levels (no owner-computes)
   int32_t* d_day_smem = nullptr;     // device copy for the persistent batch kernel
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
@@ -114,7 +115,9 @@ void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
   cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_day_ev);
+  cudaFree(h->d_day_heavy);
   h->d_rec_df = nullptr; h->d_wait_df = nullptr; h->d_thr_off = nullptr; h->d_day_ev = nullptr;
+  h->d_day_heavy = nullptr;
   h->day_df.clear();
   h->d_day_smem = nullptr;
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
@@ -232,6 +235,7 @@ struct Schedule {
   std::vector<int4> rec_df;       // {slot_src, slot_dst, position, packed}
   std::vector<int4> wait_df;      // {transfer-adds into src before it, samplings of dst before it, flags, 0}
   std::vector<int32_t> thr_off;   // [max_days][kDfThreads + 1] offsets within the day
+  std::vector<int32_t> day_heavy; // [max_days] heavy nodes (lane 0 of warps 0..heavy-1)
   std::vector<int32_t> touched;   // node ids per day slot
   std::vector<int32_t> day_touch; // [max_days + 1]
   std::vector<int32_t> lvl_start; // [levels + 1]
@@ -328,6 +332,7 @@ void build_owner_form(Schedule& S, int32_t d, int64_t s0, int64_t s1, int32_t to
     S.wait_df[base + (size_t)at] = wt[(size_t)i];
   }
   S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
+  S.day_heavy.push_back(heavy);
   (void)d;
 }
 
@@ -385,6 +390,7 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     S.rec_df.reserve((size_t)n_run);
     S.wait_df.reserve((size_t)n_run);
     S.thr_off.reserve((size_t)T * (kDfThreads + 1));
+    S.day_heavy.reserve((size_t)T);
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
   std::vector<int32_t> slot_of(N, -1), slot_day(N, -1);
   for (int32_t d = 0; d < T; ++d) {
@@ -612,6 +618,8 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
     if (err == cudaSuccess) err = dalloc(&h->d_wait_df, S.wait_df.size());
     if (err == cudaSuccess) err = dalloc(&h->d_thr_off, S.thr_off.size());
     if (err == cudaSuccess) err = dalloc(&h->d_day_ev, day_ev.size());
+    if (err == cudaSuccess) err = dalloc(&h->d_day_heavy, S.day_heavy.size());
+    if (err == cudaSuccess && !S.day_heavy.empty()) err = cudaMemcpy(h->d_day_heavy, S.day_heavy.data(), S.day_heavy.size() * 4, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !S.rec_df.empty()) err = cudaMemcpy(h->d_rec_df, S.rec_df.data(), S.rec_df.size() * 16, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !S.wait_df.empty()) err = cudaMemcpy(h->d_wait_df, S.wait_df.data(), S.wait_df.size() * 16, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !S.thr_off.empty()) err = cudaMemcpy(h->d_thr_off, S.thr_off.data(), S.thr_off.size() * 4, cudaMemcpyHostToDevice);
@@ -683,6 +691,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   EvDfArgs df{};
   df.counts = h->d_counts; df.rec = h->d_rec_df; df.wait = h->d_wait_df; df.thr_off = h->d_thr_off;
   df.day_ev = h->d_day_ev; df.touched = h->d_touched; df.day_touch = h->d_day_touch; df.ctr = h->d_ctr;
+  df.day_heavy = h->d_day_heavy;
   df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;

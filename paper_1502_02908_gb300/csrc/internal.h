@@ -97,6 +97,7 @@ struct EvDfArgs {
   const int4* rec;            // per day: grouped by owner thread, input order within
   const int4* wait;           // {adds into src before it, samplings of dst before it, flags, 0}
   const int32_t* thr_off;     // [max_days][kDfThreads + 1]
+  const int32_t* day_heavy;   // [max_days] warps whose lane 0 owns one heavy node
   const int32_t* day_ev;      // [max_days + 1] first record of each day
   const int32_t* touched;
   const int32_t* day_touch;

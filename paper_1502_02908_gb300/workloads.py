@@ -178,18 +178,27 @@ def vtec_beta():
     return np.array([math.log(2.0) / k for k in VTEC_BETA_DIV])
 
 
-def _national_events(rng, N, T, n_events, mix=(0.4, 0.3, 0.2, 0.1), max_count=5,
-                     power=2.2):
-    """Register-shaped events: sources drawn with power-law weights (out-degree
-    exponent 2.2), external-transfer destinations by preferential attachment over
-    the events in day order (P(j) ~ in-degree so far + 1, j != source)."""
+def _national_events(rng, N, T, n_events, herd, mix=(0.4, 0.3, 0.2, 0.1), max_count=5,
+                     power=2.2, e1_source="herd"):
+    """Register-shaped events.  Single-node events (exit, enter, aging) happen at
+    nodes drawn in proportion to herd size (births, deaths and aging scale with the
+    number of animals); external transfers leave nodes drawn with power-law weights
+    (out-degree exponent 2.2) and arrive at destinations chosen by preferential
+    attachment over the events in day order (P(j) ~ in-degree so far + 1,
+    j != source).  e1_source="powerlaw" draws the single-node events with the
+    power-law weights as well (a stress case: one small herd then carries a long
+    chain of events every day)."""
     weights = rng.zipf(power, size=N).astype(np.float64)
     weights = np.minimum(weights, N)
-    p = weights / weights.sum()
+    p_out = weights / weights.sum()
+    hw = np.asarray(herd, np.float64)
+    p_e1 = hw / hw.sum() if e1_source == "herd" else p_out
     kinds = rng.choice(4, size=n_events, p=np.asarray(mix, float))
     kind = np.array([EXIT, ENTER, INTERNAL, EXTERNAL])[kinds]
     day = rng.integers(0, T, size=n_events)
-    node = rng.choice(N, size=n_events, p=p)
+    node = rng.choice(N, size=n_events, p=p_e1)
+    is_ext = kind == EXTERNAL
+    node[is_ext] = rng.choice(N, size=int(is_ext.sum()), p=p_out)
     count = rng.integers(1, max_count + 1, size=n_events)
     cls = np.full(n_events, -1, np.int64)
     cls[kind == ENTER] = 0
@@ -223,14 +232,14 @@ def _national_events(rng, N, T, n_events, mix=(0.4, 0.3, 0.2, 0.1), max_count=5,
                   dest.astype(np.int32), count.astype(np.int32), cls.astype(np.int32))
 
 
-def sise3_national(N=37_000, T=1460, n_events=3_000_000, seed=1, R=1, gen_seed=2):
+def sise3_national(N=37_000, T=1460, n_events=3_000_000, seed=1, R=1, gen_seed=2, e1_source="herd"):
     """SISe3 with VTEC O157 constants (Sec. 4.1) on a national-scale synthetic
     network: herds lognormal (median 50, sigma 1, capped at 5000) split 20/20/60
     into calves/young/adults, 5% infected per class; seasonal beta."""
     rng = np.random.Generator(np.random.PCG64(gen_seed))
     herd = np.minimum(5000, np.maximum(1, _round_half_even(rng.lognormal(math.log(50.0), 1.0, size=N))))
     u0 = _initial_counts(SISE3, herd)
-    ev = _national_events(rng, N, T, n_events) if n_events else Events.empty()
+    ev = _national_events(rng, N, T, n_events, herd, e1_source=e1_source) if n_events else Events.empty()
     gam = [1.0 / d for d in VTEC_DELTA]
     params = Params.broadcast(R, VTEC_UPSILON, gam, 1.0, vtec_beta(), 1e-6)
     return Workload("sise3_national", SISE3, N, T, R, u0, np.zeros(N), params, ev, seed)

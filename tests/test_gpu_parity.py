@@ -241,10 +241,11 @@ def test_reverse_score_sweep_matches_oracle_tangents():
         assert np.max(np.abs(sc[:, k] - ref.score[:, k])) <= 1e-9 * scale
 
 
-@pytest.mark.parametrize("variant", [0, 2])
-def test_event_kernel_variants_bitexact(variant):
-    # 0: owner-computes kernel (default), 2: level-scheduled kernels
-    w = W.sise3_national()
+@pytest.mark.parametrize("variant,e1_source", [(0, "herd"), (2, "herd"), (0, "powerlaw"), (2, "powerlaw")])
+def test_event_kernel_variants_bitexact(variant, e1_source):
+    # 0: owner-computes kernel (default), 2: level-scheduled kernels; "powerlaw"
+    # puts ~8% of all events on one small herd (a long chain every day)
+    w = W.sise3_national(e1_source=e1_source)
     w.T = 90
     counts, phi, pi, pn, ctr, _ = _run_gpu(w, event_variant=variant)
     ref = oracle.run(w)
