@@ -16,7 +16,7 @@
  *         on [d, d+1) with the environmental state phi frozen at phi_d
  *         (Sec. 3.3, Eqs. sampling and sampling2);
  *   (ii)  deterministic step, Eq. numstep4: the day's scheduled events in input
- *         order ("read and incorporate", Sec. 3.3; event records Eq. event);
+ *         order (the list processor of Sec. 3.3; event records Eq. event);
  *   (iii) continuous-state update, Eq. numstep5 with the VTEC model of
  *         Eq. siminfpressure: phi <- phi*(1-beta) + alpha*I/N + epsilon, from the
  *         post-event counts (Alg. 1 order) or, on request, from the post-SSA
