@@ -219,6 +219,17 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   int32_t nb = 0;
   if (!(h->cfg.flags & SIM_FLAG_SCORE))
     while (nb < N && herd[order[nb]] >= thr) ++nb;
+  // deal the warp-path nodes round-robin over their blocks (8 warps each), so the
+  // largest herds land in different blocks (and SMs) instead of sharing one
+  // (whole blocks only: the few smallest warp-path herds past a multiple of 8
+  // go to the thread path)
+  if (nb > 8) {
+    nb = nb / 8 * 8;
+    const int nblk = nb / 8;
+    std::vector<int32_t> dealt((size_t)nb);
+    for (int k = 0; k < nb; ++k) dealt[(size_t)(k % nblk) * 8 + k / nblk] = order[k];
+    std::copy(dealt.begin(), dealt.end(), order.begin());
+  }
   if (!h->d_order) CK(h, dalloc(&h->d_order, (size_t)N), "node order allocation");
   CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_big = nb;
