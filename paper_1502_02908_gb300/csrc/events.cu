@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(512) k_events_day(EvArgs a) {
 template <int NA>
 __global__ void __launch_bounds__(kDfThreads, 1) k_events_day_df(EvDfArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  events_block_dataflow<NA>(a, blockIdx.x, smem);
+  events_block_dataflow<NA>(a, (int)(blockIdx.x / (unsigned)a.nblk), (int)(blockIdx.x % (unsigned)a.nblk), smem);
 }
 
 template <int NA>
@@ -44,8 +44,9 @@ cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st) 
     if (e != cudaSuccess) return e;
     attr_set[which] = true;
   }
-  if (n_age == 1) k_events_day_df<1><<<a.R, kDfThreads, a.smem_bytes, st>>>(a);
-  else k_events_day_df<3><<<a.R, kDfThreads, a.smem_bytes, st>>>(a);
+  const unsigned grid = (unsigned)a.R * (unsigned)a.nblk;
+  if (n_age == 1) k_events_day_df<1><<<grid, kDfThreads, a.smem_bytes, st>>>(a);
+  else k_events_day_df<3><<<grid, kDfThreads, a.smem_bytes, st>>>(a);
   return cudaGetLastError();
 }
 

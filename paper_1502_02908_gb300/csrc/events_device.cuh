@@ -513,22 +513,26 @@ __device__ __forceinline__ void apply_event_reg(int underflow_error, int32_t* er
   else if (NA == 3) one_class_reg<NA, (NA == 3 ? 2 : 0)>(kind, n, underflow_error, err, st, cd, x, applied, clamped, skipped);
 }
 
-// ---- owner-computes variant (no levels): thread t applies, in input order, the
-// events of the nodes it owns.  A sampling of node v first waits until every
+// ---- owner-computes variant (no levels): the day's touched nodes come in
+// independent blocks (unions of connected components of the day's transfer
+// graph; no event of one block touches a node of another).  In block b, thread t
+// applies, in input order, the events of the nodes it owns.  A sampling of node v first waits until every
 // transfer into v that precedes it in input order has been added (v's add
 // counter); a transfer into w first waits until every sampling of w that precedes
 // it is done (w's sampling counter).  Waits point only to earlier positions and
 // each thread follows input order, so the earliest pending event is always
 // runnable.  Waits are bounded: running out sets an error bit and an abort flag.
 template <int NA>
-__device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, unsigned char* smem) {
+__device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, int b, unsigned char* smem) {
   constexpr int NC = 2 * NA;
   const uint32_t rep = (uint32_t)(a.rep_base + r);
   int32_t* X = a.counts + (size_t)r * NC * a.N;
-  const int e0 = a.day_ev[a.day], e1 = a.day_ev[a.day + 1];
+  const int bi = a.day_blk[a.day] + b;
+  const int e0 = a.blk_ev[bi], e1 = a.blk_ev[bi + 1];
   const int nev = e1 - e0;
-  const int t0 = a.day_touch[a.day], t1 = a.day_touch[a.day + 1];
+  const int t0 = a.blk_touch[bi], t1 = a.blk_touch[bi + 1];
   const int nt = t1 - t0;
+  const int h0 = a.blk_thr[bi], nthr = a.blk_thr[bi + 1] - h0 - 1;
   int4* srec = reinterpret_cast<int4*>(smem);
   Words8* swords = reinterpret_cast<Words8*>(smem + (size_t)nev * 16);
   int4* swait = reinterpret_cast<int4*>(smem + (size_t)nev * 48);
@@ -579,16 +583,16 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
       }
     }
   }
-  const int32_t* off = a.thr_off + (size_t)a.day * (kDfThreads + 1);
-  for (int i = threadIdx.x; i <= kDfThreads; i += blockDim.x) soff[i] = off[i];
+  const int32_t* off = a.thr_off + h0;
+  for (int i = threadIdx.x; i <= kDfThreads; i += blockDim.x) soff[i] = off[i < nthr ? i : nthr];
   if (threadIdx.x == 0) *sabort = 0;
   __syncthreads();
   unsigned applied = 0, clamped = 0, skipped = 0;
   const int q0 = soff[threadIdx.x], q1 = soff[threadIdx.x + 1];
-  // a thread owning one heavy node (lane 0 of one of the first day_heavy warps)
+  // a thread owning one heavy node (lane 0 of one of the block's first heavy warps)
   // keeps the node's counts in registers; the node's shared-memory counts then
   // act as an inbox for transfers from other threads, drained after each wait
-  const bool heavy = (threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < a.day_heavy[a.day] && q0 < q1;
+  const bool heavy = (threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < a.blk_heavy[bi] && q0 < q1;
   int32_t hx[NC];
   int hslot = -1;
   if (heavy) {

@@ -55,11 +55,16 @@ struct sim_handle {
   int32_t* d_day_touch = nullptr;
   std::vector<int32_t> day_smem;     // shared-memory bytes of the staged event step per day (0: global variant)
   std::vector<int32_t> day_df;       // shared-memory bytes of the owner-computes step per day (0: not used)
+  std::vector<int32_t> day_nblk;     // owner-computes blocks per replicate per day
   int4* d_rec_df = nullptr;
   int4* d_wait_df = nullptr;
   int32_t* d_thr_off = nullptr;
-  int32_t* d_day_ev = nullptr;
-  int32_t* d_day_heavy = nullptr;
+  int32_t* d_touched_df = nullptr;
+  int32_t* d_day_blk = nullptr;
+  int32_t* d_blk_ev = nullptr;
+  int32_t* d_blk_touch = nullptr;
+  int32_t* d_blk_thr = nullptr;
+  int32_t* d_blk_heavy = nullptr;
   int32_t event_variant = 0;         // 0 auto, 1 global only, 2 levels (no owner-computes)
   int32_t* d_day_smem = nullptr;     // device copy for the persistent batch kernel
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
@@ -114,11 +119,14 @@ cudaError_t dalloc(T** p, size_t n) {
 void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
-  cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_day_ev);
-  cudaFree(h->d_day_heavy);
-  h->d_rec_df = nullptr; h->d_wait_df = nullptr; h->d_thr_off = nullptr; h->d_day_ev = nullptr;
-  h->d_day_heavy = nullptr;
+  cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_touched_df);
+  cudaFree(h->d_day_blk); cudaFree(h->d_blk_ev); cudaFree(h->d_blk_touch); cudaFree(h->d_blk_thr);
+  cudaFree(h->d_blk_heavy);
+  h->d_rec_df = nullptr; h->d_wait_df = nullptr; h->d_thr_off = nullptr; h->d_touched_df = nullptr;
+  h->d_day_blk = nullptr; h->d_blk_ev = nullptr; h->d_blk_touch = nullptr; h->d_blk_thr = nullptr;
+  h->d_blk_heavy = nullptr;
   h->day_df.clear();
+  h->day_nblk.clear();
   h->d_day_smem = nullptr;
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
   h->d_rec_slot = nullptr; h->d_touched = nullptr; h->d_day_touch = nullptr;
@@ -242,11 +250,18 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
 struct Schedule {
   std::vector<int4> rec;          // execution order
   std::vector<int4> rec_slot;     // same, with node slots of the day's touched list
-  // owner-computes form: per day, events grouped by owner thread, input order within
-  std::vector<int4> rec_df;       // {slot_src, slot_dst, position, packed}
+  // owner-computes form: per day, the touched nodes split into independent blocks
+  // (unions of connected components of the day's transfer graph); per block,
+  // events grouped by owner thread, input order within
+  std::vector<int4> rec_df;       // {block slot of src, block slot of dst, position, packed}
   std::vector<int4> wait_df;      // {transfer-adds into src before it, samplings of dst before it, flags, 0}
-  std::vector<int32_t> thr_off;   // [max_days][kDfThreads + 1] offsets within the day
-  std::vector<int32_t> day_heavy; // [max_days] heavy nodes (lane 0 of warps 0..heavy-1)
+  std::vector<int32_t> touched_df;// node ids per block slot, blocks in order
+  std::vector<int32_t> thr_off;   // per block: event offsets of its owner threads 0..nthr (block-relative)
+  std::vector<int32_t> day_blk;   // [max_days + 1] first block of each day
+  std::vector<int32_t> blk_ev;    // [blocks + 1] first record of each block in rec_df
+  std::vector<int32_t> blk_touch; // [blocks + 1] first node of each block in touched_df
+  std::vector<int32_t> blk_thr;   // [blocks + 1] first entry of each block in thr_off
+  std::vector<int32_t> blk_heavy; // [blocks] heavy nodes (lane 0 of warps 0..heavy-1)
   std::vector<int32_t> touched;   // node ids per day slot
   std::vector<int32_t> day_touch; // [max_days + 1]
   std::vector<int32_t> lvl_start; // [levels + 1]
@@ -256,95 +271,178 @@ struct Schedule {
 };
 
 // Owner-computes form of one day (events at day-stable positions [s0, s1)).
-// Every touched node is owned by one thread, which applies the node's events
-// (enter, exit, aging, transfer out) in input order.  A sampling event waits
-// until every transfer into its node that precedes it has been added; a
-// transfer waits until every sampling of its destination that precedes it is
-// done.  Waits only ever point to earlier input positions, so threads that each
-// follow input order always make progress.  Nodes with many events get a warp of
-// their own (lane 0), so that their chain is not serialised behind other lanes;
-// the others are packed longest-first onto the least-loaded threads.
-void build_owner_form(Schedule& S, int32_t d, int64_t s0, int64_t s1, int32_t touch0,
+// The day's touched nodes fall into connected components of its transfer graph;
+// events of different components never touch a common node, so the components
+// are packed longest-first onto at most max_blocks blocks that run without any
+// exchange between them.  Within a block every node is owned by one thread, which
+// applies the node's events (enter, exit, aging, transfer out) in input order.  A
+// sampling event waits until every transfer into its node that precedes it has
+// been added; a transfer waits until every sampling of its destination that
+// precedes it is done.  Waits only ever point to earlier input positions, so
+// threads that each follow input order always make progress.  Nodes with many
+// events get a warp of their own (lane 0), so that their chain is not serialised
+// behind other lanes; the others are packed longest-first onto the least-loaded
+// threads.
+void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
                       const std::vector<int64_t>& by_pos, const int32_t* kind, const int32_t* node,
                       const int32_t* dest, const int32_t* count, const int32_t* cls,
-                      const std::vector<int32_t>& slot_of) {
+                      const std::vector<int32_t>& slot_of, int max_blocks) {
   const int nt = (int)S.touched.size() - touch0;
   const int64_t n = s1 - s0;
-  std::vector<int32_t> evcount(nt, 0), owner(nt, -1);
-  for (int64_t s = s0; s < s1; ++s) evcount[slot_of[node[by_pos[(size_t)s]]]]++;
-  std::vector<int32_t> nodes;
-  for (int i = 0; i < nt; ++i) if (evcount[i] > 0) nodes.push_back(i);
-  std::stable_sort(nodes.begin(), nodes.end(), [&](int a, int b) { return evcount[a] > evcount[b]; });
-  const int warps = kDfThreads / 32;
-  int heavy = 0;
-  const int64_t heavy_min = std::max<int64_t>(32, n / 64);
-  while (heavy < (int)nodes.size() && heavy < warps / 2 && evcount[nodes[heavy]] >= heavy_min) {
-    owner[nodes[heavy]] = heavy * 32;              // lane 0 of its own warp
-    ++heavy;
-  }
-  // least-loaded threads among the warps not taken by heavy nodes
-  std::vector<std::pair<int64_t, int>> heapv;
-  for (int t = heavy * 32; t < kDfThreads; ++t) heapv.push_back({0, t});
-  auto cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
-    return a.first > b.first || (a.first == b.first && a.second > b.second);
+  S.day_blk.push_back((int32_t)S.blk_ev.size());
+  if (n == 0) return;
+  // components (union-find over the day slots)
+  std::vector<int32_t> par((size_t)nt);
+  for (int i = 0; i < nt; ++i) par[(size_t)i] = i;
+  auto find = [&](int x) {
+    while (par[(size_t)x] != x) { par[(size_t)x] = par[(size_t)par[(size_t)x]]; x = par[(size_t)x]; }
+    return x;
   };
-  std::make_heap(heapv.begin(), heapv.end(), cmp);
-  for (size_t k = heavy; k < nodes.size(); ++k) {
-    std::pop_heap(heapv.begin(), heapv.end(), cmp);
-    heapv.back().first += evcount[nodes[k]];
-    owner[nodes[k]] = heapv.back().second;
-    std::push_heap(heapv.begin(), heapv.end(), cmp);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int64_t e = by_pos[(size_t)s];
+    if (kind[e] != SIM_EXTERNAL) continue;
+    const int a = find(slot_of[node[e]]), b = find(slot_of[dest[e]]);
+    if (a != b) par[(size_t)(a < b ? b : a)] = a < b ? a : b;
+  }
+  std::vector<int32_t> comp_of((size_t)nt), comp_ev;
+  {
+    std::vector<int32_t> id((size_t)nt, -1);
+    for (int i = 0; i < nt; ++i) {
+      const int r = find(i);
+      if (id[(size_t)r] < 0) { id[(size_t)r] = (int32_t)comp_ev.size(); comp_ev.push_back(0); }
+      comp_of[(size_t)i] = id[(size_t)r];
+    }
+  }
+  std::vector<int32_t> evcount((size_t)nt, 0);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int a = slot_of[node[by_pos[(size_t)s]]];
+    evcount[(size_t)a]++;
+    comp_ev[(size_t)comp_of[(size_t)a]]++;
+  }
+  const int ncomp = (int)comp_ev.size();
+  const int G = std::max(1, std::min(max_blocks, ncomp));
+  // components longest-first onto the least-loaded block
+  std::vector<int32_t> blk_of_comp((size_t)ncomp);
+  {
+    std::vector<int32_t> cs((size_t)ncomp);
+    for (int c = 0; c < ncomp; ++c) cs[(size_t)c] = c;
+    std::stable_sort(cs.begin(), cs.end(), [&](int a, int b) { return comp_ev[(size_t)a] > comp_ev[(size_t)b]; });
+    std::vector<std::pair<int64_t, int>> heapv;
+    for (int b = 0; b < G; ++b) heapv.push_back({0, b});
+    auto cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+      return a.first > b.first || (a.first == b.first && a.second > b.second);
+    };
+    std::make_heap(heapv.begin(), heapv.end(), cmp);
+    for (int c : cs) {
+      std::pop_heap(heapv.begin(), heapv.end(), cmp);
+      heapv.back().first += comp_ev[(size_t)c];
+      blk_of_comp[(size_t)c] = heapv.back().second;
+      std::push_heap(heapv.begin(), heapv.end(), cmp);
+    }
+  }
+  // block-local slots, blocks in order, day slot order within a block
+  std::vector<int32_t> blk_nt((size_t)G, 0), local((size_t)nt);
+  for (int i = 0; i < nt; ++i) {
+    const int b = blk_of_comp[(size_t)comp_of[(size_t)i]];
+    local[(size_t)i] = blk_nt[(size_t)b]++;
+  }
+  std::vector<int32_t> blk_t0((size_t)G + 1, 0);
+  for (int b = 0; b < G; ++b) blk_t0[(size_t)b + 1] = blk_t0[(size_t)b] + blk_nt[(size_t)b];
+  const size_t tbase = S.touched_df.size();
+  S.touched_df.resize(tbase + (size_t)nt);
+  for (int i = 0; i < nt; ++i) {
+    const int b = blk_of_comp[(size_t)comp_of[(size_t)i]];
+    S.touched_df[tbase + (size_t)(blk_t0[(size_t)b] + local[(size_t)i])] = S.touched[(size_t)touch0 + (size_t)i];
   }
   // wait counts in input order, and which events must publish: a sampling of v
   // when a transfer into v follows it, a transfer into w when a sampling of w
   // follows it (only those counters are ever waited on)
-  std::vector<int32_t> adds(nt, 0), samps(nt, 0);
-  std::vector<int64_t> last_into(nt, -1), last_samp(nt, -1);
-  std::vector<int4> rec(n);
-  std::vector<int4> wt(n);
-  std::vector<int32_t> own(n);
+  std::vector<int32_t> adds((size_t)nt, 0), samps((size_t)nt, 0);
+  std::vector<int64_t> last_into((size_t)nt, -1), last_samp((size_t)nt, -1);
   for (int64_t s = s0; s < s1; ++s) {
     const int64_t e = by_pos[(size_t)s];
     const int k = kind[e];
-    if (k != SIM_ENTER) last_samp[slot_of[node[e]]] = s;
-    if (k == SIM_EXTERNAL) last_into[slot_of[dest[e]]] = s;
+    if (k != SIM_ENTER) last_samp[(size_t)slot_of[node[e]]] = s;
+    if (k == SIM_EXTERNAL) last_into[(size_t)slot_of[dest[e]]] = s;
   }
+  std::vector<int4> rec((size_t)n), wt((size_t)n);
+  std::vector<int32_t> blk_n((size_t)G, 0);
   for (int64_t s = s0; s < s1; ++s) {
     const int64_t e = by_pos[(size_t)s];
     const int k = kind[e];
     const int a = slot_of[node[e]];
     const int b = (k == SIM_EXTERNAL) ? slot_of[dest[e]] : -1;
     const uint32_t packed = (uint32_t)k | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
-    rec[(size_t)(s - s0)] = make_int4(a, b, (int32_t)s, (int32_t)packed);
+    rec[(size_t)(s - s0)] = make_int4(local[(size_t)a], b >= 0 ? local[(size_t)b] : -1, (int32_t)s, (int32_t)packed);
     int4 w = make_int4(0, 0, 0, 0);
     if (k != SIM_ENTER) {
-      w.x = adds[a]; samps[a]++;
-      if (s < last_into[a]) w.z |= kDfPublishSampling;
+      w.x = adds[(size_t)a]; samps[(size_t)a]++;
+      if (s < last_into[(size_t)a]) w.z |= kDfPublishSampling;
     }
     if (k == SIM_EXTERNAL) {
-      w.y = samps[b]; adds[b]++;
-      if (s < last_samp[b]) w.z |= kDfPublishAdd;
+      w.y = samps[(size_t)b]; adds[(size_t)b]++;
+      if (s < last_samp[(size_t)b]) w.z |= kDfPublishAdd;
     }
     if (w.x > 0 || w.y > 0) w.z |= kDfAcquire;
     wt[(size_t)(s - s0)] = w;
-    own[(size_t)(s - s0)] = owner[a];
+    blk_n[(size_t)blk_of_comp[(size_t)comp_of[(size_t)a]]]++;
   }
-  // group by owner thread, input order within
-  std::vector<int32_t> off(kDfThreads + 1, 0);
-  for (int64_t i = 0; i < n; ++i) off[(size_t)own[(size_t)i] + 1]++;
-  for (int t = 0; t < kDfThreads; ++t) off[(size_t)t + 1] += off[(size_t)t];
-  std::vector<int32_t> fill(off.begin(), off.end() - 1);
-  const size_t base = S.rec_df.size();
-  S.rec_df.resize(base + (size_t)n);
-  S.wait_df.resize(base + (size_t)n);
-  for (int64_t i = 0; i < n; ++i) {
-    const int32_t at = fill[(size_t)own[(size_t)i]]++;
-    S.rec_df[base + (size_t)at] = rec[(size_t)i];
-    S.wait_df[base + (size_t)at] = wt[(size_t)i];
+  // per block: owner threads, events grouped by owner in input order
+  std::vector<std::vector<int32_t>> blk_nodes((size_t)G);
+  for (int i = 0; i < nt; ++i) blk_nodes[(size_t)blk_of_comp[(size_t)comp_of[(size_t)i]]].push_back(i);
+  std::vector<int32_t> owner((size_t)nt, -1);
+  std::vector<std::vector<int32_t>> blk_evs((size_t)G);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int a = slot_of[node[by_pos[(size_t)s]]];
+    blk_evs[(size_t)blk_of_comp[(size_t)comp_of[(size_t)a]]].push_back((int32_t)(s - s0));
   }
-  S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
-  S.day_heavy.push_back(heavy);
-  (void)d;
+  const int warps = kDfThreads / 32;
+  for (int b = 0; b < G; ++b) {
+    std::vector<int32_t> nodes;
+    for (int i : blk_nodes[(size_t)b]) if (evcount[(size_t)i] > 0) nodes.push_back(i);
+    std::stable_sort(nodes.begin(), nodes.end(), [&](int x, int y) { return evcount[(size_t)x] > evcount[(size_t)y]; });
+    const int64_t nb = blk_n[(size_t)b];
+    int heavy = 0;
+    const int64_t heavy_min = std::max<int64_t>(32, nb / 64);
+    while (heavy < (int)nodes.size() && heavy < warps / 2 && evcount[(size_t)nodes[(size_t)heavy]] >= heavy_min) {
+      owner[(size_t)nodes[(size_t)heavy]] = heavy * 32;          // lane 0 of its own warp
+      ++heavy;
+    }
+    // least-loaded threads after the heavy warps (with every load 0 at the start,
+    // threads beyond the node count are never picked)
+    std::vector<std::pair<int64_t, int>> heapv;
+    const int tl = std::min(kDfThreads, heavy * 32 + (int)nodes.size());
+    for (int t = heavy * 32; t < tl; ++t) heapv.push_back({0, t});
+    auto cmp = [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
+      return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heapv.begin(), heapv.end(), cmp);
+    int nthr = heavy > 0 ? (heavy - 1) * 32 + 1 : 0;
+    for (size_t k = (size_t)heavy; k < nodes.size(); ++k) {
+      std::pop_heap(heapv.begin(), heapv.end(), cmp);
+      heapv.back().first += evcount[(size_t)nodes[k]];
+      owner[(size_t)nodes[k]] = heapv.back().second;
+      std::push_heap(heapv.begin(), heapv.end(), cmp);
+      nthr = std::max(nthr, owner[(size_t)nodes[k]] + 1);
+    }
+    std::vector<int32_t> off((size_t)nthr + 1, 0);
+    for (int32_t i : blk_evs[(size_t)b]) off[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]] + 1]++;
+    for (int t = 0; t < nthr; ++t) off[(size_t)t + 1] += off[(size_t)t];
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    const size_t base = S.rec_df.size();
+    S.blk_ev.push_back((int32_t)base);
+    S.blk_touch.push_back((int32_t)(tbase + (size_t)blk_t0[(size_t)b]));
+    S.blk_thr.push_back((int32_t)S.thr_off.size());
+    S.blk_heavy.push_back(heavy);
+    S.rec_df.resize(base + (size_t)nb);
+    S.wait_df.resize(base + (size_t)nb);
+    for (int32_t i : blk_evs[(size_t)b]) {
+      const int32_t at = fill[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]]]++;
+      S.rec_df[base + (size_t)at] = rec[(size_t)i];
+      S.wait_df[base + (size_t)at] = wt[(size_t)i];
+    }
+    S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
+  }
 }
 
 // Validates the events and builds the execution schedule: stable sort by day,
@@ -357,7 +455,7 @@ void build_owner_form(Schedule& S, int32_t d, int64_t s0, int64_t s1, int32_t to
 // input order.  O(n + max_days) time.
 sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, const int32_t* day,
                           const int32_t* kind, const int32_t* node, const int32_t* dest,
-                          const int32_t* count, const int32_t* cls, Schedule& S) {
+                          const int32_t* count, const int32_t* cls, int df_blocks, Schedule& S) {
   if (n < 0 || n >= ((int64_t)1 << 31)) return fail(h, SIM_E_INVALID_ARG, "event count out of range");
   if (n > 0 && (!day || !kind || !node || !dest || !count || !cls))
     return fail(h, SIM_E_INVALID_ARG, "null event array");
@@ -400,8 +498,9 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     S.day_touch.assign((size_t)T + 1, 0);
     S.rec_df.reserve((size_t)n_run);
     S.wait_df.reserve((size_t)n_run);
-    S.thr_off.reserve((size_t)T * (kDfThreads + 1));
-    S.day_heavy.reserve((size_t)T);
+    S.thr_off.reserve((size_t)n_run + (size_t)T);
+    S.touched_df.reserve((size_t)n_run);
+    S.day_blk.reserve((size_t)T + 1);
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
   std::vector<int32_t> slot_of(N, -1), slot_day(N, -1);
   for (int32_t d = 0; d < T; ++d) {
@@ -454,11 +553,15 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
       const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
       S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
     }
-    build_owner_form(S, d, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of);
+    build_owner_form(S, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of, df_blocks);
   }
   S.day_lvl[T] = (int32_t)S.lvl_start.size();
   S.day_touch[T] = (int32_t)S.touched.size();
   S.lvl_start.push_back((int32_t)n_run);
+  S.day_blk.push_back((int32_t)S.blk_ev.size());
+  S.blk_ev.push_back((int32_t)S.rec_df.size());
+  S.blk_touch.push_back((int32_t)S.touched_df.size());
+  S.blk_thr.push_back((int32_t)S.thr_off.size());
   return SIM_OK;
 }
 
@@ -603,8 +706,14 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   if (h->events_loaded) return fail(h, SIM_E_STATE, "events already loaded (sim_reset(h, 1) drops them)");
   if (h->day != 0) return fail(h, SIM_E_STATE, "events must be loaded at day 0");
   Schedule S;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  // owner-computes blocks per replicate and day: enough to spread one replicate
+  // over the SMs, one per replicate once the replicates fill them
+  const int df_blocks = std::max(1, sms / std::max(1, h->cfg.n_replicates));
   sim_status st = build_schedule(h, h->cfg.n_nodes, h->n_age, h->cfg.max_days, n, day, kind, node, dest,
-                                 count, cls, S);
+                                 count, cls, df_blocks, S);
   if (st != SIM_OK) return st;
   free_events(h);
   const int32_t T = h->cfg.max_days;
@@ -623,25 +732,33 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   if (err == cudaSuccess) err = cudaMemcpy(h->d_day_touch, S.day_touch.data(), S.day_touch.size() * 4, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
   {
-    std::vector<int32_t> day_ev((size_t)T + 1);
-    for (int32_t d = 0; d <= T; ++d) day_ev[(size_t)d] = S.lvl_start[(size_t)S.day_lvl[(size_t)d]];
-    if (err == cudaSuccess) err = dalloc(&h->d_rec_df, S.rec_df.size());
-    if (err == cudaSuccess) err = dalloc(&h->d_wait_df, S.wait_df.size());
-    if (err == cudaSuccess) err = dalloc(&h->d_thr_off, S.thr_off.size());
-    if (err == cudaSuccess) err = dalloc(&h->d_day_ev, day_ev.size());
-    if (err == cudaSuccess) err = dalloc(&h->d_day_heavy, S.day_heavy.size());
-    if (err == cudaSuccess && !S.day_heavy.empty()) err = cudaMemcpy(h->d_day_heavy, S.day_heavy.data(), S.day_heavy.size() * 4, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess && !S.rec_df.empty()) err = cudaMemcpy(h->d_rec_df, S.rec_df.data(), S.rec_df.size() * 16, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess && !S.wait_df.empty()) err = cudaMemcpy(h->d_wait_df, S.wait_df.data(), S.wait_df.size() * 16, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess && !S.thr_off.empty()) err = cudaMemcpy(h->d_thr_off, S.thr_off.data(), S.thr_off.size() * 4, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess) err = cudaMemcpy(h->d_day_ev, day_ev.data(), day_ev.size() * 4, cudaMemcpyHostToDevice);
+    auto up = [&](auto** dst, const auto& v, size_t elem) {
+      if (err == cudaSuccess) err = dalloc(dst, v.size());
+      if (err == cudaSuccess && !v.empty()) err = cudaMemcpy(*dst, v.data(), v.size() * elem, cudaMemcpyHostToDevice);
+    };
+    up(&h->d_rec_df, S.rec_df, sizeof(int4));
+    up(&h->d_wait_df, S.wait_df, sizeof(int4));
+    up(&h->d_thr_off, S.thr_off, 4);
+    up(&h->d_touched_df, S.touched_df, 4);
+    up(&h->d_day_blk, S.day_blk, 4);
+    up(&h->d_blk_ev, S.blk_ev, 4);
+    up(&h->d_blk_touch, S.blk_touch, 4);
+    up(&h->d_blk_thr, S.blk_thr, 4);
+    up(&h->d_blk_heavy, S.blk_heavy, 4);
     if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
+    // shared memory of a day's launch: its largest block (0: owner-computes not used)
     h->day_df.assign((size_t)T, 0);
+    h->day_nblk.assign((size_t)T, 0);
     for (int32_t d = 0; d < T; ++d) {
-      const int64_t ne = day_ev[(size_t)d + 1] - day_ev[(size_t)d];
-      const int64_t nt = S.day_touch[(size_t)d + 1] - S.day_touch[(size_t)d];
-      const size_t b = events_df_smem_bytes(ne, nt, h->nc);
-      h->day_df[(size_t)d] = (b <= kEventsSmemLimit) ? (int32_t)b : 0;
+      const int32_t b0 = S.day_blk[(size_t)d], b1 = S.day_blk[(size_t)d + 1];
+      size_t most = 0;
+      for (int32_t b = b0; b < b1; ++b) {
+        const int64_t ne = S.blk_ev[(size_t)b + 1] - S.blk_ev[(size_t)b];
+        const int64_t nt = S.blk_touch[(size_t)b + 1] - S.blk_touch[(size_t)b];
+        most = std::max(most, events_df_smem_bytes(ne, nt, h->nc));
+      }
+      h->day_nblk[(size_t)d] = b1 - b0;
+      h->day_df[(size_t)d] = (most <= kEventsSmemLimit) ? (int32_t)most : 0;
     }
   }
   h->day_smem.assign((size_t)T, 0);
@@ -673,7 +790,7 @@ sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days,
     return fail(nullptr, SIM_E_INVALID_ARG, "bad n_nodes / model / max_days");
   Schedule S;
   sim_status st = build_schedule(nullptr, n_nodes, model == SIM_SISE3 ? 3 : 1, max_days, n, day, kind,
-                                 node, dest, count, cls, S);
+                                 node, dest, count, cls, 1, S);
   if (st != SIM_OK) return st;
   if (order) std::memcpy(order, S.order.data(), S.order.size() * 8);
   if (level) std::memcpy(level, S.level.data(), S.level.size() * 4);
@@ -701,8 +818,8 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
   EvDfArgs df{};
   df.counts = h->d_counts; df.rec = h->d_rec_df; df.wait = h->d_wait_df; df.thr_off = h->d_thr_off;
-  df.day_ev = h->d_day_ev; df.touched = h->d_touched; df.day_touch = h->d_day_touch; df.ctr = h->d_ctr;
-  df.day_heavy = h->d_day_heavy;
+  df.touched = h->d_touched_df; df.day_blk = h->d_day_blk; df.blk_ev = h->d_blk_ev;
+  df.blk_touch = h->d_blk_touch; df.blk_thr = h->d_blk_thr; df.blk_heavy = h->d_blk_heavy; df.ctr = h->d_ctr;
   df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;
@@ -713,6 +830,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
     if (h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]) {
       if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
         df.day = d;
+        df.nblk = h->day_nblk[(size_t)d];
         df.smem_bytes = h->day_df[(size_t)d];
         CK(h, traced(h, 1, st, [&] { return launch_events_day_df(df, h->n_age, st); }), "event step launch");
       } else if (h->event_variant != 1 && h->day_smem[(size_t)d] > 0) {

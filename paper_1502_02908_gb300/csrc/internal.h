@@ -94,19 +94,22 @@ constexpr int kDfPublishSampling = 2;     // a later transfer into its node wait
 constexpr int kDfPublishAdd = 4;          // a later sampling of its destination waits on it
 struct EvDfArgs {
   int32_t* counts;
-  const int4* rec;            // per day: grouped by owner thread, input order within
+  const int4* rec;            // per block: grouped by owner thread, input order within
   const int4* wait;           // {adds into src before it, samplings of dst before it, flags, 0}
-  const int32_t* thr_off;     // [max_days][kDfThreads + 1]
-  const int32_t* day_heavy;   // [max_days] warps whose lane 0 owns one heavy node
-  const int32_t* day_ev;      // [max_days + 1] first record of each day
-  const int32_t* touched;
-  const int32_t* day_touch;
+  const int32_t* thr_off;     // per block: event offsets of owner threads 0..nthr (block-relative)
+  const int32_t* touched;     // node ids per block slot
+  const int32_t* day_blk;     // [max_days + 1] first block of each day
+  const int32_t* blk_ev;      // [blocks + 1] first record of each block
+  const int32_t* blk_touch;   // [blocks + 1] first node of each block
+  const int32_t* blk_thr;     // [blocks + 1] first thread offset of each block
+  const int32_t* blk_heavy;   // [blocks] warps whose lane 0 owns one heavy node
   unsigned long long* ctr;
   int32_t* err;
   uint64_t seed;
   int32_t rep_base;
   int32_t N, R, Nc;
   int32_t day;
+  int32_t nblk;               // blocks per replicate this day
   int32_t underflow_error;
   int32_t smem_bytes;
   int32_t spin_limit;
