@@ -221,12 +221,19 @@ int32_t sim_warp_nodes(const sim_handle* h);
 
 /* Execution options (results never depend on them):
  *   SIM_OPT_WARP_THRESHOLD: as sim_tune.
+ *   SIM_OPT_CLOCK_MARGIN: k in [0, 17].  The stochastic step (outside score
+ *     mode) first runs each node-day with a binary32 clock accumulated in fixed
+ *     point, whose distance to the binary64 clock of Eq. (numstep3) is bounded
+ *     below 2^-17 of a day; a stop/continue decision within 2^-k of the day's end
+ *     reruns the node-day with the exact binary64 arithmetic.  k = 17 (default)
+ *     is the tightest safe margin; smaller k only reruns more node-days; 0 runs
+ *     every node-day exactly.  Values outside [0, 17]: SIM_E_INVALID_ARG.
  *   SIM_OPT_LAUNCH: how sim_run_days issues a call's days -- SIM_LAUNCH_STREAM
  *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
  *     sequence captured once as a CUDA graph, keyed by start day and day count,
  *     and replayed), SIM_LAUNCH_PERSISTENT (one persistent batch-kernel launch,
  *     synchronous).  Tracing (sim_profile) always uses stream launches. */
-enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2 };
+enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3 };
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 
@@ -263,6 +270,12 @@ sim_status sim_profile_read(sim_handle* h, double* ms, int64_t* launches);
  * -log(u) for u = (2 j + 1) 2^-53 on the GPU, for n device inputs j (uint64)
  * into n device doubles.  Synchronous. */
 sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n);
+
+/* Test hook (not part of the result): the binary32 -log(u) that the
+ * speculative clock of the stochastic step uses (relative error below 2^-20 by
+ * construction), for n device inputs j into n device floats.  The paper has no
+ * counterpart; it exists so that tests can check that bound.  Synchronous. */
+sim_status sim_debug_neglog_f32(const uint64_t* j_dev, float* out_dev, int64_t n);
 
 /* Test hook: the library's integer-pipe IEEE division x / y for positive
  * operands, and the reference IEEE division, on n inputs: where = SIM_HOST runs

@@ -77,6 +77,7 @@ def load_library(build_if_missing: bool = True):
             "sim_reset": [vp, i32],
             "sim_schedule_events": [i32, i32, i32, i64, pi32, pi32, pi32, pi32, pi32, pi32, pi64, pi32, pi64],
             "sim_debug_neglog": [vp, vp, i64],
+            "sim_debug_neglog_f32": [vp, vp, i64],
             "sim_debug_div": [vp, vp, vp, vp, i64, i32],
             "sim_debug_schedule": [vp, pi64, pi32],
             "sim_profile": [vp, i32],
@@ -263,6 +264,10 @@ class Sim:
     def set_launch(self, mode):
         _check(self.L, self.h, self.L.sim_set_option(self.h, 2, self.LAUNCH[mode]))
 
+    def set_clock_margin(self, k):
+        """Speculative clock margin 2^-k, k in [0, 17] (0: exact clock only)."""
+        _check(self.L, self.h, self.L.sim_set_option(self.h, 3, int(k)))
+
     def profile(self, enable=True):
         _check(self.L, self.h, self.L.sim_profile(self.h, 1 if enable else 0))
 
@@ -306,4 +311,10 @@ def debug_div(x, y, out, ref, n, device):
 def debug_neglog(j_dev_ptr, out_dev_ptr, n):
     L = load_library()
     st = L.sim_debug_neglog(ctypes.c_void_p(j_dev_ptr), ctypes.c_void_p(out_dev_ptr), int(n))
+    _check(L, None, st)
+
+
+def debug_neglog_f32(j_dev_ptr, out_dev_ptr, n):
+    L = load_library()
+    st = L.sim_debug_neglog_f32(ctypes.c_void_p(j_dev_ptr), ctypes.c_void_p(out_dev_ptr), int(n))
     _check(L, None, st)

@@ -44,6 +44,8 @@ struct sim_handle {
   int32_t* d_order = nullptr;       // node order of the stochastic step
   int32_t n_big = 0;                // leading nodes of the order simulated one per warp
   int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
+  int32_t clock_margin_log2 = 17;   // speculative clock margin 2^-k (0: exact clock only)
+  int32_t sm_count = 1;             // SMs of the handle's device
   double* d_phi0 = nullptr;
   // event schedule
   bool events_loaded = false;
@@ -203,6 +205,8 @@ SsaArgs ssa_args(sim_handle* h) {
   a.order = h->d_order;
   a.n_big = h->n_big;
   a.warp_blocks = (h->n_big + 7) / 8;
+  a.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
+  a.sm_count = h->sm_count;
   return a;
 }
 
@@ -227,17 +231,6 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   int32_t nb = 0;
   if (!(h->cfg.flags & SIM_FLAG_SCORE))
     while (nb < N && herd[order[nb]] >= thr) ++nb;
-  // deal the warp-path nodes round-robin over their blocks (8 warps each), so the
-  // largest herds land in different blocks (and SMs) instead of sharing one
-  // (whole blocks only: the few smallest warp-path herds past a multiple of 8
-  // go to the thread path)
-  if (nb > 8) {
-    nb = nb / 8 * 8;
-    const int nblk = nb / 8;
-    std::vector<int32_t> dealt((size_t)nb);
-    for (int k = 0; k < nb; ++k) dealt[(size_t)(k % nblk) * 8 + k / nblk] = order[k];
-    std::copy(dealt.begin(), dealt.end(), order.begin());
-  }
   if (!h->d_order) CK(h, dalloc(&h->d_order, (size_t)N), "node order allocation");
   CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_big = nb;
@@ -661,6 +654,12 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     }
   }
   cudaError_t e = cudaSuccess;
+  {
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    h->sm_count = sms > 0 ? sms : 1;
+  }
   const size_t stats = (size_t)R * (cfg->max_days > 0 ? cfg->max_days : 1);
   if (e == cudaSuccess) e = dalloc(&h->d_counts, n_counts(h));
   if (e == cudaSuccess) e = dalloc(&h->d_phi, n_phi(h));
@@ -1213,6 +1212,13 @@ sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
       free_graph(h);
       h->launch_mode = (int32_t)value;
       return SIM_OK;
+    case SIM_OPT_CLOCK_MARGIN:
+      if (value < 0 || value > 17)
+        return fail(h, SIM_E_INVALID_ARG, "clock margin exponent %lld outside [0, 17]", (long long)value);
+      CK(h, cudaDeviceSynchronize(), "synchronize");
+      free_graph(h);
+      h->clock_margin_log2 = (int32_t)value;
+      return SIM_OK;
     default:
       return fail(h, SIM_E_INVALID_ARG, "unknown option %d", option);
   }
@@ -1252,6 +1258,13 @@ const char* sim_last_error(const sim_handle* h) {
 sim_status sim_debug_neglog(const uint64_t* j_dev, double* out_dev, int64_t n) {
   if (n < 0 || (n > 0 && (!j_dev || !out_dev))) return SIM_E_INVALID_ARG;
   cudaError_t e = launch_debug_neglog(j_dev, out_dev, n, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+}
+
+sim_status sim_debug_neglog_f32(const uint64_t* j_dev, float* out_dev, int64_t n) {
+  if (n < 0 || (n > 0 && (!j_dev || !out_dev))) return SIM_E_INVALID_ARG;
+  cudaError_t e = launch_debug_neglog_f32(j_dev, out_dev, n, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   return e == cudaSuccess ? SIM_OK : SIM_E_CUDA;
 }

@@ -43,6 +43,8 @@ struct SsaArgs {
   const int32_t* order;       // node order: first n_big nodes warp-cooperative, the rest per thread (NULL: identity)
   int32_t n_big;              // nodes simulated one per warp
   int32_t warp_blocks;        // blocks (of 8 warps) given to them
+  uint64_t clock_margin;      // Q62 margin of the speculative binary32 clock (0: exact clock only)
+  int32_t sm_count;           // SMs of the device (grid of the dealt mapping)
 };
 
 // One scheduled event, 16 bytes: node, dest, position in the day-stable order,
@@ -129,6 +131,7 @@ cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
 // After the last day of a call: phi update (post-event mode) and statistics of day a.day.
 cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
 cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st);
+cudaError_t launch_debug_neglog_f32(const uint64_t* j, float* out, int64_t n, cudaStream_t st);
 
 // Reverse sweep of the phi recursion over days [0, ndays) for every (r, v):
 // lambda_d = c_d + (1 - beta_d) lambda_{d+1}; adds -lambda_{d+1} phi_d to the

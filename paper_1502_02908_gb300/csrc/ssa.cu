@@ -10,6 +10,8 @@
 //   a0 = A_1 or (A_1 + A_2) + A_3;  tau = E / a0;  stop when t + tau >= 1;
 //   r = a0 * u2 selects inf_1, rec_1, inf_2, ... by left-to-right thresholds.
 // IEEE binary64 operations are explicit intrinsics (never contracted).
+#include <algorithm>
+
 #include "ssa_device.cuh"
 
 namespace episim {
@@ -22,8 +24,36 @@ __global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_r
   node_day_block<NA, SCORE, MODE>(a, r, bx);
 }
 
+template <int NA>
+__global__ void __launch_bounds__(256, 2) k_node_day_dealt(SsaArgs a) {
+  node_day_dealt<NA>(a);
+}
+
 template <int MODE>
 static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
+  if (MODE == 0 && !score && a.order) {
+    // resident grid: G = SMs x (blocks of 8 warps an SM holds, fewer when the
+    // units do not fill them); W warps per block, each looping over its units
+    static int resident[2] = {0, 0};
+    const int which = n_age == 1 ? 0 : 1;
+    if (!resident[which]) {
+      int nb = 0;
+      cudaError_t e = n_age == 1
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<1>, 256, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<3>, 256, 0);
+      if (e != cudaSuccess) return e;
+      resident[which] = nb > 0 ? nb : 1;
+    }
+    const int64_t units = (int64_t)a.R * (a.n_big + (a.N - a.n_big + 31) / 32);
+    if (units == 0) return cudaSuccess;
+    const int64_t sms = a.sm_count > 0 ? a.sm_count : 1;
+    const int64_t per_sm = std::min<int64_t>(resident[which], (units + sms * 8 - 1) / (sms * 8));
+    const int64_t G = sms * per_sm;
+    const int W = (int)std::min<int64_t>(8, (units + G - 1) / G);
+    if (n_age == 1) k_node_day_dealt<1><<<(unsigned)G, 32 * W, 0, st>>>(a);
+    else k_node_day_dealt<3><<<(unsigned)G, 32 * W, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const int warp_blocks = (MODE == 0 && !score) ? a.warp_blocks : 0;
   const int n_thread = a.N - ((MODE == 0 && !score && a.order) ? a.n_big : 0);
   const int bpr = warp_blocks + (n_thread + 255) / 256;
@@ -51,6 +81,11 @@ __global__ void k_debug_neglog(const uint64_t* j, double* out, int64_t n) {
   if (i < n) out[i] = neglog_u(j[i]);
 }
 
+__global__ void k_debug_neglog_f32(const uint64_t* j, float* out, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = neglog_f32(j[i]);
+}
+
 __global__ void k_debug_div(const double* x, const double* y, double* out, double* ref, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) { out[i] = div_pos(x[i], y[i]); ref[i] = __ddiv_rn(x[i], y[i]); }
@@ -65,6 +100,12 @@ cudaError_t launch_debug_div(const double* x, const double* y, double* out, doub
 cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_debug_neglog<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(j, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_neglog_f32(const uint64_t* j, float* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_debug_neglog_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(j, out, n);
   return cudaGetLastError();
 }
 

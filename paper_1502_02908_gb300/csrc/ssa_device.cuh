@@ -137,22 +137,7 @@ __device__ __forceinline__ uint32_t ssa_node_day(const DevParams& p, uint64_t se
 }
 
 // ---------------------------------------------------------------------------
-// Warp-cooperative direct method for one node-day (large herds).  Identical
-// results to ssa_node_day, bit for bit, in four phases per block of 32 draws:
-//  1. lane l computes draw k0 + l: Philox, E = -log(u1), u2 (independent of the
-//     state, so all 32 in parallel);
-//  2. every lane runs the embedded jump chain (which transition each draw
-//     fires) over the block in FP32.  Each FP32 comparison is decisive only when
-//     the operands are at least 64 float ulps apart (relative gap >= 2^-18,
-//     beyond the <= 2^-20 error of the FP32 rates, sums and product against the
-//     specification's binary64 values); otherwise that draw is decided with the
-//     specification's exact binary64 arithmetic;
-//  3. lane l computes the exact binary64 propensity sum a0 of its draw's state
-//     and tau_l = E_l / a0;
-//  4. the binary64 clock t + tau_l runs in draw order; the first draw reaching
-//     t >= 1 ends the day in the state before that draw.
-// On GB300 the serial chain of the per-thread method costs ~8 FP64 instructions
-// (64 cycles each) plus a divide per transition; here it is FP32 and integer.
+// binary32 helpers of the speculative methods below.
 
 __device__ __forceinline__ float trunc_to_f32(double x) {
   // positive normal double within float range -> float with the top 23 fraction bits
@@ -172,6 +157,132 @@ __device__ __forceinline__ int cmp_f32(float a, float b) {
   if (ia < 0x00800000 || ib < 0x00800000) return 0;  // zero or subnormal: exact path
   const int d = ia - ib;
   return d <= -64 ? -1 : (d >= 64 ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Speculative binary32 clock.  The specification's clock is the binary64 chain
+// t_{k+1} = fl(t_k + fl(E_k / a0_k)) and a day ends at the first k with
+// t_{k+1} >= 1.  Here tau~_k = E~_k / a0~_k in binary32 (E~ the binary32 -log of
+// the draw below, a0~ the binary32 propensity sum) is accumulated exactly in Q62
+// fixed point.  With u = 2^-24: a0~ is within 6u of a0 (constants truncated to
+// binary32: 2u, product u, three sums u each), E~ within 16u of E, and the
+// division adds u, so tau~_k is within rho = 23u < 2^-19.4 of tau_k.  At a
+// decision the Q62 sum is below 2.5, hence within 2.5 rho (< 2^-18.1) plus
+// k (2^-53 + 2^-62) of the binary64 chain for k < 2^24: a margin of 2^-17 makes
+// "sum >= 1 + margin" a certain stop and "sum + margin < 1" a certain continue;
+// anything between is handed to the exact binary64 method.  The stochastic
+// choices are taken in binary32 only when decisive (below) and in binary64
+// otherwise, so the result is the specification's, bit for bit.
+constexpr uint64_t kQ62One = 1ull << 62;
+constexpr uint64_t kClockMargin = kQ62One >> 17;   // largest allowed margin exponent: 17
+constexpr uint32_t kSpecMaxSteps = 1u << 24;
+
+// binary32 of m 2^-53 for 1 <= m < 2^53, rounded to nearest (ties away): within u.
+__device__ __forceinline__ float f32_of_q53(uint64_t m) {
+  const int lz = __clzll(m);
+  const uint32_t top = ((uint32_t)((m << lz) >> 39) + 1u) >> 1;   // 24 bits, or 2^24 on carry
+  const uint32_t e = (uint32_t)(137 - lz) + (top >> 24);
+  return __uint_as_float((e << 23) | (top & 0x7FFFFFu));
+}
+
+// binary32 -log(u) for u = (2j+1) 2^-53, within 16u of -log(u).  Below 1/sqrt2,
+// u = f 2^e with f in [1/sqrt2, sqrt2) and log u = e ln2 + 2 atanh((f-1)/(f+1));
+// from 1/sqrt2 on, log u = log(1 - v) = 2 atanh(-v/(2-v)) with v = 1 - u taken
+// exactly from the integers.  Either way |s| <= 0.1716 and atanh(s)/s is the
+// series 1 + s^2/3 + s^4/5 + s^6/7 + s^8/9 (remainder below 2^-28).  Error
+// budget: the argument's rounding (u, amplified at most 2x near the split),
+// f + 1 or 2 - v and the quotient (u each), the series (2u), the product and the
+// final sum (u each, the sum's cancellation amplifying the e ln2 part at most 2x).
+__device__ __forceinline__ float neglog_f32(uint64_t j) {
+  constexpr uint64_t kSplit = 3184525836262886ull;   // first j with (2j+1) 2^-53 >= 1/sqrt2
+  const bool hi = j >= kSplit;
+  const float x = f32_of_q53(hi ? ((((1ull << 52) - j) << 1) - 1ull) : ((j << 1) | 1ull));
+  // low side: f = mantissa of x in [1/sqrt2, sqrt2), e = its exponent
+  const uint32_t b = __float_as_uint(x);
+  float f = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+  int e = (int)(b >> 23) - 127;
+  if (f >= 1.41421356f) { f = __fmul_rn(f, 0.5f); e += 1; }
+  const float num = hi ? -x : __fsub_rn(f, 1.0f);
+  const float den = hi ? __fsub_rn(2.0f, x) : __fadd_rn(f, 1.0f);
+  const float sc = hi ? 0.0f : (float)e;
+  const float sq = __fdiv_rn(num, den);
+  const float z = __fmul_rn(sq, sq);
+  float poly = __fadd_rn(0.142857149f, __fmul_rn(z, 0.111111112f));
+  poly = __fadd_rn(0.200000003f, __fmul_rn(z, poly));
+  poly = __fadd_rn(0.333333343f, __fmul_rn(z, poly));
+  poly = __fadd_rn(1.0f, __fmul_rn(z, poly));
+  const float lg = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, sq), poly), __fmul_rn(sc, 0.693147182f));
+  return -lg;
+}
+
+// floor(f 2^62) for 0 <= f <= 1.5 (f normal or subnormal).
+__device__ __forceinline__ uint64_t q62_of(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)(b >> 23);
+  const uint64_t m = e ? (uint64_t)((b & 0x7FFFFFu) | 0x800000u) : (uint64_t)(b & 0x7FFFFFu);
+  const int sh = (e ? e : 1) - 127 - 23 + 62;
+  return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+}
+
+// binary32 copies of a node-day's rate constants; false when the binary32 bounds
+// above do not hold (a constant outside [2^-100, 2^60] or a herd of 2^22 or more).
+template <int NA>
+__device__ __forceinline__ bool spec_constants(const DevParams& p, const double (&cinf)[NA], const int32_t (&x)[2 * NA],
+                                               float (&cinff)[NA], float (&gamf)[NA]) {
+  bool ok = true;
+  int32_t herd = 0;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    for (int q = 0; q < 2; ++q) {
+      const double c = q ? p.gam[j] : cinf[j];
+      const int e = (int)(double_bits(c) >> 52) - 1023;
+      if (pos(c) && (e < -100 || e > 60)) ok = false;
+    }
+    cinff[j] = trunc_to_f32(cinf[j]);
+    gamf[j] = trunc_to_f32(p.gam[j]);
+    herd += x[2 * j] + x[2 * j + 1];
+  }
+  return ok && herd < (1 << 22);
+}
+
+// binary32 selection thresholds of state x, in the specification's order and
+// rounding: a_inf,1, P_1, P_1 + a_inf,2, P_2, ...; a0~ = P_NA.  Returns whether
+// any rate is positive (exact, from the counts and constants).
+template <int NA>
+__device__ __forceinline__ bool thresholds_f32(const bool (&cpos)[NA], const bool (&gpos)[NA],
+                                               const float (&cinff)[NA], const float (&gamf)[NA],
+                                               const int32_t (&x)[2 * NA], float (&T)[2 * NA - 1], float& a0f) {
+  bool any = false;
+  float P = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    any = any || (cpos[j] && x[2 * j] > 0) || (gpos[j] && x[2 * j + 1] > 0);
+    const float aif = __fmul_rn(cinff[j], small_int_to_f32(x[2 * j]));
+    const float A = __fadd_rn(aif, __fmul_rn(gamf[j], small_int_to_f32(x[2 * j + 1])));
+    if (j == 0) { T[0] = aif; P = A; }
+    else { T[2 * j] = __fadd_rn(P, aif); P = __fadd_rn(P, A); }
+    if (2 * j + 1 < 2 * NA - 1) T[(2 * j + 1 < 2 * NA - 1) ? 2 * j + 1 : 0] = P;
+  }
+  a0f = P;
+  return any;
+}
+
+// The transition the draw r = a0 u2 fires, from binary32 values: r falls in the
+// k-th of the intervals cut by the thresholds (zero-width intervals, from zero
+// rates, are never chosen), so k = 2*class + (1 if recovery) is the number of
+// thresholds below r.  Decided only when every comparison is decisive (exactly
+// zero thresholds always are); otherwise -1.
+template <int NA>
+__device__ __forceinline__ int choice_count_f32(const float (&T)[2 * NA - 1], float rf) {
+  int c = 0;
+  bool amb = false;
+#pragma unroll
+  for (int i = 0; i < 2 * NA - 1; ++i) {
+    const int cmp = (T[i] == 0.0f) ? 1 : cmp_f32(rf, T[i]);
+    amb = amb || cmp == 0;
+    c += cmp > 0 ? 1 : 0;
+  }
+  return amb ? -1 : c;
 }
 
 // Exact decision of the specification for the state x and uniform u2: returns
@@ -208,94 +319,171 @@ __device__ __forceinline__ int exact_choice(const double (&cinf)[NA], const DevP
   return out;
 }
 
+// The direct method for one node-day with the speculative clock (one thread):
+// transitions fired, or -1 when a clock decision was too close to call (the
+// caller then reruns the node-day with ssa_node_day from the same state).  One
+// exit test per step; the draw of step k + 1 is computed during step k (it does
+// not depend on the state), so its latency overlaps the state-dependent chain.
 template <int NA>
-__device__ __forceinline__ uint32_t ssa_warp_node_day(const DevParams& p, uint64_t seed, uint32_t rep, int v,
-                                                      int day, double phi, NodeState<NA>& s) {
+__device__ __forceinline__ int32_t ssa_node_day_spec(const DevParams& p, uint64_t seed, uint32_t rep, int v, int day,
+                                                     const double (&cinf)[NA], const float (&cinff)[NA],
+                                                     const float (&gamf)[NA], uint64_t margin, NodeState<NA>& s) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  bool cpos[NA], gpos[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) { cpos[j] = pos(cinf[j]); gpos[j] = pos(p.gam[j]); }
+  uint64_t tq = 0;
+  uint4 wn = philox10(make_uint4((uint32_t)v, (uint32_t)day, 0u, rep), k0, k1);
+  for (uint32_t k = 0;; ++k) {
+    float T[2 * NA - 1], a0f;
+    const bool any = thresholds_f32<NA>(cpos, gpos, cinff, gamf, s.x, T, a0f);
+    const uint4 w = wn;
+    wn = philox10(make_uint4((uint32_t)v, (uint32_t)day, k + 1u, rep), k0, k1);
+    const float Ef = neglog_f32(((((uint64_t)w.y) << 32) | w.x) >> 12);
+    const float u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
+    int choice = choice_count_f32<NA>(T, __fmul_rn(a0f, u2f));
+    const uint64_t sq = tq + q62_of(fminf(__fdiv_rn(Ef, a0f), 1.5f));
+    if (!any || sq >= kQ62One + margin) return (int32_t)k;
+    if (sq + margin >= kQ62One || k + 1u >= kSpecMaxSteps) return -1;
+    if (choice < 0) choice = exact_choice<NA>(cinf, p, s.x, uniform_open(w.z, w.w));
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      if (2 * j == choice) { s.x[2 * j] -= 1; s.x[2 * j + 1] += 1; }
+      if (2 * j + 1 == choice) { s.x[2 * j + 1] -= 1; s.x[2 * j] += 1; }
+    }
+    tq = sq;
+  }
+}
+
+// Warp-cooperative direct method for one node-day (large herds), all 32 lanes
+// together; phases per block of 32 draws:
+//  1. lane l computes draw k0 + l: Philox, E = -log(u1), u2 (independent of the
+//     state, so all 32 in parallel);
+//  2. the embedded jump chain (which transition each draw fires): binary32
+//     comparisons decide only when the operands are at least 64 float ulps apart
+//     (relative gap >= 2^-18, beyond the <= 2^-20 error of the binary32 rates,
+//     sums and product against the specification's binary64 values); otherwise
+//     that draw is decided with the specification's binary64 arithmetic.  With
+//     CLOCK > 0 all lanes decide at once by the fixed-point iteration below; with
+//     CLOCK = 0 the lanes walk the chain in draw order;
+//  3-4. the clock.  CLOCK = 2: lane l forms tau~_l from its draw's binary32
+//     propensity sum; an inclusive warp scan of the Q62 values gives the clock
+//     after every draw, and the first draw that is not a certain continue ends
+//     the day (certain stop) or returns -1 (too close to call).  CLOCK = 1: the
+//     same scan of the exact binary64 tau_l (a0 of the lane's state, the exact
+//     -log), whose sum is within (k + 2) 2^-53 of the binary64 chain, so only a
+//     decision within that of the day's end returns -1.  CLOCK = 0: the binary64
+//     clock t + tau_l runs in draw order; the first draw reaching t >= 1 ends the
+//     day in the state before that draw.
+// Returns the transitions fired, or -1 (CLOCK > 0) for the caller to rerun the
+// node-day with a smaller CLOCK from the same state.
+// floor(x 2^62) for a non-negative binary64 x <= 1.5 (exact bits).
+__device__ __forceinline__ uint64_t q62_of_f64(double x) {
+  const uint64_t b = double_bits(x);
+  const int e = (int)(b >> 52);
+  const uint64_t m = e ? ((b & ((1ull << 52) - 1)) | (1ull << 52)) : (b & ((1ull << 52) - 1));
+  const int sh = (e ? e : 1) - 1023 - 52 + 62;
+  return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+}
+
+template <int NA, int CLOCK>
+__device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_t seed, uint32_t rep, int v, int day,
+                                                     double phi, uint64_t margin, NodeState<NA>& s) {
   constexpr int NC = 2 * NA;
   const int lane = threadIdx.x & 31;
   const uint32_t full = 0xffffffffu;
   double cinf[NA];
   float cinff[NA], gamf[NA];
-  bool spec_ok = true;
-  int32_t herd = 0;
 #pragma unroll
-  for (int j = 0; j < NA; ++j) {
-    cinf[j] = __dmul_rn(p.ups[j], phi);
-    for (int q = 0; q < 2; ++q) {
-      const double c = q ? p.gam[j] : cinf[j];
-      const int e = (int)(double_bits(c) >> 52) - 1023;
-      if (pos(c) && (e < -100 || e > 60)) spec_ok = false;
-    }
-    cinff[j] = trunc_to_f32(cinf[j]);
-    gamf[j] = trunc_to_f32(p.gam[j]);
-    herd += s.x[2 * j] + s.x[2 * j + 1];
-  }
-  if (herd >= (1 << 22)) spec_ok = false;
+  for (int j = 0; j < NA; ++j) cinf[j] = __dmul_rn(p.ups[j], phi);
+  constexpr bool SPEC = CLOCK == 2;
+  const bool spec_ok = spec_constants<NA>(p, cinf, s.x, cinff, gamf);
+  if (SPEC && !spec_ok) return -1;
+  bool cpos[NA], gpos[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) { cpos[j] = pos(cinf[j]); gpos[j] = pos(p.gam[j]); }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   double t = 0.0;
-  uint32_t fired = 0;
+  uint64_t tq = 0;
+  int32_t fired = 0;
   for (uint32_t kb = 0;; kb += 32) {
+    if (CLOCK > 0 && kb >= kSpecMaxSteps) return -1;
     // 1. draws of this block
     const uint4 w = philox10(make_uint4((uint32_t)v, (uint32_t)day, kb + (uint32_t)lane, rep), k0, k1);
-    const double E = neglog_u(((((uint64_t)w.y) << 32) | w.x) >> 12);
+    const uint64_t j52 = ((((uint64_t)w.y) << 32) | w.x) >> 12;
+    double E = 0.0;
+    float Ef = 0.0f;
+    if (CLOCK == 2) Ef = neglog_f32(j52);
+    else E = neglog_u(j52);
     const double u2 = uniform_open(w.z, w.w);
-    const float u2f = trunc_to_f32(u2);
+    const float u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
     // 2. embedded chain
     int32_t x[NC], xs[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) { x[c] = s.x[c]; xs[c] = x[c]; }
+    float a0l = 0.0f;
     int stop_at = 32;
-    for (int l = 0; l < 32; ++l) {
+    if (CLOCK > 0) {
+      // Fixed-point iteration over the lanes: every lane takes as its state the
+      // block's start plus the transitions currently guessed for the lanes before
+      // it and decides its own draw there.  A lane whose predecessors' guesses are
+      // right decides right, so each round confirms at least one more leading lane
+      // and the iteration stops, after at most 33 rounds, with every guess equal to
+      // the sequential chain's choice.  Guesses are net infections per class,
+      // 10-bit fields of one int (|count| <= 32), summed by a warp scan.
+      int ch = -3;                                 // -3: no guess yet, -2: a0 = 0 here
+      for (int it = 0; it <= 32; ++it) {
+        const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
+        int32_t inc = enc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(full, inc, o);
+          if (lane >= o) inc += y;
+        }
+        int32_t rest = inc - enc;                  // exclusive prefix
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
+          rest = (rest - d) >> 10;
+          xs[2 * j] = x[2 * j] - d;
+          xs[2 * j + 1] = x[2 * j + 1] + d;
+        }
+        float T[2 * NA - 1], a0f;
+        int nc = -2;
+        if (thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f)) {
+          a0l = a0f;
+          nc = spec_ok ? choice_count_f32<NA>(T, __fmul_rn(a0f, u2f)) : -1;
+          if (nc < 0) nc = exact_choice<NA>(cinf, p, xs, u2);
+        }
+        const unsigned diff = __ballot_sync(full, nc != ch);
+        ch = nc;
+        if (diff == 0u) break;
+      }
+      const unsigned stops = __ballot_sync(full, ch == -2);
+      stop_at = stops ? __ffs(stops) - 1 : 32;
+      // state after the block: the stopping lane's, or the last lane's after its draw
+      const int src = stop_at < 32 ? stop_at : 31;
+      int32_t after[NC];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int dj = (ch >= 0 && (ch >> 1) == j) ? ((ch & 1) ? -1 : 1) : 0;
+        after[2 * j] = xs[2 * j] - (stop_at < 32 ? 0 : dj);
+        after[2 * j + 1] = xs[2 * j + 1] + (stop_at < 32 ? 0 : dj);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) x[c] = __shfl_sync(full, after[c], src);
+    }
+    for (int l = 0; l < (CLOCK > 0 ? 0 : 32); ++l) {
       if (l == lane) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) xs[c] = x[c];
       }
-      bool posA[NA], posI[NA];
-      float aif[NA], Pf[NA];
-      bool any = false;
-#pragma unroll
-      for (int j = 0; j < NA; ++j) {
-        posI[j] = pos(cinf[j]) && x[2 * j] > 0;
-        const bool posR = pos(p.gam[j]) && x[2 * j + 1] > 0;
-        posA[j] = posI[j] || posR;
-        any = any || posA[j];
-        aif[j] = __fmul_rn(cinff[j], small_int_to_f32(x[2 * j]));
-        const float arf = __fmul_rn(gamf[j], small_int_to_f32(x[2 * j + 1]));
-        const float Af = __fadd_rn(aif[j], arf);
-        Pf[j] = (j == 0) ? Af : __fadd_rn(Pf[j > 0 ? j - 1 : 0], Af);
-      }
+      float T[2 * NA - 1], a0f;
+      const bool any = thresholds_f32<NA>(cpos, gpos, cinff, gamf, x, T, a0f);
       if (!any) { stop_at = l; break; }           // a0 = 0: nothing can fire
+      if (l == lane) a0l = a0f;
       const float ul = __shfl_sync(full, u2f, l);
-      int choice = -1;
-      if (spec_ok) {
-        const float rf = __fmul_rn(Pf[NA - 1], ul);
-        int cls = -1, last = -1;
-        bool amb = false;
-#pragma unroll
-        for (int j = 0; j < NA; ++j) {
-          if (cls < 0 && !amb && posA[j]) {
-            last = j;
-            const int cmp = cmp_f32(rf, Pf[j]);
-            if (cmp == 0) amb = true;
-            else if (cmp < 0) cls = j;
-          }
-        }
-        if (!amb) {
-          if (cls < 0) cls = last;
-#pragma unroll
-          for (int j = 0; j < NA; ++j) {
-            if (j != cls) continue;
-            const bool posR = pos(p.gam[j]) && x[2 * j + 1] > 0;
-            if (!posI[j]) choice = 2 * j + 1;
-            else if (!posR) choice = 2 * j;
-            else {
-              const float thrf = (j == 0) ? aif[0] : __fadd_rn(Pf[j > 0 ? j - 1 : 0], aif[j]);
-              const int cmp = cmp_f32(rf, thrf);
-              if (cmp != 0) choice = 2 * j + (cmp < 0 ? 0 : 1);
-            }
-          }
-        }
-      }
+      int choice = spec_ok ? choice_count_f32<NA>(T, __fmul_rn(a0f, ul)) : -1;
       if (choice < 0) {                            // too close to call: exact arithmetic
         const double ud = __shfl_sync(full, u2, l);
         choice = exact_choice<NA>(cinf, p, x, ud);
@@ -306,23 +494,53 @@ __device__ __forceinline__ uint32_t ssa_warp_node_day(const DevParams& p, uint64
         if (2 * j + 1 == choice) { x[2 * j + 1] -= 1; x[2 * j] += 1; }
       }
     }
-    // 3. exact a0 and tau of each lane's draw
-    double P = 0.0;
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const double ainf = __dmul_rn(cinf[j], i2d_exact(xs[2 * j]));
-      const double arec = __dmul_rn(p.gam[j], i2d_exact(xs[2 * j + 1]));
-      const double A = __dadd_rn(ainf, arec);
-      P = (j == 0) ? A : __dadd_rn(P, A);
-    }
-    const double tau = (lane < stop_at && pos(P)) ? div_pos(E, P) : 0.0;
-    // 4. clock in draw order
     int end_at = -1;
-    for (int l = 0; l < stop_at; ++l) {
-      const double tl = __shfl_sync(full, tau, l);
-      const double tn = __dadd_rn(t, tl);
-      if (le_nonneg(1.0, tn)) { end_at = l; break; }
-      t = tn;
+    double tau = 0.0;
+    if (CLOCK < 2) {
+      // 3. exact a0 and tau of each lane's draw
+      double P = 0.0;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const double ainf = __dmul_rn(cinf[j], i2d_exact(xs[2 * j]));
+        const double arec = __dmul_rn(p.gam[j], i2d_exact(xs[2 * j + 1]));
+        const double A = __dadd_rn(ainf, arec);
+        P = (j == 0) ? A : __dadd_rn(P, A);
+      }
+      tau = (lane < stop_at && pos(P)) ? div_pos(E, P) : 0.0;
+    }
+    if (CLOCK > 0) {
+      // 4. Q62 scan of tau~ (binary32) or tau (binary64), certain decisions only
+      const bool valid = lane < stop_at;
+      uint64_t sc = 0ull, m = margin;
+      if (CLOCK == 2) {
+        sc = valid ? q62_of(fminf(__fdiv_rn(Ef, a0l), 1.5f)) : 0ull;
+      } else {
+        sc = valid ? q62_of_f64(le_nonneg(tau, 1.5) ? tau : 1.5) : 0ull;
+        m = ((uint64_t)kb + (uint64_t)lane + 2ull) << 10;   // (k + 2) 2^-52
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(full, sc, o);
+        if (lane >= o) sc += y;
+      }
+      const uint64_t sl = tq + sc;
+      const unsigned nc = __ballot_sync(full, valid && !(sl + m < kQ62One));
+      if (nc != 0) {
+        const int f = __ffs(nc) - 1;
+        const unsigned st = __ballot_sync(full, valid && sl >= kQ62One + m);
+        if (!((st >> f) & 1u)) return -1;         // too close to call
+        end_at = f;
+      } else {
+        tq = __shfl_sync(full, sl, 31);
+      }
+    } else {
+      // 4. clock in draw order
+      for (int l = 0; l < stop_at; ++l) {
+        const double tl = __shfl_sync(full, tau, l);
+        const double tn = __dadd_rn(t, tl);
+        if (le_nonneg(1.0, tn)) { end_at = l; break; }
+        t = tn;
+      }
     }
     if (end_at >= 0 || stop_at < 32) {
       const int at = end_at >= 0 ? end_at : stop_at;
@@ -333,7 +551,7 @@ __device__ __forceinline__ uint32_t ssa_warp_node_day(const DevParams& p, uint64
 #pragma unroll
         for (int c = 0; c < NC; ++c) s.x[c] = x[c];
       }
-      return fired + (uint32_t)at;
+      return fired + at;
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) s.x[c] = x[c];
@@ -374,12 +592,110 @@ __device__ __forceinline__ void accumulate_score(const SsaArgs& a, const DevPara
 
 // MODE 0: day a.day (prologue for a.day - 1 when a.prologue); MODE 1: finalize
 // after the last day a.day (statistics of a.day; phi update in post-event mode).
-// With a node order (MODE 0), blocks [0, a.warp_blocks) give each warp one of the
-// first a.n_big nodes of the order (warp-cooperative method); the other blocks
-// give each thread one of the remaining nodes.
+// One thread's part of node v of replicate r (warp_role: the whole warp shares
+// node v and lane 0 stores and reports); then the warp's statistics and counters.
+template <int NA, bool SCORE, int MODE>
+__device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bool active, bool warp_role) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t full = 0xffffffffu;
+  unsigned long long sI = 0, sN = 0, fired = 0;
+  const bool do_prologue = (MODE == 1) || a.prologue;
+  const int dprev = (MODE == 1) ? a.day : a.day - 1;
+  const bool owner = !warp_role || lane == 0;     // the thread that stores and reports
+  const DevParams& p = a.params[r];
+  const uint32_t rep = (uint32_t)(a.rep_base + r);
+  double* phip = a.phi + (size_t)r * a.N + v;
+  NodeState<NA> s, s0;
+  double phi = 0.0;
+  int32_t f = 0;
+  if (active) {
+    load_counts<NA>(a, r, v, s);
+    phi = __ldcg(phip);
+    if (do_prologue) {
+      if (owner) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) { sI += (unsigned)s.x[2 * j + 1]; sN += (unsigned)(s.x[2 * j] + s.x[2 * j + 1]); }
+      }
+      if (!a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, dprev, s, phi);
+    }
+    s0 = s;
+    if (MODE == 0 && !warp_role) {
+      f = -1;
+      if (!SCORE && a.clock_margin) {
+        double cinf[NA];
+        float cinff[NA], gamf[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) cinf[j] = __dmul_rn(p.ups[j], phi);
+        if (spec_constants<NA>(p, cinf, s.x, cinff, gamf)) {
+          f = ssa_node_day_spec<NA>(p, a.seed, rep, v, a.day, cinf, cinff, gamf, a.clock_margin, s);
+          if (f < 0) s = s0;
+        }
+      }
+      if (SCORE) {
+        DayTerms T[NA];
+        f = (int32_t)ssa_node_day<NA, true>(p, a.seed, rep, v, a.day, phi, s, T);
+        accumulate_score<NA>(a, p, r, v, phi, T);
+      }
+    }
+  }
+  if (MODE == 0 && !SCORE) {
+    if (warp_role) {
+      if (active) {                                // warp-uniform
+        f = -1;
+        if (a.clock_margin) {
+          f = ssa_warp_node_day<NA, 2>(p, a.seed, rep, v, a.day, phi, a.clock_margin, s);
+          if (f < 0) s = s0;
+        }
+        if (f < 0) {
+          f = ssa_warp_node_day<NA, 1>(p, a.seed, rep, v, a.day, phi, 0, s);
+          if (f < 0) { s = s0; f = ssa_warp_node_day<NA, 0>(p, a.seed, rep, v, a.day, phi, 0, s); }
+        }
+      }
+    } else {
+      // lanes the binary32 clock could not decide (or could not take): the whole
+      // warp runs the binary64 warp method for each of them in turn
+      unsigned need = __ballot_sync(full, active && f < 0);
+      while (need) {
+        const int l = __ffs(need) - 1;
+        need &= need - 1;
+        const int vl = __shfl_sync(full, v, l);
+        const double phil = __shfl_sync(full, phi, l);
+        NodeState<NA> t, t0;
+#pragma unroll
+        for (int c = 0; c < 2 * NA; ++c) t.x[c] = t0.x[c] = __shfl_sync(full, s0.x[c], l);
+        int32_t g = ssa_warp_node_day<NA, 1>(p, a.seed, rep, vl, a.day, phil, 0, t);
+        if (g < 0) { t = t0; g = ssa_warp_node_day<NA, 0>(p, a.seed, rep, vl, a.day, phil, 0, t); }
+        if (lane == l) { s = t; f = g; }
+      }
+    }
+  }
+  if (active) {
+    if (MODE == 0) {
+      if (owner) fired = (unsigned long long)f;
+      if (a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, a.day, s, phi);
+      if (owner) store_counts<NA>(a, r, v, s);
+    }
+    if (owner) *phip = phi;
+  }
+  if (!__any_sync(0xffffffffu, active)) return;
+  fired = warp_sum(fired);
+  sI = warp_sum(sI);
+  sN = warp_sum(sN);
+  if (lane == 0) {
+    if (MODE == 0 && fired) atomicAdd(a.ctr + (size_t)r * 4 + 0, fired);
+    if (do_prologue) {
+      atomicAdd(a.prev_i + (size_t)r * a.max_days + dprev, sI);
+      atomicAdd(a.prev_n + (size_t)r * a.max_days + dprev, sN);
+    }
+  }
+}
+
+// Block-contiguous mapping (the persistent batch kernel, score mode and the
+// finalisation): with a node order (MODE 0), blocks [0, a.warp_blocks) give each
+// warp one of the first a.n_big nodes of the order (warp-cooperative method);
+// the other blocks give each thread one of the remaining nodes.
 template <int NA, bool SCORE, int MODE>
 __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) {
-  const int lane = threadIdx.x & 31;
   const bool warp_role = (MODE == 0) && !SCORE && bx < a.warp_blocks;
   int v;
   bool active;
@@ -393,46 +709,36 @@ __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) 
     active = i + base < a.N;
     v = active ? (a.order && MODE == 0 && !SCORE ? a.order[base + i] : i + base) : 0;
   }
-  unsigned long long sI = 0, sN = 0, fired = 0;
-  const bool do_prologue = (MODE == 1) || a.prologue;
-  const int dprev = (MODE == 1) ? a.day : a.day - 1;
-  const bool owner = !warp_role || lane == 0;     // the thread that stores and reports
-  if (active) {
-    const DevParams& p = a.params[r];
-    NodeState<NA> s;
-    load_counts<NA>(a, r, v, s);
-    double* phip = a.phi + (size_t)r * a.N + v;
-    double phi = __ldcg(phip);
-    if (do_prologue) {
-      if (owner) {
-#pragma unroll
-        for (int j = 0; j < NA; ++j) { sI += (unsigned)s.x[2 * j + 1]; sN += (unsigned)(s.x[2 * j] + s.x[2 * j + 1]); }
-      }
-      if (!a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, dprev, s, phi);
+  node_day_work<NA, SCORE, MODE>(a, r, v, active, warp_role);
+}
+
+// Dealt mapping of the per-day stochastic step: the work units are the
+// warp-method nodes (largest first, a node's replicates together) and then groups
+// of 32 consecutive per-thread nodes of the order.  The grid is resident (at most
+// one wave); warp w = slot * G + block takes units w, w + T, w + 2T, ... (T warps
+// in all), so every block receives the same mix of heavy and light units, the
+// heaviest ones first, and no SM carries the largest herds alone.
+template <int NA>
+__device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t T = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t uw = (int64_t)a.R * a.n_big, ntu = (a.N - a.n_big + 31) / 32;
+  const int64_t units = uw + (int64_t)a.R * ntu;
+  for (int64_t u = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; u < units; u += T) {
+    int r = 0, v = 0;
+    bool active = false, warp_role = false;
+    if (u < uw) {
+      r = (int)(u % a.R);
+      v = a.order[u / a.R];
+      active = warp_role = true;
+    } else {
+      const int64_t ut = u - uw;
+      r = (int)(ut % a.R);
+      const int64_t i = a.n_big + (ut / a.R) * 32 + lane;
+      active = i < a.N;
+      v = active ? a.order[i] : 0;
     }
-    if (MODE == 0) {
-      if (warp_role) {
-        const uint32_t f = ssa_warp_node_day<NA>(p, a.seed, (uint32_t)(a.rep_base + r), v, a.day, phi, s);
-        if (owner) fired = f;
-      } else {
-        DayTerms T[NA];
-        fired = ssa_node_day<NA, SCORE>(p, a.seed, (uint32_t)(a.rep_base + r), v, a.day, phi, s, T);
-        if (SCORE) accumulate_score<NA>(a, p, r, v, phi, T);
-      }
-      if (a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, a.day, s, phi);
-      if (owner) store_counts<NA>(a, r, v, s);
-    }
-    if (owner) *phip = phi;
-  }
-  fired = warp_sum(fired);
-  sI = warp_sum(sI);
-  sN = warp_sum(sN);
-  if (lane == 0) {
-    if (MODE == 0 && fired) atomicAdd(a.ctr + (size_t)r * 4 + 0, fired);
-    if (do_prologue) {
-      atomicAdd(a.prev_i + (size_t)r * a.max_days + dprev, sI);
-      atomicAdd(a.prev_n + (size_t)r * a.max_days + dprev, sN);
-    }
+    node_day_work<NA, false, 0>(a, r, v, active, warp_role);
   }
 }
 

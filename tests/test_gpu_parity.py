@@ -200,7 +200,7 @@ def test_warp_per_node_path_bitexact_sise3(threshold):
     s = B.Sim.from_workload(w)
     nwarp = s.tune(threshold)
     expect = 4000 if threshold == 0 else int((w.u0.sum(0) >= threshold).sum())
-    assert nwarp == (expect // 8 * 8 if expect > 8 else expect)
+    assert nwarp == expect
     s.run(w.T)
     counts, phi, _ = s.state()
     pi, pn, ctr = s.stats()
@@ -215,7 +215,7 @@ def test_warp_per_node_path_bitexact_sise_many_transitions():
     # prevalence near 1: ~19 transitions per node-day, long warp chains
     w = W.sise_plain(N=600, T=200, n_events=12_000)
     s = B.Sim.from_workload(w)
-    assert s.tune(0) == 600 // 8 * 8
+    assert s.tune(0) == 600
     s.run(w.T)
     counts, phi, _ = s.state()
     _, _, ctr = s.stats()
