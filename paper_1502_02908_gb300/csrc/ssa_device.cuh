@@ -166,9 +166,9 @@ __device__ __forceinline__ int cmp_f32(float a, float b) {
 // the draw below, a0~ the binary32 propensity sum) is accumulated exactly in Q62
 // fixed point.  With u = 2^-24: a0~ is within 6u of a0 (constants truncated to
 // binary32: 2u, product u, three sums u each), E~ within 16u of E, and the
-// division adds u, so tau~_k is within rho = 23u < 2^-19.4 of tau_k.  At a
-// decision the Q62 sum is below 2.5, hence within 2.5 rho (< 2^-18.1) plus
-// k (2^-53 + 2^-62) of the binary64 chain for k < 2^24: a margin of 2^-17 makes
+// division (__fdividef, 2 ulps) adds 4u, so tau~_k is within rho = 26u < 2^-19.2
+// of tau_k.  At a decision the Q62 sum is below 2.5, hence within 2.5 rho
+// (< 2^-17.9) plus k (2^-53 + 2^-62) of the binary64 chain for k < 2^24: a margin of 2^-17 makes
 // "sum >= 1 + margin" a certain stop and "sum + margin < 1" a certain continue;
 // anything between is handed to the exact binary64 method.  The stochastic
 // choices are taken in binary32 only when decisive (below) and in binary64
@@ -191,8 +191,9 @@ __device__ __forceinline__ float f32_of_q53(uint64_t m) {
 // exactly from the integers.  Either way |s| <= 0.1716 and atanh(s)/s is the
 // series 1 + s^2/3 + s^4/5 + s^6/7 + s^8/9 (remainder below 2^-28).  Error
 // budget: the argument's rounding (u, amplified at most 2x near the split),
-// f + 1 or 2 - v and the quotient (u each), the series (2u), the product and the
-// final sum (u each, the sum's cancellation amplifying the e ln2 part at most 2x).
+// f + 1 or 2 - v (u), the quotient (__fdividef: 2 ulps), the series (2u), the
+// product and the final sum (u each, the sum's cancellation amplifying the e ln2
+// part at most 2x): below 14u.
 __device__ __forceinline__ float neglog_f32(uint64_t j) {
   constexpr uint64_t kSplit = 3184525836262886ull;   // first j with (2j+1) 2^-53 >= 1/sqrt2
   const bool hi = j >= kSplit;
@@ -205,7 +206,7 @@ __device__ __forceinline__ float neglog_f32(uint64_t j) {
   const float num = hi ? -x : __fsub_rn(f, 1.0f);
   const float den = hi ? __fsub_rn(2.0f, x) : __fadd_rn(f, 1.0f);
   const float sc = hi ? 0.0f : (float)e;
-  const float sq = __fdiv_rn(num, den);
+  const float sq = __fdividef(num, den);
   const float z = __fmul_rn(sq, sq);
   float poly = __fadd_rn(0.142857149f, __fmul_rn(z, 0.111111112f));
   poly = __fadd_rn(0.200000003f, __fmul_rn(z, poly));
@@ -274,13 +275,15 @@ __device__ __forceinline__ bool thresholds_f32(const bool (&cpos)[NA], const boo
 // zero thresholds always are); otherwise -1.
 template <int NA>
 __device__ __forceinline__ int choice_count_f32(const float (&T)[2 * NA - 1], float rf) {
+  const int ir = __float_as_int(rf);
+  bool amb = ir < 0x00800000;                      // r~ zero or subnormal: exact path
   int c = 0;
-  bool amb = false;
 #pragma unroll
   for (int i = 0; i < 2 * NA - 1; ++i) {
-    const int cmp = (T[i] == 0.0f) ? 1 : cmp_f32(rf, T[i]);
-    amb = amb || cmp == 0;
-    c += cmp > 0 ? 1 : 0;
+    const int d = ir - __float_as_int(T[i]);       // thresholds are 0 or normal
+    const bool zero = T[i] == 0.0f;
+    amb = amb || (!zero && d > -64 && d < 64);
+    c += (zero || d > 0) ? 1 : 0;
   }
   return amb ? -1 : c;
 }
@@ -342,7 +345,7 @@ __device__ __forceinline__ int32_t ssa_node_day_spec(const DevParams& p, uint64_
     const float Ef = neglog_f32(((((uint64_t)w.y) << 32) | w.x) >> 12);
     const float u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
     int choice = choice_count_f32<NA>(T, __fmul_rn(a0f, u2f));
-    const uint64_t sq = tq + q62_of(fminf(__fdiv_rn(Ef, a0f), 1.5f));
+    const uint64_t sq = tq + q62_of(fminf(__fdividef(Ef, a0f), 1.5f));
     if (!any || sq >= kQ62One + margin) return (int32_t)k;
     if (sq + margin >= kQ62One || k + 1u >= kSpecMaxSteps) return -1;
     if (choice < 0) choice = exact_choice<NA>(cinf, p, s.x, uniform_open(w.z, w.w));
@@ -423,7 +426,77 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
     for (int c = 0; c < NC; ++c) { x[c] = s.x[c]; xs[c] = x[c]; }
     float a0l = 0.0f;
     int stop_at = 32;
-    if (CLOCK > 0) {
+    if (CLOCK == 2) {
+      // The fixed-point iteration below with the binary32 clock in every round:
+      // the clock after each draw comes from the lanes' current states, and the
+      // first draw that is not a certain continue (a0 = 0, a certain stop, or too
+      // close to call) is the day's end candidate e.  Once no choice of the draws
+      // before e changes, those choices are the chain's, so are the states up to
+      // e and the clock through e: the block is decided without waiting for the
+      // draws after e, which cannot matter.
+      int ch = -3;
+      for (int it = 0; it <= 32; ++it) {
+        const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
+        int32_t inc = enc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int32_t y = __shfl_up_sync(full, inc, o);
+          if (lane >= o) inc += y;
+        }
+        int32_t rest = inc - enc;                  // exclusive prefix
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
+          rest = (rest - d) >> 10;
+          xs[2 * j] = x[2 * j] - d;
+          xs[2 * j + 1] = x[2 * j + 1] + d;
+        }
+        float T[2 * NA - 1], a0f;
+        int nc = -2;
+        const bool valid = thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f);
+        if (valid) {
+          nc = choice_count_f32<NA>(T, __fmul_rn(a0f, u2f));
+          if (nc < 0) nc = exact_choice<NA>(cinf, p, xs, u2);
+        }
+        uint64_t sc = valid ? q62_of(fminf(__fdividef(Ef, a0f), 1.5f)) : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t y = __shfl_up_sync(full, sc, o);
+          if (lane >= o) sc += y;
+        }
+        const uint64_t sl = tq + sc;
+        const unsigned notcont = __ballot_sync(full, !(valid && sl + margin < kQ62One));
+        const int e = notcont ? __ffs(notcont) - 1 : 32;
+        const unsigned diff = __ballot_sync(full, nc != ch) & (e < 32 ? ((1u << e) - 1u) : full);
+        ch = nc;
+        if (diff != 0u) {
+          if (it == 32) return -1;                  // cannot happen (33 rounds suffice)
+          continue;
+        }
+        if (e < 32) {
+          const unsigned ok = __ballot_sync(full, !valid || sl >= kQ62One + margin);
+          if (!((ok >> e) & 1u)) return -1;         // too close to call
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s.x[c] = __shfl_sync(full, xs[c], e);
+          return fired + e;
+        }
+        tq = __shfl_sync(full, sl, 31);
+        break;
+      }
+      // the whole block continues: the state after lane 31's draw
+      int32_t after[NC];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int dj = (ch >= 0 && (ch >> 1) == j) ? ((ch & 1) ? -1 : 1) : 0;
+        after[2 * j] = xs[2 * j] - dj;
+        after[2 * j + 1] = xs[2 * j + 1] + dj;
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s.x[c] = __shfl_sync(full, after[c], 31);
+      fired += 32;
+      continue;
+    }
+    if (CLOCK == 1) {
       // Fixed-point iteration over the lanes: every lane takes as its state the
       // block's start plus the transitions currently guessed for the lanes before
       // it and decides its own draw there.  A lane whose predecessors' guesses are
@@ -512,12 +585,8 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
       // 4. Q62 scan of tau~ (binary32) or tau (binary64), certain decisions only
       const bool valid = lane < stop_at;
       uint64_t sc = 0ull, m = margin;
-      if (CLOCK == 2) {
-        sc = valid ? q62_of(fminf(__fdiv_rn(Ef, a0l), 1.5f)) : 0ull;
-      } else {
-        sc = valid ? q62_of_f64(le_nonneg(tau, 1.5) ? tau : 1.5) : 0ull;
-        m = ((uint64_t)kb + (uint64_t)lane + 2ull) << 10;   // (k + 2) 2^-52
-      }
+      sc = valid ? q62_of_f64(le_nonneg(tau, 1.5) ? tau : 1.5) : 0ull;
+      m = ((uint64_t)kb + (uint64_t)lane + 2ull) << 10;   // (k + 2) 2^-52
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint64_t y = __shfl_up_sync(full, sc, o);
