@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(512, 1) k_events_day_smem(EvSmemArgs a) {
 
 size_t events_df_smem_bytes(int64_t n_events, int64_t n_touched, int nc) {
   if (n_events == 0) return 0;
-  return (size_t)n_events * 64 + (size_t)n_touched * (nc + 2) * 4 + (size_t)(kDfThreads + 2) * 4 + 16;
+  return (size_t)n_events * 64 + (size_t)n_touched * (nc + 2) * 4 + (size_t)(2 * kDfThreads + 1) * 4 + 16;
 }
 
 cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st) {

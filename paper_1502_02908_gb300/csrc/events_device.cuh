@@ -527,20 +527,21 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
   constexpr int NC = 2 * NA;
   const uint32_t rep = (uint32_t)(a.rep_base + r);
   int32_t* X = a.counts + (size_t)r * NC * a.N;
-  const int bi = a.day_blk[a.day] + b;
-  const int e0 = a.blk_ev[bi], e1 = a.blk_ev[bi + 1];
-  const int nev = e1 - e0;
-  const int t0 = a.blk_touch[bi], t1 = a.blk_touch[bi + 1];
-  const int nt = t1 - t0;
-  const int h0 = a.blk_thr[bi], nthr = a.blk_thr[bi + 1] - h0 - 1;
+  const int4 m0 = a.blk_meta[a.blk0 + b], m1 = a.blk_meta[a.blk0 + b + 1];
+  const int e0 = m0.x, nev = m1.x - m0.x;
+  const int t0 = m0.y, nt = m1.y - m0.y;
+  const int h0 = m0.z, nslot = m1.z - m0.z - 1;
   int4* srec = reinterpret_cast<int4*>(smem);
   Words8* swords = reinterpret_cast<Words8*>(smem + (size_t)nev * 16);
   int4* swait = reinterpret_cast<int4*>(smem + (size_t)nev * 48);
   int32_t* scnt = reinterpret_cast<int32_t*>(smem + (size_t)nev * 64);
   int32_t* sadd = scnt + (size_t)nt * NC;
   int32_t* ssmp = sadd + nt;
-  int32_t* soff = ssmp + nt;
-  int32_t* sabort = soff + (kDfThreads + 1);
+  int32_t* sbeg = ssmp + nt;                       // per thread: its events [sbeg, send)
+  int32_t* send = sbeg + kDfThreads;
+  int32_t* sabort = send + kDfThreads;
+  for (int i = threadIdx.x; i < kDfThreads; i += blockDim.x) { sbeg[i] = 0; send[i] = 0; }
+  __syncthreads();
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   // setup: the scattered count loads and the record loads of up to 4 nodes and 4
   // events per thread are issued first; the Philox blocks are computed while they
@@ -583,18 +584,51 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
       }
     }
   }
-  const int32_t* off = a.thr_off + h0;
-  for (int i = threadIdx.x; i <= kDfThreads; i += blockDim.x) soff[i] = off[i < nthr ? i : nthr];
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
+    const int t = a.thr_id[h0 + i];
+    sbeg[t] = a.thr_off[h0 + i];
+    send[t] = a.thr_off[h0 + i + 1];
+  }
   if (threadIdx.x == 0) *sabort = 0;
   __syncthreads();
   unsigned applied = 0, clamped = 0, skipped = 0;
-  const int q0 = soff[threadIdx.x], q1 = soff[threadIdx.x + 1];
+  const int q0 = sbeg[threadIdx.x], q1 = send[threadIdx.x];
   // a thread owning one heavy node (lane 0 of one of the block's first heavy warps)
   // keeps the node's counts in registers; the node's shared-memory counts then
   // act as an inbox for transfers from other threads, drained after each wait
-  const bool heavy = (threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < a.blk_heavy[bi] && q0 < q1;
+  const bool whole = (m0.w >> 16) != 0;
+  const bool heavy = !whole && (threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < (m0.w & 0xFFFF) && q0 < q1;
   int32_t hx[NC];
   int hslot = -1;
+  if (whole) {
+    // every thread owns whole components: no other thread touches its nodes, so
+    // the counts of the node its events currently sample stay in registers
+    // (written back when the sampled node changes); adds to other nodes go to
+    // shared memory, where a later switch reads them
+    int4 rcw = make_int4(0, 0, 0, 0);
+    Words8 wdw;
+    if (q0 < q1) { rcw = srec[q0]; wdw = swords[q0]; }
+    for (int q = q0; q < q1; ++q) {
+      int4 nrc = rcw;
+      Words8 nwd = wdw;
+      if (q + 1 < q1) { nrc = srec[q + 1]; nwd = swords[q + 1]; }
+      if (rcw.x != hslot) {
+        if (hslot >= 0) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) scnt[hslot * NC + c] = hx[c];
+        }
+        hslot = rcw.x;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hx[c] = scnt[hslot * NC + c];
+      }
+      apply_event_reg<NA>(a.underflow_error, a.err, a.day, a.seed, scnt, rep, rcw, wdw, hx, applied, clamped, skipped);
+      rcw = nrc; wdw = nwd;
+    }
+    if (hslot >= 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) scnt[hslot * NC + c] = hx[c];
+    }
+  }
   if (heavy) {
     hslot = srec[q0].x;
 #pragma unroll
@@ -603,7 +637,7 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
   int4 rc = make_int4(0, 0, 0, 0), wt = make_int4(0, 0, 0, 0);
   Words8 wd;
   if (q0 < q1) { rc = srec[q0]; wt = swait[q0]; wd = swords[q0]; }
-  for (int q = q0; q < q1; ++q) {
+  for (int q = (whole ? q1 : q0); q < q1; ++q) {
     // next record in flight while this one is applied
     int4 nrc = rc, nwt = wt;
     Words8 nwd = wd;

@@ -62,11 +62,9 @@ struct sim_handle {
   int4* d_wait_df = nullptr;
   int32_t* d_thr_off = nullptr;
   int32_t* d_touched_df = nullptr;
-  int32_t* d_day_blk = nullptr;
-  int32_t* d_blk_ev = nullptr;
-  int32_t* d_blk_touch = nullptr;
-  int32_t* d_blk_thr = nullptr;
-  int32_t* d_blk_heavy = nullptr;
+  std::vector<int32_t> day_blk0;     // first block of each day
+  int4* d_blk_meta = nullptr;
+  int32_t* d_thr_id = nullptr;
   int32_t event_variant = 0;         // 0 auto, 1 global only, 2 levels (no owner-computes)
   int32_t* d_day_smem = nullptr;     // device copy for the persistent batch kernel
   std::vector<int64_t> sched_order;  // position in the day-stable order, execution order
@@ -122,11 +120,10 @@ void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
   cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_touched_df);
-  cudaFree(h->d_day_blk); cudaFree(h->d_blk_ev); cudaFree(h->d_blk_touch); cudaFree(h->d_blk_thr);
-  cudaFree(h->d_blk_heavy);
+  cudaFree(h->d_blk_meta); cudaFree(h->d_thr_id);
   h->d_rec_df = nullptr; h->d_wait_df = nullptr; h->d_thr_off = nullptr; h->d_touched_df = nullptr;
-  h->d_day_blk = nullptr; h->d_blk_ev = nullptr; h->d_blk_touch = nullptr; h->d_blk_thr = nullptr;
-  h->d_blk_heavy = nullptr;
+  h->d_blk_meta = nullptr; h->d_thr_id = nullptr;
+  h->day_blk0.clear();
   h->day_df.clear();
   h->day_nblk.clear();
   h->d_day_smem = nullptr;
@@ -249,12 +246,10 @@ struct Schedule {
   std::vector<int4> rec_df;       // {block slot of src, block slot of dst, position, packed}
   std::vector<int4> wait_df;      // {transfer-adds into src before it, samplings of dst before it, flags, 0}
   std::vector<int32_t> touched_df;// node ids per block slot, blocks in order
-  std::vector<int32_t> thr_off;   // per block: event offsets of its owner threads 0..nthr (block-relative)
+  std::vector<int32_t> thr_off;   // per block: event offsets of its owner threads in use (block-relative), + end
+  std::vector<int32_t> thr_id;    // per block, aligned with thr_off: those threads' indices, then -1
   std::vector<int32_t> day_blk;   // [max_days + 1] first block of each day
-  std::vector<int32_t> blk_ev;    // [blocks + 1] first record of each block in rec_df
-  std::vector<int32_t> blk_touch; // [blocks + 1] first node of each block in touched_df
-  std::vector<int32_t> blk_thr;   // [blocks + 1] first entry of each block in thr_off
-  std::vector<int32_t> blk_heavy; // [blocks] heavy nodes (lane 0 of warps 0..heavy-1)
+  std::vector<int4> blk_meta;     // [blocks + 1] first record, first node, first thr_off entry, heavy units
   std::vector<int32_t> touched;   // node ids per day slot
   std::vector<int32_t> day_touch; // [max_days + 1]
   std::vector<int32_t> lvl_start; // [levels + 1]
@@ -279,10 +274,10 @@ struct Schedule {
 void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
                       const std::vector<int64_t>& by_pos, const int32_t* kind, const int32_t* node,
                       const int32_t* dest, const int32_t* count, const int32_t* cls,
-                      const std::vector<int32_t>& slot_of, int max_blocks) {
+                      const std::vector<int32_t>& slot_of, const std::vector<int32_t>& lvl_of, int max_blocks) {
   const int nt = (int)S.touched.size() - touch0;
   const int64_t n = s1 - s0;
-  S.day_blk.push_back((int32_t)S.blk_ev.size());
+  S.day_blk.push_back((int32_t)S.blk_meta.size());
   if (n == 0) return;
   // components (union-find over the day slots)
   std::vector<int32_t> par((size_t)nt);
@@ -380,10 +375,21 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
     wt[(size_t)(s - s0)] = w;
     blk_n[(size_t)blk_of_comp[(size_t)comp_of[(size_t)a]]]++;
   }
-  // per block: owner threads, events grouped by owner in input order
-  std::vector<std::vector<int32_t>> blk_nodes((size_t)G);
+  // per block: owner threads, events grouped by owner in input order.  A
+  // component whose events are about as many as its dependency depth (a chain,
+  // as register-shaped days mostly give) is owned whole by one thread: its events
+  // then need no wait and no publication at all.  A block holding a component
+  // with much more parallelism inside gives each of its nodes a thread instead.
+  std::vector<int32_t> comp_depth((size_t)ncomp, 0), comp_nodes((size_t)ncomp, 0);
+  for (int64_t s = s0; s < s1; ++s) {
+    const int c = comp_of[(size_t)slot_of[node[by_pos[(size_t)s]]]];
+    comp_depth[(size_t)c] = std::max(comp_depth[(size_t)c], lvl_of[(size_t)s]);
+  }
+  for (int i = 0; i < nt; ++i) comp_nodes[(size_t)comp_of[(size_t)i]]++;
+  std::vector<std::vector<int32_t>> blk_nodes((size_t)G), blk_comps((size_t)G);
   for (int i = 0; i < nt; ++i) blk_nodes[(size_t)blk_of_comp[(size_t)comp_of[(size_t)i]]].push_back(i);
-  std::vector<int32_t> owner((size_t)nt, -1);
+  for (int c = 0; c < ncomp; ++c) blk_comps[(size_t)blk_of_comp[(size_t)c]].push_back(c);
+  std::vector<int32_t> owner((size_t)nt, -1), comp_owner((size_t)ncomp, -1);
   std::vector<std::vector<int32_t>> blk_evs((size_t)G);
   for (int64_t s = s0; s < s1; ++s) {
     const int a = slot_of[node[by_pos[(size_t)s]]];
@@ -391,50 +397,85 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
   }
   const int warps = kDfThreads / 32;
   for (int b = 0; b < G; ++b) {
-    std::vector<int32_t> nodes;
-    for (int i : blk_nodes[(size_t)b]) if (evcount[(size_t)i] > 0) nodes.push_back(i);
-    std::stable_sort(nodes.begin(), nodes.end(), [&](int x, int y) { return evcount[(size_t)x] > evcount[(size_t)y]; });
+    bool whole = true;
+    for (int c : blk_comps[(size_t)b])
+      if (comp_ev[(size_t)c] > 4 * comp_depth[(size_t)c] + 32) whole = false;
+    // owner units: components (whole) or nodes, with their event counts and
+    // whether all their events sample one node (register-resident chains)
+    std::vector<int32_t> units;
+    std::vector<int64_t> uev;
+    std::vector<char> single;
+    if (whole) {
+      for (int c : blk_comps[(size_t)b]) {
+        units.push_back(c); uev.push_back(comp_ev[(size_t)c]); single.push_back(comp_nodes[(size_t)c] == 1);
+      }
+    } else {
+      for (int i : blk_nodes[(size_t)b])
+        if (evcount[(size_t)i] > 0) { units.push_back(i); uev.push_back(evcount[(size_t)i]); single.push_back(1); }
+    }
+    std::vector<int32_t> ord(units.size());
+    for (size_t k = 0; k < ord.size(); ++k) ord[k] = (int32_t)k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return uev[(size_t)x] > uev[(size_t)y]; });
+    std::vector<int32_t> uowner(units.size(), -1);
     const int64_t nb = blk_n[(size_t)b];
     int heavy = 0;
     const int64_t heavy_min = std::max<int64_t>(32, nb / 64);
-    while (heavy < (int)nodes.size() && heavy < warps / 2 && evcount[(size_t)nodes[(size_t)heavy]] >= heavy_min) {
-      owner[(size_t)nodes[(size_t)heavy]] = heavy * 32;          // lane 0 of its own warp
+    while (heavy < (int)ord.size() && heavy < warps / 2 && uev[(size_t)ord[(size_t)heavy]] >= heavy_min &&
+           single[(size_t)ord[(size_t)heavy]]) {
+      uowner[(size_t)ord[(size_t)heavy]] = heavy * 32;            // lane 0 of its own warp
       ++heavy;
     }
-    // least-loaded threads after the heavy warps (with every load 0 at the start,
-    // threads beyond the node count are never picked)
-    std::vector<std::pair<int64_t, int>> heapv;
-    const int tl = std::min(kDfThreads, heavy * 32 + (int)nodes.size());
-    for (int t = heavy * 32; t < tl; ++t) heapv.push_back({0, t});
-    auto cmp = [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
-      return x.first > y.first || (x.first == y.first && x.second > y.second);
-    };
-    std::make_heap(heapv.begin(), heapv.end(), cmp);
-    int nthr = heavy > 0 ? (heavy - 1) * 32 + 1 : 0;
-    for (size_t k = (size_t)heavy; k < nodes.size(); ++k) {
-      std::pop_heap(heapv.begin(), heapv.end(), cmp);
-      heapv.back().first += evcount[(size_t)nodes[k]];
-      owner[(size_t)nodes[k]] = heapv.back().second;
-      std::push_heap(heapv.begin(), heapv.end(), cmp);
-      nthr = std::max(nthr, owner[(size_t)nodes[k]] + 1);
+    // the others dealt lane-major over the remaining warps (a warp per unit while
+    // they last, heaviest first, so that units share no warp: their event kinds
+    // would diverge); past 32 per warp, least-loaded threads
+    const int wfree = warps - heavy;
+    std::vector<int64_t> load((size_t)kDfThreads, 0);
+    for (int h = 0; h < heavy; ++h) load[(size_t)h * 32] = uev[(size_t)ord[(size_t)h]];
+    for (size_t k = (size_t)heavy; k < ord.size(); ++k) {
+      const int64_t kk = (int64_t)k - heavy;
+      int t;
+      if (kk < (int64_t)wfree * 32) {
+        t = (heavy + (int)(kk % wfree)) * 32 + (int)(kk / wfree);
+      } else {
+        t = heavy * 32;
+        for (int q = heavy * 32; q < kDfThreads; ++q) if (load[(size_t)q] < load[(size_t)t]) t = q;
+      }
+      uowner[(size_t)ord[k]] = t;
+      load[(size_t)t] += uev[(size_t)ord[k]];
     }
-    std::vector<int32_t> off((size_t)nthr + 1, 0);
-    for (int32_t i : blk_evs[(size_t)b]) off[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]] + 1]++;
-    for (int t = 0; t < nthr; ++t) off[(size_t)t + 1] += off[(size_t)t];
+    if (whole) {
+      for (size_t k = 0; k < units.size(); ++k) comp_owner[(size_t)units[k]] = uowner[k];
+      for (int i : blk_nodes[(size_t)b]) owner[(size_t)i] = comp_owner[(size_t)comp_of[(size_t)i]];
+    } else {
+      for (size_t k = 0; k < units.size(); ++k) owner[(size_t)units[k]] = uowner[k];
+    }
+    if (whole)                                       // one thread per component: no waits
+      for (int32_t i : blk_evs[(size_t)b]) wt[(size_t)i] = make_int4(0, 0, 0, 0);
+    // owner threads in use, ascending; events grouped by them, input order within
+    std::vector<int32_t> slot_of_thr((size_t)kDfThreads, -1), thr_ids;
+    for (int t = 0; t < kDfThreads; ++t)
+      if (load[(size_t)t] > 0) { slot_of_thr[(size_t)t] = (int32_t)thr_ids.size(); thr_ids.push_back(t); }
+    const int nslot = (int)thr_ids.size();
+    std::vector<int32_t> off((size_t)nslot + 1, 0);
+    auto slot_of_ev = [&](int32_t i) {
+      return slot_of_thr[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]]];
+    };
+    for (int32_t i : blk_evs[(size_t)b]) off[(size_t)slot_of_ev(i) + 1]++;
+    for (int q = 0; q < nslot; ++q) off[(size_t)q + 1] += off[(size_t)q];
     std::vector<int32_t> fill(off.begin(), off.end() - 1);
     const size_t base = S.rec_df.size();
-    S.blk_ev.push_back((int32_t)base);
-    S.blk_touch.push_back((int32_t)(tbase + (size_t)blk_t0[(size_t)b]));
-    S.blk_thr.push_back((int32_t)S.thr_off.size());
-    S.blk_heavy.push_back(heavy);
+    S.blk_meta.push_back(make_int4((int32_t)base, (int32_t)(tbase + (size_t)blk_t0[(size_t)b]),
+                                   (int32_t)S.thr_off.size(), heavy | (whole ? (1 << 16) : 0)));
     S.rec_df.resize(base + (size_t)nb);
     S.wait_df.resize(base + (size_t)nb);
     for (int32_t i : blk_evs[(size_t)b]) {
-      const int32_t at = fill[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]]]++;
+      const int32_t at = fill[(size_t)slot_of_ev(i)]++;
       S.rec_df[base + (size_t)at] = rec[(size_t)i];
       S.wait_df[base + (size_t)at] = wt[(size_t)i];
     }
     S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
+    S.thr_id.insert(S.thr_id.end(), thr_ids.begin(), thr_ids.end());
+    S.thr_id.push_back(-1);                          // aligned with thr_off
   }
 }
 
@@ -546,15 +587,13 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
       const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
       S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
     }
-    build_owner_form(S, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of, df_blocks);
+    build_owner_form(S, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of, lvl_of, df_blocks);
   }
   S.day_lvl[T] = (int32_t)S.lvl_start.size();
   S.day_touch[T] = (int32_t)S.touched.size();
   S.lvl_start.push_back((int32_t)n_run);
-  S.day_blk.push_back((int32_t)S.blk_ev.size());
-  S.blk_ev.push_back((int32_t)S.rec_df.size());
-  S.blk_touch.push_back((int32_t)S.touched_df.size());
-  S.blk_thr.push_back((int32_t)S.thr_off.size());
+  S.day_blk.push_back((int32_t)S.blk_meta.size());
+  S.blk_meta.push_back(make_int4((int32_t)S.rec_df.size(), (int32_t)S.touched_df.size(), (int32_t)S.thr_off.size(), 0));
   return SIM_OK;
 }
 
@@ -739,24 +778,23 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
     up(&h->d_wait_df, S.wait_df, sizeof(int4));
     up(&h->d_thr_off, S.thr_off, 4);
     up(&h->d_touched_df, S.touched_df, 4);
-    up(&h->d_day_blk, S.day_blk, 4);
-    up(&h->d_blk_ev, S.blk_ev, 4);
-    up(&h->d_blk_touch, S.blk_touch, 4);
-    up(&h->d_blk_thr, S.blk_thr, 4);
-    up(&h->d_blk_heavy, S.blk_heavy, 4);
+    up(&h->d_blk_meta, S.blk_meta, sizeof(int4));
+    up(&h->d_thr_id, S.thr_id, 4);
     if (err != cudaSuccess) { free_events(h); return cuda_fail(h, err, "event upload"); }
     // shared memory of a day's launch: its largest block (0: owner-computes not used)
     h->day_df.assign((size_t)T, 0);
     h->day_nblk.assign((size_t)T, 0);
+    h->day_blk0.assign((size_t)T, 0);
     for (int32_t d = 0; d < T; ++d) {
       const int32_t b0 = S.day_blk[(size_t)d], b1 = S.day_blk[(size_t)d + 1];
       size_t most = 0;
       for (int32_t b = b0; b < b1; ++b) {
-        const int64_t ne = S.blk_ev[(size_t)b + 1] - S.blk_ev[(size_t)b];
-        const int64_t nt = S.blk_touch[(size_t)b + 1] - S.blk_touch[(size_t)b];
+        const int64_t ne = S.blk_meta[(size_t)b + 1].x - S.blk_meta[(size_t)b].x;
+        const int64_t nt = S.blk_meta[(size_t)b + 1].y - S.blk_meta[(size_t)b].y;
         most = std::max(most, events_df_smem_bytes(ne, nt, h->nc));
       }
       h->day_nblk[(size_t)d] = b1 - b0;
+      h->day_blk0[(size_t)d] = b0;
       h->day_df[(size_t)d] = (most <= kEventsSmemLimit) ? (int32_t)most : 0;
     }
   }
@@ -817,8 +855,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
   EvDfArgs df{};
   df.counts = h->d_counts; df.rec = h->d_rec_df; df.wait = h->d_wait_df; df.thr_off = h->d_thr_off;
-  df.touched = h->d_touched_df; df.day_blk = h->d_day_blk; df.blk_ev = h->d_blk_ev;
-  df.blk_touch = h->d_blk_touch; df.blk_thr = h->d_blk_thr; df.blk_heavy = h->d_blk_heavy; df.ctr = h->d_ctr;
+  df.touched = h->d_touched_df; df.blk_meta = h->d_blk_meta; df.thr_id = h->d_thr_id; df.ctr = h->d_ctr;
   df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;
@@ -830,6 +867,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
       if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
         df.day = d;
         df.nblk = h->day_nblk[(size_t)d];
+        df.blk0 = h->day_blk0[(size_t)d];
         df.smem_bytes = h->day_df[(size_t)d];
         CK(h, traced(h, 1, st, [&] { return launch_events_day_df(df, h->n_age, st); }), "event step launch");
       } else if (h->event_variant != 1 && h->day_smem[(size_t)d] > 0) {

@@ -98,13 +98,11 @@ struct EvDfArgs {
   int32_t* counts;
   const int4* rec;            // per block: grouped by owner thread, input order within
   const int4* wait;           // {adds into src before it, samplings of dst before it, flags, 0}
-  const int32_t* thr_off;     // per block: event offsets of owner threads 0..nthr (block-relative)
+  const int32_t* thr_off;     // per block: event offsets of the owner threads in use (block-relative), + end
+  const int32_t* thr_id;      // aligned with thr_off: those threads' indices
   const int32_t* touched;     // node ids per block slot
-  const int32_t* day_blk;     // [max_days + 1] first block of each day
-  const int32_t* blk_ev;      // [blocks + 1] first record of each block
-  const int32_t* blk_touch;   // [blocks + 1] first node of each block
-  const int32_t* blk_thr;     // [blocks + 1] first thread offset of each block
-  const int32_t* blk_heavy;   // [blocks] warps whose lane 0 owns one heavy node
+  const int4* blk_meta;       // [blocks + 1]: first record, first node, first thr_off entry,
+                              // heavy warps | (1 << 16 when threads own whole components)
   unsigned long long* ctr;
   int32_t* err;
   uint64_t seed;
@@ -112,6 +110,7 @@ struct EvDfArgs {
   int32_t N, R, Nc;
   int32_t day;
   int32_t nblk;               // blocks per replicate this day
+  int32_t blk0;               // the day's first block
   int32_t underflow_error;
   int32_t smem_bytes;
   int32_t spin_limit;
