@@ -228,12 +228,16 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     reruns the node-day with the exact binary64 arithmetic.  k = 17 (default)
  *     is the tightest safe margin; smaller k only reruns more node-days; 0 runs
  *     every node-day exactly.  Values outside [0, 17]: SIM_E_INVALID_ARG.
+ *   SIM_OPT_OVERLAP: 1 (default) launches the day's stochastic-step and event
+ *     kernels with programmatic dependent launch (each waits for the previous
+ *     kernel only where it reads that kernel's results, so setup and launch
+ *     latency overlap the previous kernel's tail); 0 plain stream order.
  *   SIM_OPT_LAUNCH: how sim_run_days issues a call's days -- SIM_LAUNCH_STREAM
  *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
  *     sequence captured once as a CUDA graph, keyed by start day and day count,
  *     and replayed), SIM_LAUNCH_PERSISTENT (one persistent batch-kernel launch,
  *     synchronous).  Tracing (sim_profile) always uses stream launches. */
-enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3 };
+enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4 };
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 

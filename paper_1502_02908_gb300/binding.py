@@ -264,6 +264,10 @@ class Sim:
     def set_launch(self, mode):
         _check(self.L, self.h, self.L.sim_set_option(self.h, 2, self.LAUNCH[mode]))
 
+    def set_overlap(self, on):
+        """Programmatic dependent launch between the day's kernels (results unchanged)."""
+        _check(self.L, self.h, self.L.sim_set_option(self.h, 4, 1 if on else 0))
+
     def set_clock_margin(self, k):
         """Speculative clock margin 2^-k, k in [0, 17] (0: exact clock only)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 3, int(k)))

@@ -128,6 +128,13 @@ __device__ __forceinline__ uint32_t lemire(uint32_t s, Next&& next) {
   return (uint32_t)(m >> 32);
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel lets the next one in
+// its stream be scheduled early, and that one waits for the previous grid's
+// completion (and memory) only where it reads what the previous grid wrote.
+// Both are no-ops for kernels launched without the programmatic attribute.
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int season_of(int day) {
   int dm = day % 365;
   return dm <= 91 ? 0 : dm <= 182 ? 1 : dm <= 273 ? 2 : 3;

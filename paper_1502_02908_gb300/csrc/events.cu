@@ -44,10 +44,10 @@ cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st) 
     if (e != cudaSuccess) return e;
     attr_set[which] = true;
   }
-  const unsigned grid = (unsigned)a.R * (unsigned)a.nblk;
-  if (n_age == 1) k_events_day_df<1><<<grid, kDfThreads, a.smem_bytes, st>>>(a);
-  else k_events_day_df<3><<<grid, kDfThreads, a.smem_bytes, st>>>(a);
-  return cudaGetLastError();
+  const dim3 grid((unsigned)a.R * (unsigned)a.nblk);
+  return n_age == 1
+      ? launch_maybe_pdl(k_events_day_df<1>, grid, dim3(kDfThreads), (size_t)a.smem_bytes, st, a.overlap != 0, a)
+      : launch_maybe_pdl(k_events_day_df<3>, grid, dim3(kDfThreads), (size_t)a.smem_bytes, st, a.overlap != 0, a);
 }
 
 cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st) {

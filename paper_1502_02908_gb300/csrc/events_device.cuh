@@ -525,6 +525,7 @@ __device__ __forceinline__ void apply_event_reg(int underflow_error, int32_t* er
 template <int NA>
 __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, int b, unsigned char* smem) {
   constexpr int NC = 2 * NA;
+  grid_dependents_launch();
   const uint32_t rep = (uint32_t)(a.rep_base + r);
   int32_t* X = a.counts + (size_t)r * NC * a.N;
   const int4 m0 = a.blk_meta[a.blk0 + b], m1 = a.blk_meta[a.blk0 + b + 1];
@@ -543,36 +544,38 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
   for (int i = threadIdx.x; i < kDfThreads; i += blockDim.x) { sbeg[i] = 0; send[i] = 0; }
   __syncthreads();
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-  // setup: the scattered count loads and the record loads of up to 4 nodes and 4
-  // events per thread are issued first; the Philox blocks are computed while they
-  // are in flight
-  for (int i0 = threadIdx.x; i0 < (nt > nev ? nt : nev); i0 += 4 * blockDim.x) {
+  // setup, first what does not depend on the previous kernel (records, waits,
+  // Philox blocks, the thread table), then, after the grid dependency is
+  // resolved, the scattered count loads of up to 4 nodes per thread
+  for (int i = threadIdx.x; i < nev; i += blockDim.x) {
+    const int4 rc = a.rec[e0 + i];
+    const int4 wv = a.wait[e0 + i];
+    const uint4 c0 = make_uint4((uint32_t)rc.z, (uint32_t)a.day | kEventTag, 0u, rep);
+    Words8 w;
+    w.a = philox10(c0, k0, k1);
+    w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
+    swords[i] = w;
+    srec[i] = rc;
+    swait[i] = wv;
+  }
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
+    const int t = a.thr_id[h0 + i];
+    sbeg[t] = a.thr_off[h0 + i];
+    send[t] = a.thr_off[h0 + i + 1];
+  }
+  grid_dependency_wait();
+  for (int i0 = threadIdx.x; i0 < nt; i0 += 4 * blockDim.x) {
     int v[4];
-    int4 rc[4], wv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * blockDim.x;
       v[u] = i < nt ? a.touched[t0 + i] : -1;
-      if (i < nev) { rc[u] = a.rec[e0 + i]; wv[u] = a.wait[e0 + i]; }
     }
     int32_t x[4][NC];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int c = 0; c < NC; ++c) x[u][c] = v[u] >= 0 ? __ldcg(X + (size_t)c * a.N + v[u]) : 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * blockDim.x;
-      if (i < nev) {
-        const uint4 c0 = make_uint4((uint32_t)rc[u].z, (uint32_t)a.day | kEventTag, 0u, rep);
-        Words8 w;
-        w.a = philox10(c0, k0, k1);
-        w.b = philox10(make_uint4(c0.x, c0.y, 1u, rep), k0, k1);
-        swords[i] = w;
-        srec[i] = rc[u];
-        swait[i] = wv[u];
-      }
-    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + u * blockDim.x;
@@ -583,11 +586,6 @@ __device__ __forceinline__ void events_block_dataflow(const EvDfArgs& a, int r, 
         ssmp[i] = 0;
       }
     }
-  }
-  for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
-    const int t = a.thr_id[h0 + i];
-    sbeg[t] = a.thr_off[h0 + i];
-    send[t] = a.thr_off[h0 + i + 1];
   }
   if (threadIdx.x == 0) *sabort = 0;
   __syncthreads();

@@ -46,6 +46,7 @@ struct sim_handle {
   int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
   int32_t clock_margin_log2 = 17;   // speculative clock margin 2^-k (0: exact clock only)
   int32_t sm_count = 1;             // SMs of the handle's device
+  int32_t overlap = 1;              // programmatic dependent launch between the day's kernels
   double* d_phi0 = nullptr;
   // event schedule
   bool events_loaded = false;
@@ -204,6 +205,7 @@ SsaArgs ssa_args(sim_handle* h) {
   a.warp_blocks = (h->n_big + 7) / 8;
   a.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
   a.sm_count = h->sm_count;
+  a.overlap = h->overlap;
   return a;
 }
 
@@ -859,6 +861,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;
+  df.overlap = h->overlap;
   for (int32_t d = d0; d < d0 + ndays; ++d) {
     a.day = d;
     a.prologue = d > d0;
@@ -1249,6 +1252,12 @@ sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
       CK(h, cudaDeviceSynchronize(), "synchronize");
       free_graph(h);
       h->launch_mode = (int32_t)value;
+      return SIM_OK;
+    case SIM_OPT_OVERLAP:
+      if (value != 0 && value != 1) return fail(h, SIM_E_INVALID_ARG, "overlap must be 0 or 1");
+      CK(h, cudaDeviceSynchronize(), "synchronize");
+      free_graph(h);
+      h->overlap = (int32_t)value;
       return SIM_OK;
     case SIM_OPT_CLOCK_MARGIN:
       if (value < 0 || value > 17)

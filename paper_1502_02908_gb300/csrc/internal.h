@@ -45,6 +45,7 @@ struct SsaArgs {
   int32_t warp_blocks;        // blocks (of 8 warps) given to them
   uint64_t clock_margin;      // Q62 margin of the speculative binary32 clock (0: exact clock only)
   int32_t sm_count;           // SMs of the device (grid of the dealt mapping)
+  int32_t overlap;            // launch with programmatic stream serialization
 };
 
 // One scheduled event, 16 bytes: node, dest, position in the day-stable order,
@@ -111,11 +112,31 @@ struct EvDfArgs {
   int32_t day;
   int32_t nblk;               // blocks per replicate this day
   int32_t blk0;               // the day's first block
+  int32_t overlap;            // launch with programmatic stream serialization
   int32_t underflow_error;
   int32_t smem_bytes;
   int32_t spin_limit;
 };
 cudaError_t launch_events_day_df(const EvDfArgs& a, int n_age, cudaStream_t st);
+
+// Launch with programmatic stream serialization when pdl is set: the kernel may
+// be scheduled while the previous one in the stream finishes, and waits for it
+// with griddepcontrol.wait where it reads that kernel's results.
+template <class... P, class... A>
+inline cudaError_t launch_maybe_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    bool pdl, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 size_t events_df_smem_bytes(int64_t n_events, int64_t n_touched, int nc);
 // Shared memory the staged event step needs for a day (0 if the day has no events).
 size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc);

@@ -26,6 +26,8 @@ __global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_r
 
 template <int NA>
 __global__ void __launch_bounds__(256, 2) k_node_day_dealt(SsaArgs a) {
+  grid_dependents_launch();
+  grid_dependency_wait();                          // counts and phi of the previous step
   node_day_dealt<NA>(a);
 }
 
@@ -50,9 +52,9 @@ static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStre
     const int64_t per_sm = std::min<int64_t>(resident[which], (units + sms * 8 - 1) / (sms * 8));
     const int64_t G = sms * per_sm;
     const int W = (int)std::min<int64_t>(8, (units + G - 1) / G);
-    if (n_age == 1) k_node_day_dealt<1><<<(unsigned)G, 32 * W, 0, st>>>(a);
-    else k_node_day_dealt<3><<<(unsigned)G, 32 * W, 0, st>>>(a);
-    return cudaGetLastError();
+    return n_age == 1
+        ? launch_maybe_pdl(k_node_day_dealt<1>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a)
+        : launch_maybe_pdl(k_node_day_dealt<3>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a);
   }
   const int warp_blocks = (MODE == 0 && !score) ? a.warp_blocks : 0;
   const int n_thread = a.N - ((MODE == 0 && !score && a.order) ? a.n_big : 0);

@@ -252,3 +252,22 @@ def test_event_kernel_variants_bitexact(variant, e1_source):
     ref = oracle.run(w)
     assert np.array_equal(counts, ref.counts) and np.array_equal(ctr, ref.counters)
     _assert_phi(phi, ref.phi)
+
+
+@pytest.mark.parametrize("launch", ["stream", "graph"])
+def test_programmatic_overlap_on_and_off_bitexact(launch):
+    # the day's kernels launched with programmatic dependent launch (default) or
+    # in plain stream order give the oracle's result either way
+    w = W.sise3_national(N=5000, T=60, n_events=60_000)
+    ref = oracle.run(w)
+    for on in (True, False):
+        s = B.Sim.from_workload(w)
+        s.set_overlap(on)
+        s.set_launch(launch)
+        s.run(w.T)
+        counts, phi, _ = s.state()
+        pi, pn, ctr = s.stats()
+        s.close()
+        assert np.array_equal(counts, ref.counts)
+        _assert_phi(phi, ref.phi)
+        assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
