@@ -40,6 +40,34 @@ FP64_PEAK_LANE_OPS = 6.25e11
 #   per node-day: closing draw 2 + 7 + 1 = 10; rates 3 x 4 = 12; phi update 12  = 34
 FP64_PER_TRANSITION = {3: 15, 1: 12}
 FP64_PER_NODE_DAY = {3: 34, 1: 24}
+# ncu summary of the stochastic-step kernel: its DRAM bytes per launch count as the
+# roofline's traffic only while the kernel sources still hash to the captured ones
+SSA_PROFILE = os.path.join(ROOT, "profiles", "k_node_day_dealt_national_day300.md")
+
+
+def kernel_sources_digest():
+    import hashlib
+    d = os.path.join(ROOT, "paper_1502_02908_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(path):
+    """DRAM bytes per launch from an ncu summary (lines `dram_bytes_per_launch: N`
+    and `sources_sha256: H`), or None when absent or taken on other sources."""
+    try:
+        with open(path) as fh:
+            kv = dict(line.strip("- `\n").split(": ", 1) for line in fh if ": " in line and line.startswith("- `"))
+        if kv.get("sources_sha256") != kernel_sources_digest():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -282,9 +310,9 @@ def main():
     fp64_ops = FP64_PER_TRANSITION[w.model] * transitions + FP64_PER_NODE_DAY[w.model] * N * T
     ssa_avg_s = ssa_ms / 1000 / max(ssa_n, 1)
     achieved = fp64_ops / ssa_n / ssa_avg_s if ssa_n else 0.0
-    roofline = {"kernel": "k_node_day (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
+    roofline = {"kernel": "k_node_day_dealt (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
                 "peak": FP64_PEAK_LANE_OPS / 1e9, "unit": "G FP64 lane-ops/s",
-                "frac": achieved / FP64_PEAK_LANE_OPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_LANE_OPS, "traffic": profiled_traffic(SSA_PROFILE),
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (derived; see DESIGN.md)",
                 "kernel_share": {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k},
                 "avg_launch_us": {"ssa": 1000 * ssa_ms / max(ssa_n, 1), "events": 1000 * ev_ms / max(ev_n, 1)}}

@@ -236,7 +236,9 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
  *     sequence captured once as a CUDA graph, keyed by start day and day count,
  *     and replayed), SIM_LAUNCH_PERSISTENT (one persistent batch-kernel launch,
- *     synchronous).  Tracing (sim_profile) always uses stream launches. */
+ *     synchronous).  Under tracing (sim_profile), SIM_LAUNCH_GRAPH runs a
+ *     one-shot graph with the event records inside, the other modes stream
+ *     launches. */
 enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4 };
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);

@@ -611,11 +611,16 @@ cudaError_t traced(sim_handle* h, int kind, cudaStream_t st, F&& fn) {
       h->ev_pool.push_back(e);
     }
   }
-  cudaError_t err = cudaEventRecord(h->ev_pool[h->ev_used], st);
+  // under stream capture the records must be external to become event-record nodes
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(st, &cap);
+  if (err != cudaSuccess) return err;
+  const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  err = cudaEventRecordWithFlags(h->ev_pool[h->ev_used], st, flags);
   if (err != cudaSuccess) return err;
   err = fn();
   if (err != cudaSuccess) return err;
-  err = cudaEventRecord(h->ev_pool[h->ev_used + 1], st);
+  err = cudaEventRecordWithFlags(h->ev_pool[h->ev_used + 1], st, flags);
   h->ev_used += 2;
   h->ev_kind.push_back(kind);
   return err;
@@ -900,6 +905,30 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
     sim_handle* one[1] = {h};
     sim_status s = sim_run_batch(one, 1, &until, stream);
     if (s != SIM_OK) return fail(h, s, "%s", sim_last_error(nullptr));
+    return SIM_OK;
+  }
+  if (h->launch_mode == 1 && h->profiling) {
+    // traced graph mode: a one-shot graph with the event records inside, so the
+    // per-kernel times carry no host launch gaps
+    cudaStream_t cs;
+    CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    sim_status s = SIM_OK;
+    if (e == cudaSuccess) s = enqueue_days(h, d0, ndays, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && s == SIM_OK) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (s != SIM_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(h, e, "traced graph capture");
+    e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return cuda_fail(h, e, "traced graph launch");
+    h->day = d0 + ndays;
     return SIM_OK;
   }
   if (h->launch_mode == 1 && !h->profiling) {

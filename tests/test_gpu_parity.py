@@ -271,3 +271,25 @@ def test_programmatic_overlap_on_and_off_bitexact(launch):
         assert np.array_equal(counts, ref.counts)
         _assert_phi(phi, ref.phi)
         assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
+
+
+@pytest.mark.parametrize("launch", ["stream", "graph"])
+def test_tracing_times_every_launch_and_keeps_results(launch):
+    # sim_profile: one timed pair per kernel launch (graph mode: event-record
+    # nodes inside a one-shot graph); traced runs give the untraced result
+    w = W.sise3_national(N=3000, T=20, n_events=20_000)
+    ref = oracle.run(w)
+    s = B.Sim.from_workload(w)
+    s.set_launch(launch)
+    s.profile(True)
+    s.run(w.T)
+    prof = s.profile_read()
+    s.profile(False)
+    counts, _, _ = s.state()
+    s.close()
+    assert np.array_equal(counts, ref.counts)
+    ms, n = prof["ssa"]
+    assert n == w.T and ms > 0
+    ems, en = prof["events"]
+    assert en == len(set(np.asarray(w.events.day).tolist()) & set(range(w.T))) and ems > 0
+    assert prof["finalize"][1] == 1
