@@ -313,7 +313,7 @@ def main():
     roofline = {"kernel": "k_node_day_dealt (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
                 "peak": FP64_PEAK_LANE_OPS / 1e9, "unit": "G FP64 lane-ops/s",
                 "frac": achieved / FP64_PEAK_LANE_OPS, "traffic": profiled_traffic(SSA_PROFILE),
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (derived; see DESIGN.md)",
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (an FMA counts two flops)",
                 "kernel_share": {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k},
                 "avg_launch_us": {"ssa": 1000 * ssa_ms / max(ssa_n, 1), "events": 1000 * ev_ms / max(ev_n, 1)}}
 
