@@ -232,6 +232,11 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     kernels with programmatic dependent launch (each waits for the previous
  *     kernel only where it reads that kernel's results, so setup and launch
  *     latency overlap the previous kernel's tail); 0 plain stream order.
+ *   SIM_OPT_SPLIT: 1 runs the stochastic step of a day that follows a
+ *     day with events as two launches: the herds the previous day's events left
+ *     untouched, on a second stream alongside that event step (they do not depend
+ *     on it), and the touched herds after it; 0 (default) one launch per day.  The calling
+ *     stream is joined before every event step and at the end of the call.
  *   SIM_OPT_LAUNCH: how sim_run_days issues a call's days -- SIM_LAUNCH_STREAM
  *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
  *     sequence captured once as a CUDA graph, keyed by start day and day count,
@@ -239,7 +244,8 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     synchronous).  Under tracing (sim_profile), SIM_LAUNCH_GRAPH runs a
  *     one-shot graph with the event records inside, the other modes stream
  *     launches. */
-enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4 };
+enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4,
+       SIM_OPT_SPLIT = 5 };
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 

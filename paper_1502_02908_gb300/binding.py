@@ -268,6 +268,10 @@ class Sim:
         """Programmatic dependent launch between the day's kernels (results unchanged)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 4, 1 if on else 0))
 
+    def set_split(self, on):
+        """Untouched herds' stochastic step alongside the previous day's events (results unchanged)."""
+        _check(self.L, self.h, self.L.sim_set_option(self.h, 5, 1 if on else 0))
+
     def set_clock_margin(self, k):
         """Speculative clock margin 2^-k, k in [0, 17] (0: exact clock only)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 3, int(k)))

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(512) k_events_day(EvArgs a) {
 }
 
 template <int NA>
-__global__ void __launch_bounds__(kDfThreads, 1) k_events_day_df(EvDfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) k_events_day_df(EvDfArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   events_block_dataflow<NA>(a, (int)(blockIdx.x / (unsigned)a.nblk), (int)(blockIdx.x % (unsigned)a.nblk), smem);
 }

@@ -47,6 +47,15 @@ struct sim_handle {
   int32_t clock_margin_log2 = 17;   // speculative clock margin 2^-k (0: exact clock only)
   int32_t sm_count = 1;             // SMs of the handle's device
   int32_t overlap = 1;              // programmatic dependent launch between the day's kernels
+  int32_t split = 0;                // next day's untouched herds alongside the event step
+  int32_t eff_threshold = 1 << 30;  // herd size of the warp path in effect
+  std::vector<int32_t> touched_host;   // per day, the herds the day's events touch
+  std::vector<int32_t> day_touch_host; // [max_days + 1]
+  std::vector<int32_t> tlist_nbig;     // per day: warp-path herds at the head of the day's touched list
+  uint32_t* d_skip = nullptr;          // [max_days][ceil(N/32)] touched-herd bitmaps
+  int32_t* d_tlist = nullptr;          // per day: touched herds, warp-path ones first, largest first
+  cudaStream_t side = nullptr;         // stream of the untouched herds' step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_phi0 = nullptr;
   // event schedule
   bool events_loaded = false;
@@ -117,6 +126,12 @@ cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc((void**)p, n * sizeof(T));
 }
 
+void free_split(sim_handle* h) {
+  cudaFree(h->d_skip); cudaFree(h->d_tlist);
+  h->d_skip = nullptr; h->d_tlist = nullptr;
+  h->tlist_nbig.clear();
+}
+
 void free_events(sim_handle* h) {
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
@@ -131,6 +146,8 @@ void free_events(sim_handle* h) {
   h->d_rec = nullptr; h->d_lvl_start = nullptr; h->d_day_lvl = nullptr;
   h->d_rec_slot = nullptr; h->d_touched = nullptr; h->d_day_touch = nullptr;
   h->sched_order.clear(); h->sched_level.clear(); h->day_lvl.clear(); h->day_smem.clear();
+  h->touched_host.clear(); h->day_touch_host.clear();
+  free_split(h);
   h->events_loaded = false;
 }
 
@@ -147,6 +164,11 @@ void free_graph(sim_handle* h) {
 
 void free_all(sim_handle* h) {
   free_graph(h);
+  free_split(h);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->side = nullptr; h->ev_fork = h->ev_join = nullptr;
   free_profile(h);
   free_events(h);
   cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
@@ -206,6 +228,8 @@ SsaArgs ssa_args(sim_handle* h) {
   a.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
   a.sm_count = h->sm_count;
   a.overlap = h->overlap;
+  a.n_list = h->cfg.n_nodes;
+  a.skip = nullptr;
   return a;
 }
 
@@ -214,6 +238,44 @@ SsaArgs ssa_args(sim_handle* h) {
 // first, one thread each (similar work per warp).  threshold < 0: automatic --
 // warps only while the per-thread work leaves the GPU under-occupied (fewer than
 // 152 x 1024 node-replicates), for herds of 400 animals or more.
+// Tables of the split day step: the stochastic step of day d + 1 runs as two
+// launches, the herds that day d's events leave untouched (alongside the event
+// step of day d, on a second stream) and the touched ones (after it).  Per day:
+// a bitmap of the touched herds and their list, warp-path herds first, each part
+// largest first.
+sim_status build_split(sim_handle* h) {
+  free_split(h);
+  if (!h->events_loaded || (h->cfg.flags & SIM_FLAG_SCORE) || h->day_touch_host.empty()) return SIM_OK;
+  const int N = h->cfg.n_nodes;
+  const int32_t T = h->cfg.max_days;
+  const size_t words = ((size_t)N + 31) / 32;
+  std::vector<int64_t> herd(N, 0);
+  for (int c = 0; c < h->nc; ++c)
+    for (int v = 0; v < N; ++v) herd[v] += h->u0[(size_t)c * N + v];
+  std::vector<uint32_t> skip;
+  std::vector<int32_t> tl(h->touched_host.size());
+  try { skip.assign((size_t)T * words, 0u); } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  h->tlist_nbig.assign((size_t)T, 0);
+  for (int32_t d = 0; d < T; ++d) {
+    const int32_t b = h->day_touch_host[(size_t)d], e = h->day_touch_host[(size_t)d + 1];
+    for (int32_t i = b; i < e; ++i) {
+      const int v = h->touched_host[(size_t)i];
+      skip[(size_t)d * words + (size_t)(v >> 5)] |= 1u << (v & 31);
+      tl[(size_t)i] = v;
+    }
+    std::stable_sort(tl.begin() + b, tl.begin() + e, [&](int32_t x, int32_t y) { return herd[x] > herd[y]; });
+    int32_t nb = 0;
+    while (b + nb < e && herd[tl[(size_t)(b + nb)]] >= h->eff_threshold) ++nb;
+    h->tlist_nbig[(size_t)d] = nb;
+  }
+  cudaError_t err = dalloc(&h->d_skip, skip.size());
+  if (err == cudaSuccess) err = dalloc(&h->d_tlist, tl.size());
+  if (err == cudaSuccess && !skip.empty()) err = cudaMemcpy(h->d_skip, skip.data(), skip.size() * 4, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && !tl.empty()) err = cudaMemcpy(h->d_tlist, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) { free_split(h); return cuda_fail(h, err, "split tables"); }
+  return SIM_OK;
+}
+
 sim_status set_order(sim_handle* h, int32_t threshold) {
   const int N = h->cfg.n_nodes;
   std::vector<int64_t> herd(N, 0);
@@ -234,8 +296,9 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_big = nb;
   h->warp_threshold = threshold;
+  h->eff_threshold = (h->cfg.flags & SIM_FLAG_SCORE) ? (1 << 30) : thr;
   free_graph(h);
-  return SIM_OK;
+  return build_split(h);
 }
 
 
@@ -755,8 +818,9 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 1;
   // owner-computes blocks per replicate and day: enough to spread one replicate
-  // over the SMs, one per replicate once the replicates fill them
-  const int df_blocks = std::max(1, sms / std::max(1, h->cfg.n_replicates));
+  // over the SMs (two 256-thread blocks fit on one), one per replicate once the
+  // replicates fill them
+  const int df_blocks = std::max(1, 2 * sms / std::max(1, h->cfg.n_replicates));
   sim_status st = build_schedule(h, h->cfg.n_nodes, h->n_age, h->cfg.max_days, n, day, kind, node, dest,
                                  count, cls, df_blocks, S);
   if (st != SIM_OK) return st;
@@ -821,9 +885,11 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
   h->sched_order.swap(S.order);
   h->sched_level.swap(S.level);
   h->day_lvl.swap(S.day_lvl);
+  h->touched_host.swap(S.touched);
+  h->day_touch_host.swap(S.day_touch);
   h->events_loaded = true;
   free_graph(h);
-  return SIM_OK;
+  return build_split(h);
 }
 
 sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days, int64_t n,
@@ -867,11 +933,50 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;
   df.overlap = h->overlap;
+  // Split day step: after a day d with events, the stochastic step of day d + 1
+  // runs as two launches -- the herds d's events leave untouched, on the side
+  // stream as soon as day d's stochastic step is complete (alongside d's event
+  // step), and the touched herds after the event step; the side launch is joined
+  // before the event step of day d + 1.  Without events the day is one launch.
+  const bool split = h->split && !score && h->events_loaded && h->d_skip && h->d_tlist;
+  const size_t words = ((size_t)h->cfg.n_nodes + 31) / 32;
+  if (split && !h->side) {
+    CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
+    CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "fork event");
+    CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "join event");
+  }
+  auto has_events = [&](int32_t d) { return h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]; };
   for (int32_t d = d0; d < d0 + ndays; ++d) {
     a.day = d;
     a.prologue = d > d0;
-    CK(h, traced(h, 0, st, [&] { return launch_ssa_day(a, h->n_age, score, st); }), "stochastic step launch");
-    if (h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d]) {
+    if (split && d > d0 && has_events(d - 1)) {
+      // touched herds of day d - 1 (the untouched ones were launched on the side stream)
+      SsaArgs at = a;
+      const int32_t b0 = h->day_touch_host[(size_t)d - 1], b1 = h->day_touch_host[(size_t)d];
+      at.order = h->d_tlist + b0;
+      at.n_list = b1 - b0;
+      at.n_big = h->tlist_nbig[(size_t)d - 1];
+      if (at.n_list > 0)
+        CK(h, traced(h, 0, st, [&] { return launch_ssa_day(at, h->n_age, score, st); }), "stochastic step launch");
+      CK(h, cudaStreamWaitEvent(st, h->ev_join, 0), "join");
+    } else {
+      CK(h, traced(h, 0, st, [&] { return launch_ssa_day(a, h->n_age, score, st); }), "stochastic step launch");
+    }
+    if (split && d + 1 < d0 + ndays && has_events(d)) {
+      CK(h, cudaEventRecord(h->ev_fork, st), "fork");
+      CK(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork");
+      SsaArgs au = a;
+      au.day = d + 1;
+      au.prologue = 1;
+      au.skip = h->d_skip + (size_t)d * words;
+      au.overlap = 0;                                // after an event wait: plain stream order
+      au.max_per_sm = 1;                             // one block of up to 12 warps per SM: with
+      au.max_warps = 12;                             // 128 registers a thread, room for an event block
+      CK(h, traced(h, 0, h->side, [&] { return launch_ssa_day(au, h->n_age, score, h->side); }),
+         "stochastic step launch");
+      CK(h, cudaEventRecord(h->ev_join, h->side), "join");
+    }
+    if (has_events(d)) {
       if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
         df.day = d;
         df.nblk = h->day_nblk[(size_t)d];
@@ -1287,6 +1392,12 @@ sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
       CK(h, cudaDeviceSynchronize(), "synchronize");
       free_graph(h);
       h->overlap = (int32_t)value;
+      return SIM_OK;
+    case SIM_OPT_SPLIT:
+      if (value != 0 && value != 1) return fail(h, SIM_E_INVALID_ARG, "split must be 0 or 1");
+      CK(h, cudaDeviceSynchronize(), "synchronize");
+      free_graph(h);
+      h->split = (int32_t)value;
       return SIM_OK;
     case SIM_OPT_CLOCK_MARGIN:
       if (value < 0 || value > 17)

@@ -41,11 +41,15 @@ struct SsaArgs {
   int32_t pre_event;          // 1: phi update from post-SSA counts in the epilogue
   double* traj;               // reverse-mode score: [3][max_days][R][N] = c_d, phi_d, I_d/N_d (NULL otherwise)
   const int32_t* order;       // node order: first n_big nodes warp-cooperative, the rest per thread (NULL: identity)
+  int32_t n_list;             // nodes in the order list (N, or a day's touched list)
+  const uint32_t* skip;       // bitmap [N] of nodes this launch leaves out (NULL: none)
   int32_t n_big;              // nodes simulated one per warp
   int32_t warp_blocks;        // blocks (of 8 warps) given to them
   uint64_t clock_margin;      // Q62 margin of the speculative binary32 clock (0: exact clock only)
   int32_t sm_count;           // SMs of the device (grid of the dealt mapping)
   int32_t overlap;            // launch with programmatic stream serialization
+  int32_t max_per_sm;         // dealt grid: at most this many blocks per SM (0: as many as fit)
+  int32_t max_warps;          // dealt grid: warps per block (0: 8)
 };
 
 // One scheduled event, 16 bytes: node, dest, position in the day-stable order,
@@ -90,7 +94,7 @@ cudaError_t launch_events_day_smem(const EvSmemArgs& a, int n_age, cudaStream_t 
 // order, the events of the nodes it owns, waiting on shared-memory counters for
 // the transfers into a node that precede a sampling of it and for the samplings of
 // a destination that precede a transfer into it.
-constexpr int kDfThreads = 512;
+constexpr int kDfThreads = 128;
 constexpr int kEventWaitTimeout = 4;      // error bit: an event-step wait ran out
 constexpr int kDfAcquire = 1;             // the event waited on another thread's counter
 constexpr int kDfPublishSampling = 2;     // a later transfer into its node waits on it

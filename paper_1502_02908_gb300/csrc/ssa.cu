@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_r
 }
 
 template <int NA>
-__global__ void __launch_bounds__(256, 2) k_node_day_dealt(SsaArgs a) {
+__global__ void __launch_bounds__(512, 1) k_node_day_dealt(SsaArgs a) {
   grid_dependents_launch();
   grid_dependency_wait();                          // counts and phi of the previous step
   node_day_dealt<NA>(a);
@@ -46,12 +46,14 @@ static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStre
       if (e != cudaSuccess) return e;
       resident[which] = nb > 0 ? nb : 1;
     }
-    const int64_t units = (int64_t)a.R * (a.n_big + (a.N - a.n_big + 31) / 32);
+    const int64_t units = (int64_t)a.R * (a.n_big + (a.n_list - a.n_big + 31) / 32);
     if (units == 0) return cudaSuccess;
     const int64_t sms = a.sm_count > 0 ? a.sm_count : 1;
-    const int64_t per_sm = std::min<int64_t>(resident[which], (units + sms * 8 - 1) / (sms * 8));
+    const int64_t wmax = a.max_warps > 0 ? a.max_warps : 8;
+    const int64_t fit = a.max_per_sm > 0 ? std::min(resident[which], a.max_per_sm) : resident[which];
+    const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(fit, (units + sms * wmax - 1) / (sms * wmax)));
     const int64_t G = sms * per_sm;
-    const int W = (int)std::min<int64_t>(8, (units + G - 1) / G);
+    const int W = (int)std::min<int64_t>(wmax, (units + G - 1) / G);
     return n_age == 1
         ? launch_maybe_pdl(k_node_day_dealt<1>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a)
         : launch_maybe_pdl(k_node_day_dealt<3>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a);

@@ -783,7 +783,8 @@ __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) 
 
 // Dealt mapping of the per-day stochastic step: the work units are the
 // warp-method nodes (largest first, a node's replicates together) and then groups
-// of 32 consecutive per-thread nodes of the order.  The grid is resident (at most
+// of 32 consecutive per-thread nodes of the order (a.n_list of them; nodes marked
+// in a.skip are left to another launch).  The grid is resident (at most
 // one wave); warp w = slot * G + block takes units w, w + T, w + 2T, ... (T warps
 // in all), so every block receives the same mix of heavy and light units, the
 // heaviest ones first, and no SM carries the largest herds alone.
@@ -791,7 +792,7 @@ template <int NA>
 __device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
   const int lane = threadIdx.x & 31;
   const int64_t T = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t uw = (int64_t)a.R * a.n_big, ntu = (a.N - a.n_big + 31) / 32;
+  const int64_t uw = (int64_t)a.R * a.n_big, ntu = (a.n_list - a.n_big + 31) / 32;
   const int64_t units = uw + (int64_t)a.R * ntu;
   for (int64_t u = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; u < units; u += T) {
     int r = 0, v = 0;
@@ -804,9 +805,10 @@ __device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
       const int64_t ut = u - uw;
       r = (int)(ut % a.R);
       const int64_t i = a.n_big + (ut / a.R) * 32 + lane;
-      active = i < a.N;
+      active = i < a.n_list;
       v = active ? a.order[i] : 0;
     }
+    if (a.skip && active && ((__ldg(a.skip + (v >> 5)) >> (v & 31)) & 1u)) active = false;
     node_day_work<NA, false, 0>(a, r, v, active, warp_role);
   }
 }

@@ -273,14 +273,15 @@ def test_programmatic_overlap_on_and_off_bitexact(launch):
         assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
 
 
-@pytest.mark.parametrize("launch", ["stream", "graph"])
-def test_tracing_times_every_launch_and_keeps_results(launch):
+@pytest.mark.parametrize("launch,split", [("stream", False), ("graph", False), ("graph", True)])
+def test_tracing_times_every_launch_and_keeps_results(launch, split):
     # sim_profile: one timed pair per kernel launch (graph mode: event-record
     # nodes inside a one-shot graph); traced runs give the untraced result
     w = W.sise3_national(N=3000, T=20, n_events=20_000)
     ref = oracle.run(w)
     s = B.Sim.from_workload(w)
     s.set_launch(launch)
+    s.set_split(split)
     s.profile(True)
     s.run(w.T)
     prof = s.profile_read()
@@ -289,7 +290,32 @@ def test_tracing_times_every_launch_and_keeps_results(launch):
     s.close()
     assert np.array_equal(counts, ref.counts)
     ms, n = prof["ssa"]
-    assert n == w.T and ms > 0
+    # one launch per day, plus the touched herds' launch of each day after a day
+    # with events (split day step)
+    ev_days = set(np.asarray(w.events.day).tolist()) & set(range(w.T))
+    assert n == w.T + (len([d for d in range(1, w.T) if d - 1 in ev_days]) if split else 0) and ms > 0
     ems, en = prof["events"]
     assert en == len(set(np.asarray(w.events.day).tolist()) & set(range(w.T))) and ems > 0
     assert prof["finalize"][1] == 1
+
+
+@pytest.mark.parametrize("launch,threshold,R", [("stream", 400, 1), ("graph", 400, 1), ("graph", 0, 2),
+                                                 ("graph", 1 << 30, 1)])
+def test_split_day_step_bitexact(launch, threshold, R):
+    # the next day's untouched herds on a second stream alongside the event step,
+    # the touched ones after it, or one launch per day: the oracle's result both ways
+    w = W.sise3_national(N=5000, T=45, n_events=60_000, R=R)
+    ref = oracle.run(w)
+    for split in (True, False):
+        s = B.Sim.from_workload(w)
+        s.tune(threshold)
+        s.set_split(split)
+        s.set_launch(launch)
+        s.run(20)
+        s.run(w.T - 20)                              # a second call starts with a full launch
+        counts, phi, _ = s.state()
+        pi, pn, ctr = s.stats()
+        s.close()
+        assert np.array_equal(counts, ref.counts)
+        _assert_phi(phi, ref.phi)
+        assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i) and np.array_equal(pn, ref.prev_n)
