@@ -221,6 +221,10 @@ int32_t sim_warp_nodes(const sim_handle* h);
 
 /* Execution options (results never depend on them):
  *   SIM_OPT_WARP_THRESHOLD: as sim_tune.
+ *   SIM_OPT_GROUP_THRESHOLD: herds below the warp threshold with at least this
+ *     many animals (initial herd) are simulated four to a warp, eight lanes each
+ *     drawing eight steps at a time; -1 = automatic (200 while node-replicates
+ *     number fewer than 152 x 1024, else none), a very large value disables it.
  *   SIM_OPT_CLOCK_MARGIN: k in [0, 17].  The stochastic step (outside score
  *     mode) first runs each node-day with a binary32 clock accumulated in fixed
  *     point, whose distance to the binary64 clock of Eq. (numstep3) is bounded
@@ -245,7 +249,7 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     one-shot graph with the event records inside, the other modes stream
  *     launches. */
 enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4,
-       SIM_OPT_SPLIT = 5 };
+       SIM_OPT_SPLIT = 5, SIM_OPT_GROUP_THRESHOLD = 6 };
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 

@@ -1,9 +1,10 @@
 """Launch-shape autotuner.
 
-For one workload it times each candidate setting -- the herd size from which a
-node gets a warp (warp-per-node vs thread-per-node stochastic step) and the
-launch mode of the daily loop (stream launches, a captured CUDA graph, or the
-persistent work-stealing kernel) -- over a short prefix of the horizon, checks
+For one workload it times each candidate setting -- the herd sizes from which a
+node gets a warp or an 8-lane group (warp-per-node, four-per-warp and
+thread-per-node stochastic step) and the launch mode of the daily loop (stream
+launches, a captured CUDA graph, or the persistent work-stealing kernel) -- over
+a short prefix of the horizon, checks
 that every candidate ends in the bit-identical state (counts, phi, statistics,
 counters), and keeps the fastest.  Settings never change results; the check
 guards the implementation.
@@ -18,6 +19,7 @@ import numpy as np
 from . import binding as B
 
 WARP_THRESHOLDS = (1 << 30, 1600, 800, 400, 200)
+GROUP_THRESHOLDS = (1 << 30, 300, 200, 100)
 LAUNCH_MODES = ("stream", "graph", "persistent")
 
 
@@ -27,8 +29,11 @@ def _fingerprint(sim):
     return (c.tobytes(), p.tobytes(), pi.tobytes(), pn.tobytes(), ctr.tobytes(), d)
 
 
-def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES, repeats=2):
-    """Returns (best {"warp_threshold", "launch"}, table [(threshold, mode, ms)])."""
+def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES, repeats=2,
+             groups=(1 << 30,)):
+    """Returns (best {"warp_threshold", "group_threshold", "launch"}, table
+    [(threshold, group threshold, mode, ms)]).  Group thresholds at or above the
+    warp threshold are skipped (no herd would take the group path)."""
     import torch
     w = workload
     nd = min(w.T, days if days is not None else max(10, w.T // 10))
@@ -38,7 +43,10 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
     ref = None
     table = []
     try:
-        for thr, mode in itertools.product(thresholds, modes):
+        for thr, gthr, mode in itertools.product(thresholds, groups, modes):
+            if gthr >= thr and gthr != groups[0]:
+                continue
+            sim.set_group_threshold(gthr)
             sim.tune(thr)
             sim.set_launch(mode)
             best = float("inf")
@@ -56,9 +64,9 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
             if ref is None:
                 ref = fp
             elif fp != ref:
-                raise AssertionError(f"setting ({thr}, {mode}) changed the results")
-            table.append((thr, mode, best))
+                raise AssertionError(f"setting ({thr}, {gthr}, {mode}) changed the results")
+            table.append((thr, gthr, mode, best))
     finally:
         sim.close()
-    thr, mode, _ = min(table, key=lambda x: x[2])
-    return {"warp_threshold": thr, "launch": mode}, table
+    thr, gthr, mode, _ = min(table, key=lambda x: x[3])
+    return {"warp_threshold": thr, "group_threshold": gthr, "launch": mode}, table

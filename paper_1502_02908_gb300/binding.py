@@ -268,6 +268,10 @@ class Sim:
         """Programmatic dependent launch between the day's kernels (results unchanged)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 4, 1 if on else 0))
 
+    def set_group_threshold(self, herd):
+        """Herd size from which a node gets an 8-lane group (-1 automatic; results unchanged)."""
+        _check(self.L, self.h, self.L.sim_set_option(self.h, 6, int(herd)))
+
     def set_split(self, on):
         """Untouched herds' stochastic step alongside the previous day's events (results unchanged)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 5, 1 if on else 0))

@@ -44,11 +44,15 @@ struct sim_handle {
   int32_t* d_order = nullptr;       // node order of the stochastic step
   int32_t n_big = 0;                // leading nodes of the order simulated one per warp
   int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
+  int32_t group_threshold = -1;     // herd size from which a node gets an 8-lane group (-1: automatic)
+  int32_t n_mid = 0;                // nodes after the warp-path ones simulated one per 8-lane group
   int32_t clock_margin_log2 = 17;   // speculative clock margin 2^-k (0: exact clock only)
   int32_t sm_count = 1;             // SMs of the handle's device
   int32_t overlap = 1;              // programmatic dependent launch between the day's kernels
   int32_t split = 0;                // next day's untouched herds alongside the event step
   int32_t eff_threshold = 1 << 30;  // herd size of the warp path in effect
+  int32_t eff_group_threshold = 1 << 30;  // herd size of the group path in effect
+  std::vector<int32_t> tlist_nmid;     // per day: group-path herds after them
   std::vector<int32_t> touched_host;   // per day, the herds the day's events touch
   std::vector<int32_t> day_touch_host; // [max_days + 1]
   std::vector<int32_t> tlist_nbig;     // per day: warp-path herds at the head of the day's touched list
@@ -224,6 +228,7 @@ SsaArgs ssa_args(sim_handle* h) {
   a.traj = h->d_traj;
   a.order = h->d_order;
   a.n_big = h->n_big;
+  a.n_mid = h->n_mid;
   a.warp_blocks = (h->n_big + 7) / 8;
   a.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
   a.sm_count = h->sm_count;
@@ -256,6 +261,7 @@ sim_status build_split(sim_handle* h) {
   std::vector<int32_t> tl(h->touched_host.size());
   try { skip.assign((size_t)T * words, 0u); } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
   h->tlist_nbig.assign((size_t)T, 0);
+  h->tlist_nmid.assign((size_t)T, 0);
   for (int32_t d = 0; d < T; ++d) {
     const int32_t b = h->day_touch_host[(size_t)d], e = h->day_touch_host[(size_t)d + 1];
     for (int32_t i = b; i < e; ++i) {
@@ -264,9 +270,11 @@ sim_status build_split(sim_handle* h) {
       tl[(size_t)i] = v;
     }
     std::stable_sort(tl.begin() + b, tl.begin() + e, [&](int32_t x, int32_t y) { return herd[x] > herd[y]; });
-    int32_t nb = 0;
+    int32_t nb = 0, nm = 0;
     while (b + nb < e && herd[tl[(size_t)(b + nb)]] >= h->eff_threshold) ++nb;
+    while (b + nb + nm < e && herd[tl[(size_t)(b + nb + nm)]] >= h->eff_group_threshold) ++nm;
     h->tlist_nbig[(size_t)d] = nb;
+    h->tlist_nmid[(size_t)d] = nm;
   }
   cudaError_t err = dalloc(&h->d_skip, skip.size());
   if (err == cudaSuccess) err = dalloc(&h->d_tlist, tl.size());
@@ -289,12 +297,21 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
     const int64_t work = (int64_t)N * h->cfg.n_replicates;
     thr = (work < 152 * 1024) ? 400 : (1 << 30);
   }
-  int32_t nb = 0;
-  if (!(h->cfg.flags & SIM_FLAG_SCORE))
+  int32_t gthr = h->group_threshold;
+  if (gthr < 0) {
+    const int64_t work = (int64_t)N * h->cfg.n_replicates;
+    gthr = (work < 152 * 1024) ? 200 : (1 << 30);
+  }
+  int32_t nb = 0, nm = 0;
+  if (!(h->cfg.flags & SIM_FLAG_SCORE)) {
     while (nb < N && herd[order[nb]] >= thr) ++nb;
+    while (nb + nm < N && herd[order[nb + nm]] >= gthr) ++nm;
+  }
   if (!h->d_order) CK(h, dalloc(&h->d_order, (size_t)N), "node order allocation");
   CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_big = nb;
+  h->n_mid = nm;
+  h->eff_group_threshold = (h->cfg.flags & SIM_FLAG_SCORE) ? (1 << 30) : gthr;
   h->warp_threshold = threshold;
   h->eff_threshold = (h->cfg.flags & SIM_FLAG_SCORE) ? (1 << 30) : thr;
   free_graph(h);
@@ -956,6 +973,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
       at.order = h->d_tlist + b0;
       at.n_list = b1 - b0;
       at.n_big = h->tlist_nbig[(size_t)d - 1];
+      at.n_mid = h->tlist_nmid[(size_t)d - 1];
       if (at.n_list > 0)
         CK(h, traced(h, 0, st, [&] { return launch_ssa_day(at, h->n_age, score, st); }), "stochastic step launch");
       CK(h, cudaStreamWaitEvent(st, h->ev_join, 0), "join");
@@ -1393,6 +1411,11 @@ sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
       free_graph(h);
       h->overlap = (int32_t)value;
       return SIM_OK;
+    case SIM_OPT_GROUP_THRESHOLD:
+      if (value < -1) return fail(h, SIM_E_INVALID_ARG, "group threshold must be >= -1");
+      CK(h, cudaDeviceSynchronize(), "synchronize");
+      h->group_threshold = (int32_t)std::min<int64_t>(value, 1 << 30);
+      return set_order(h, h->warp_threshold);
     case SIM_OPT_SPLIT:
       if (value != 0 && value != 1) return fail(h, SIM_E_INVALID_ARG, "split must be 0 or 1");
       CK(h, cudaDeviceSynchronize(), "synchronize");

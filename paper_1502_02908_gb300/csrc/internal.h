@@ -44,6 +44,7 @@ struct SsaArgs {
   int32_t n_list;             // nodes in the order list (N, or a day's touched list)
   const uint32_t* skip;       // bitmap [N] of nodes this launch leaves out (NULL: none)
   int32_t n_big;              // nodes simulated one per warp
+  int32_t n_mid;              // next nodes of the order, one per 8-lane group (dealt grid only)
   int32_t warp_blocks;        // blocks (of 8 warps) given to them
   uint64_t clock_margin;      // Q62 margin of the speculative binary32 clock (0: exact clock only)
   int32_t sm_count;           // SMs of the device (grid of the dealt mapping)

@@ -46,7 +46,8 @@ static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStre
       if (e != cudaSuccess) return e;
       resident[which] = nb > 0 ? nb : 1;
     }
-    const int64_t units = (int64_t)a.R * (a.n_big + (a.n_list - a.n_big + 31) / 32);
+    const int64_t units =
+        (int64_t)a.R * (a.n_big + (a.n_mid + 3) / 4 + (a.n_list - a.n_big - a.n_mid + 31) / 32);
     if (units == 0) return cudaSuccess;
     const int64_t sms = a.sm_count > 0 ? a.sm_count : 1;
     const int64_t wmax = a.max_warps > 0 ? a.max_warps : 8;

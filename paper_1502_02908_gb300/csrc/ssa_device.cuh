@@ -628,6 +628,119 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
   }
 }
 
+// Group method: the warp's lanes form 32/SEG groups of SEG lanes, one node each
+// (medium herds), with the binary32 clock: per round each group draws SEG steps
+// at once and decides them by the fixed-point iteration of the warp method, with
+// the clock inside every round (CLOCK = 2 above), all groups in lockstep (the
+// warp iterates until every group is decided; a decided group's values stay put,
+// as re-deciding a consistent guess gives the same values).  Every lane returns
+// its group's result: the transitions fired, or -1 (binary32 bounds not met, or a
+// clock decision too close to call) for the caller to rerun that node-day with
+// the binary64 warp method.  Inactive groups (no node) return 0 at once.
+template <int NA, int SEG>
+__device__ __forceinline__ int32_t ssa_seg_node_day(const DevParams& p, uint64_t seed, uint32_t rep, int v, int day,
+                                                    double phi, uint64_t margin, bool active, NodeState<NA>& s) {
+  constexpr int NC = 2 * NA;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (SEG - 1);
+  const int base = lane & ~(SEG - 1);
+  const uint32_t full = 0xffffffffu;
+  const uint32_t gfull = SEG == 32 ? full : ((1u << SEG) - 1u);
+  double cinf[NA];
+  float cinff[NA], gamf[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) cinf[j] = __dmul_rn(p.ups[j], phi);
+  const bool spec_ok = spec_constants<NA>(p, cinf, s.x, cinff, gamf);
+  bool cpos[NA], gpos[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) { cpos[j] = pos(cinf[j]); gpos[j] = pos(p.gam[j]); }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  int32_t result = 0, fired = 0;
+  bool done = !active;
+  if (active && !spec_ok) { result = -1; done = true; }
+  uint64_t tq = 0;
+  for (uint32_t kb = 0;; kb += SEG) {
+    if (!done && kb >= kSpecMaxSteps) { result = -1; done = true; }
+    if (__all_sync(full, done)) break;
+    // 1. draws of this round
+    const uint4 w = philox10(make_uint4((uint32_t)v, (uint32_t)day, kb + (uint32_t)gl, rep), k0, k1);
+    const float Ef = neglog_f32(((((uint64_t)w.y) << 32) | w.x) >> 12);
+    const float u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
+    // 2-4. fixed-point iteration with the clock in every round
+    int32_t xs[NC];
+    int ch = -3, e = SEG;
+    uint64_t sl = 0;
+    bool valid = false;
+    unsigned okb = 0;
+    for (int it = 0; it <= SEG; ++it) {
+      const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
+      int32_t inc = enc;
+#pragma unroll
+      for (int o = 1; o < SEG; o <<= 1) {
+        const int32_t y = __shfl_up_sync(full, inc, o, SEG);
+        if (gl >= o) inc += y;
+      }
+      int32_t rest = inc - enc;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
+        rest = (rest - d) >> 10;
+        xs[2 * j] = s.x[2 * j] - d;
+        xs[2 * j + 1] = s.x[2 * j + 1] + d;
+      }
+      float T[2 * NA - 1], a0f;
+      int nc = -2;
+      valid = !done && thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f);
+      if (valid) {
+        nc = choice_count_f32<NA>(T, __fmul_rn(a0f, u2f));
+        if (nc < 0) nc = exact_choice<NA>(cinf, p, xs, uniform_open(w.z, w.w));
+      }
+      uint64_t sc = valid ? q62_of(fminf(__fdividef(Ef, a0f), 1.5f)) : 0ull;
+#pragma unroll
+      for (int o = 1; o < SEG; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(full, sc, o, SEG);
+        if (gl >= o) sc += y;
+      }
+      sl = tq + sc;
+      const unsigned notcont = (__ballot_sync(full, !(valid && sl + margin < kQ62One)) >> base) & gfull;
+      e = notcont ? __ffs(notcont) - 1 : SEG;
+      okb = (__ballot_sync(full, !valid || sl >= kQ62One + margin) >> base) & gfull;
+      const unsigned diff = (__ballot_sync(full, nc != ch) >> base) & gfull & (e < SEG ? ((1u << e) - 1u) : gfull);
+      ch = nc;
+      if (__all_sync(full, done || diff == 0u)) break;
+    }
+    // outcome of the round, per group (every lane takes part in the shuffles)
+    const int src = e < SEG ? e : SEG - 1;
+    int32_t xe[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xe[c] = __shfl_sync(full, xs[c], base + src);
+    const int che = __shfl_sync(full, ch, base + src);
+    const uint64_t sle = __shfl_sync(full, sl, base + src);
+    if (!done) {
+      if (e < SEG) {
+        if ((okb >> e) & 1u) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s.x[c] = xe[c];
+          result = fired + e;
+        } else {
+          result = -1;                               // too close to call
+        }
+        done = true;
+      } else {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          const int dj = (che >= 0 && (che >> 1) == j) ? ((che & 1) ? -1 : 1) : 0;
+          s.x[2 * j] = xe[2 * j] - dj;
+          s.x[2 * j + 1] = xe[2 * j + 1] + dj;
+        }
+        tq = sle;
+        fired += SEG;
+      }
+    }
+  }
+  return result;
+}
+
 // Adds one node-day's score terms to the node's accumulators (same op order as
 // the oracle).
 template <int NA>
@@ -661,16 +774,21 @@ __device__ __forceinline__ void accumulate_score(const SsaArgs& a, const DevPara
 
 // MODE 0: day a.day (prologue for a.day - 1 when a.prologue); MODE 1: finalize
 // after the last day a.day (statistics of a.day; phi update in post-event mode).
-// One thread's part of node v of replicate r (warp_role: the whole warp shares
-// node v and lane 0 stores and reports); then the warp's statistics and counters.
+constexpr int kRoleThread = 0;  // one node per thread
+constexpr int kRoleWarp = 1;    // one node per warp (lane 0 stores and reports)
+constexpr int kRoleGroup = 2;   // one node per group of kGroupLanes lanes (its first lane stores and reports)
+constexpr int kGroupLanes = 8;
+
+// One thread's part of node v of replicate r in the given role; then the warp's
+// statistics and counters.
 template <int NA, bool SCORE, int MODE>
-__device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bool active, bool warp_role) {
+__device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bool active, int role) {
   const int lane = threadIdx.x & 31;
   const uint32_t full = 0xffffffffu;
   unsigned long long sI = 0, sN = 0, fired = 0;
   const bool do_prologue = (MODE == 1) || a.prologue;
   const int dprev = (MODE == 1) ? a.day : a.day - 1;
-  const bool owner = !warp_role || lane == 0;     // the thread that stores and reports
+  const bool owner = role == kRoleThread || (role == kRoleWarp ? lane == 0 : (lane & (kGroupLanes - 1)) == 0);
   const DevParams& p = a.params[r];
   const uint32_t rep = (uint32_t)(a.rep_base + r);
   double* phip = a.phi + (size_t)r * a.N + v;
@@ -688,7 +806,7 @@ __device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bo
       if (!a.pre_event) phi = phi_step<NA, SCORE>(a, p, r, v, dprev, s, phi);
     }
     s0 = s;
-    if (MODE == 0 && !warp_role) {
+    if (MODE == 0 && role == kRoleThread) {
       f = -1;
       if (!SCORE && a.clock_margin) {
         double cinf[NA];
@@ -708,7 +826,7 @@ __device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bo
     }
   }
   if (MODE == 0 && !SCORE) {
-    if (warp_role) {
+    if (role == kRoleWarp) {
       if (active) {                                // warp-uniform
         f = -1;
         if (a.clock_margin) {
@@ -721,9 +839,15 @@ __device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bo
         }
       }
     } else {
-      // lanes the binary32 clock could not decide (or could not take): the whole
+      if (role == kRoleGroup) {                    // every lane of the warp takes part
+        f = a.clock_margin ? ssa_seg_node_day<NA, kGroupLanes>(p, a.seed, rep, v, a.day, phi, a.clock_margin,
+                                                               active, s)
+                           : (active ? -1 : 0);
+        if (f < 0) s = s0;
+      }
+      // nodes the binary32 clock could not decide (or could not take): the whole
       // warp runs the binary64 warp method for each of them in turn
-      unsigned need = __ballot_sync(full, active && f < 0);
+      unsigned need = __ballot_sync(full, owner && active && f < 0);
       while (need) {
         const int l = __ffs(need) - 1;
         need &= need - 1;
@@ -734,7 +858,8 @@ __device__ __forceinline__ void node_day_work(const SsaArgs& a, int r, int v, bo
         for (int c = 0; c < 2 * NA; ++c) t.x[c] = t0.x[c] = __shfl_sync(full, s0.x[c], l);
         int32_t g = ssa_warp_node_day<NA, 1>(p, a.seed, rep, vl, a.day, phil, 0, t);
         if (g < 0) { t = t0; g = ssa_warp_node_day<NA, 0>(p, a.seed, rep, vl, a.day, phil, 0, t); }
-        if (lane == l) { s = t; f = g; }
+        const bool mine = role == kRoleGroup ? (lane & ~(kGroupLanes - 1)) == l : lane == l;
+        if (mine) { s = t; f = g; }
       }
     }
   }
@@ -778,7 +903,7 @@ __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) 
     active = i + base < a.N;
     v = active ? (a.order && MODE == 0 && !SCORE ? a.order[base + i] : i + base) : 0;
   }
-  node_day_work<NA, SCORE, MODE>(a, r, v, active, warp_role);
+  node_day_work<NA, SCORE, MODE>(a, r, v, active, warp_role ? kRoleWarp : kRoleThread);
 }
 
 // Dealt mapping of the per-day stochastic step: the work units are the
@@ -792,24 +917,35 @@ template <int NA>
 __device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
   const int lane = threadIdx.x & 31;
   const int64_t T = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t uw = (int64_t)a.R * a.n_big, ntu = (a.n_list - a.n_big + 31) / 32;
-  const int64_t units = uw + (int64_t)a.R * ntu;
+  const int64_t R = a.R;
+  const int64_t uw = R * a.n_big;                                    // one node per warp
+  const int64_t ug = R * ((a.n_mid + 3) / 4);                        // four nodes per warp
+  const int64_t ntu = (a.n_list - a.n_big - a.n_mid + 31) / 32;      // 32 nodes per warp
+  const int64_t units = uw + ug + R * ntu;
   for (int64_t u = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; u < units; u += T) {
-    int r = 0, v = 0;
-    bool active = false, warp_role = false;
+    int r = 0, v = 0, role = kRoleThread;
+    bool active = false;
     if (u < uw) {
-      r = (int)(u % a.R);
-      v = a.order[u / a.R];
-      active = warp_role = true;
-    } else {
+      r = (int)(u % R);
+      v = a.order[u / R];
+      active = true;
+      role = kRoleWarp;
+    } else if (u < uw + ug) {
       const int64_t ut = u - uw;
-      r = (int)(ut % a.R);
-      const int64_t i = a.n_big + (ut / a.R) * 32 + lane;
+      r = (int)(ut % R);
+      const int64_t i = a.n_big + (ut / R) * 4 + (lane / kGroupLanes);
+      active = i < a.n_big + a.n_mid;
+      v = active ? a.order[i] : 0;
+      role = kRoleGroup;
+    } else {
+      const int64_t ut = u - uw - ug;
+      r = (int)(ut % R);
+      const int64_t i = a.n_big + a.n_mid + (ut / R) * 32 + lane;
       active = i < a.n_list;
       v = active ? a.order[i] : 0;
     }
     if (a.skip && active && ((__ldg(a.skip + (v >> 5)) >> (v & 31)) & 1u)) active = false;
-    node_day_work<NA, false, 0>(a, r, v, active, warp_role);
+    node_day_work<NA, false, 0>(a, r, v, active, role);
   }
 }
 

@@ -108,5 +108,6 @@ def test_graph_and_persistent_launch_modes_match_stream_launches():
 def test_autotuner_keeps_results_and_picks_a_setting():
     from paper_1502_02908_gb300 import autotune
     w = W.sise3_national(N=2000, T=30, n_events=40_000)
-    best, table = autotune.autotune(w, days=20, thresholds=(1 << 30, 200), repeats=1)
-    assert len(table) == 6 and best["launch"] in autotune.LAUNCH_MODES
+    best, table = autotune.autotune(w, days=20, thresholds=(1 << 30, 200), repeats=1, groups=(1 << 30, 100))
+    assert len(table) == 12 and best["launch"] in autotune.LAUNCH_MODES
+    assert best["group_threshold"] in (1 << 30, 100)

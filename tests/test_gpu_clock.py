@@ -101,3 +101,40 @@ def test_clock_margin_rejects_unsafe_values():
         with pytest.raises(B.SimError):
             s.set_clock_margin(bad)
     s.close()
+
+
+@pytest.mark.parametrize("warp,group", [(1 << 30, 0), (400, 50), (1 << 30, 150)])
+@pytest.mark.parametrize("k", [17, 1])
+def test_group_path_bitexact_sise3(warp, group, k):
+    # herds below the warp threshold and at or above the group threshold run four
+    # to a warp, eight lanes each; group 0: every node in a group
+    w = W.sise3_national(N=3000, T=60, n_events=40_000)
+    s = B.Sim.from_workload(w)
+    s.set_group_threshold(group)
+    s.tune(warp)
+    s.set_clock_margin(k)
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    pi, pn, ctr = s.stats()
+    s.close()
+    ref = _oracle("sise3", w)
+    assert np.array_equal(counts, ref.counts)
+    np.testing.assert_allclose(phi, ref.phi, rtol=1e-12, atol=0)
+    assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i) and np.array_equal(pn, ref.prev_n)
+
+
+@pytest.mark.parametrize("k", [17, 1])
+def test_group_path_bitexact_sise_many_transitions(k):
+    w = W.sise_plain(N=600, T=120, n_events=8_000)
+    s = B.Sim.from_workload(w)
+    s.set_group_threshold(0)
+    s.tune(1 << 30)
+    s.set_clock_margin(k)
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    _, _, ctr = s.stats()
+    s.close()
+    ref = _oracle("sise", w)
+    assert np.array_equal(counts, ref.counts)
+    np.testing.assert_allclose(phi, ref.phi, rtol=1e-12, atol=0)
+    assert np.array_equal(ctr, ref.counters)
