@@ -319,3 +319,24 @@ def test_split_day_step_bitexact(launch, threshold, R):
         assert np.array_equal(counts, ref.counts)
         _assert_phi(phi, ref.phi)
         assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i) and np.array_equal(pn, ref.prev_n)
+
+
+@pytest.mark.parametrize("underflow_error", [False, True])
+def test_event_step_bitexact_with_clamps_and_error_policy(underflow_error):
+    # "powerlaw" puts ~8 % of the events on one small herd: a long daily chain in
+    # one component, many of its events clamped or, under the ERROR policy, skipped
+    w = W.sise3_national(N=3000, T=40, n_events=60_000, e1_source="powerlaw")
+    ref = oracle.run(w, underflow_error=underflow_error)
+    assert ref.counters[0, 2 + int(underflow_error)] > 0
+    s = B.Sim.from_workload(w, underflow_error=underflow_error)
+    s.run(w.T)
+    if underflow_error:
+        with pytest.raises(B.SimError) as ei:
+            s.sync()
+        assert ei.value.status == B.SIM_E_UNDERFLOW
+    counts, phi, _ = s.state()
+    _, _, ctr = s.stats()
+    s.close()
+    assert np.array_equal(counts, ref.counts)
+    _assert_phi(phi, ref.phi)
+    assert np.array_equal(ctr, ref.counters)
