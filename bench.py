@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-synthetic", action="store_true")
     return ap.parse_args()
 
 
@@ -175,6 +176,56 @@ def batched_leg(args, B, W, torch, plain_value):
     return {"workload": f"SISe3 national network, {w.R} replicates x {w.T} days, own (upsilon, gamma) each",
             "value": value, "unit": "node-days/s", "steps": steps, "warmup": warm, "ms_per_step": ms,
             "events_per_s": (trans + evs) / (ms / 1000), "launch": best, "vs_plain": value / plain_value}
+
+
+def synthetic_leg(args, B, W, torch, oracle_check):
+    """The paper's synthetic benchmark (Sec. 4.2): 1,000 nodes with S = I = 1,000,
+    unit rates both ways, 1,000 days, rho = 0.1 with k = 16 sub-domains (12 transfers
+    a day): about 2,000 transitions per node-day.  Launch shape by a short autotune;
+    bit-exactness checked against the oracle over the first days."""
+    from paper_1502_02908_gb300 import autotune
+    w = W.synthetic_sis()
+    best, _ = autotune.autotune(w, days=10, thresholds=(1 << 30, 400), modes=("graph",), repeats=1,
+                                groups=(1 << 30, 100))
+    sim = B.Sim.from_workload(w)
+    sim.set_group_threshold(best["group_threshold"]); sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
+    u0 = w.u0[None]; phi0 = w.phi0[None]
+    steps, warm = 2, 1
+    times = []
+    _, _, c0 = sim.stats()
+    for i in range(warm + steps):
+        sim.set_state(u0, phi0, 0)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(); sim.run(w.T); e1.record()
+        torch.cuda.synchronize()
+        if i >= warm:
+            times.append(e0.elapsed_time(e1))
+    _, _, c1 = sim.stats()
+    sim.close()
+    ms = sum(times) / steps
+    trans = int(c1[0, 0] - c0[0, 0]) // (warm + steps)
+    line = {"workload": f"synthetic SIS (Sec. 4.2): {w.N} nodes, S = I = 1000, unit rates, {w.T} days, "
+                        f"rho = 0.1, k = 16 ({len(w.events)} transfers)",
+            "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "transitions_per_s": trans / (ms / 1000),
+            "transitions_per_step": trans, "steps": steps, "warmup": warm, "ms_per_step": ms,
+            "launch": best}
+    if oracle_check:
+        import oracle
+        oracle.build()
+        days = 3
+        t0 = time.perf_counter()
+        ref = oracle.run(w, ndays=days, replicates=[0])
+        dt = time.perf_counter() - t0
+        chk = B.Sim.from_workload(w)
+        chk.set_group_threshold(best["group_threshold"]); chk.tune(best["warp_threshold"])
+        chk.run(days)
+        c, p, _ = chk.state()
+        chk.close()
+        line["bitexact_vs_oracle"] = {"days": days, "counts_equal": bool(np.array_equal(c[0], ref.counts[0])),
+                                      "phi_equal": bool(np.array_equal(p[0], ref.phi[0]))}
+        line["oracle_transitions_per_s"] = int(ref.counters[0, 0]) / dt
+    return line
 
 
 def dist_setup():
@@ -333,6 +384,8 @@ def main():
     line["config"]["launch"] = tuned
     if not args.no_batched:
         line["batched"] = batched_leg(args, B, W, torch, value)
+    if not args.no_synthetic and rank == 0:
+        line["synthetic"] = synthetic_leg(args, B, W, torch, not args.no_cpu_baseline)
     if rank == 0 and not args.no_cpu_baseline:
         days = min(365, T)
         base, ref = oracle_baseline(w, days, "national SISe3")

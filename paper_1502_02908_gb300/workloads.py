@@ -169,6 +169,36 @@ def sise_plain(N=1000, T=365, n_events=20_000, seed=1, R=1, herd_lo=20, herd_hi=
     return Workload("sise_plain", SISE, N, T, R, u0, np.zeros(N), params, ev, seed)
 
 
+def synthetic_sis(N=1000, T=1000, S0=1000, I0=1000, rho=0.1, k=16, count=1, seed=1, R=1, gen_seed=26):
+    """The synthetic benchmark of Sec. 4.2: two compartments S and I on N nodes with
+    S -> I and I -> S both at unit rate per animal, S = I = 1000 per node at the
+    start, T daily windows.  As an SISe instance: upsilon = gamma = 1 and phi held
+    at 1 (phi0 = 1, alpha = beta = epsilon = 0, so the update returns phi
+    unchanged).  The nodes form k contiguous sub-domains; at the end of every day
+    round(rho k (k-1) / 2) external transfers of `count` animals each connect a
+    random node of one sub-domain to a random node of another (both drawn
+    uniformly, the two sub-domains distinct).  The paper leaves the transfer size
+    open; one animal by default."""
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    u0 = np.zeros((2, N), np.int32)
+    u0[0] = S0
+    u0[1] = I0
+    m = int(round(rho * k * (k - 1) / 2))
+    dom = (np.arange(N) * k) // N
+    members = [np.nonzero(dom == d)[0] for d in range(k)]
+    n_ev = m * T
+    day = np.repeat(np.arange(T), m)
+    a = rng.integers(0, k, size=n_ev)
+    b = rng.integers(0, k - 1, size=n_ev)
+    b = b + (b >= a)                                  # a different sub-domain
+    src = np.array([members[x][rng.integers(0, members[x].size)] for x in a], dtype=np.int64)
+    dst = np.array([members[x][rng.integers(0, members[x].size)] for x in b], dtype=np.int64)
+    ev = Events(day.astype(np.int32), np.full(n_ev, EXTERNAL, np.int32), src.astype(np.int32),
+                dst.astype(np.int32), np.full(n_ev, count, np.int32), np.full(n_ev, -1, np.int32))
+    params = Params.broadcast(R, 1.0, 1.0, 0.0, 0.0, 0.0)
+    return Workload("synthetic_sis", SISE, N, T, R, u0, np.ones(N), params, ev, seed)
+
+
 VTEC_UPSILON = (8e-3, 7e-3, 1e-3)          # Sec. 4.1, per age class
 VTEC_DELTA = (28.0, 25.0, 22.0)           # mean infectious period, days
 VTEC_BETA_DIV = (14.0, 26.0, 20.0, 12.0)  # beta = log(2)/k per season

@@ -340,3 +340,21 @@ def test_event_step_bitexact_with_clamps_and_error_policy(underflow_error):
     assert np.array_equal(counts, ref.counts)
     _assert_phi(phi, ref.phi)
     assert np.array_equal(ctr, ref.counters)
+
+
+@pytest.mark.parametrize("warp,group", [(400, 1 << 30), (1 << 30, 100), (1 << 30, 1 << 30)])
+def test_synthetic_benchmark_bitexact(warp, group):
+    # Sec. 4.2 benchmark shape (about S + I transitions per node-day), small
+    w = W.synthetic_sis(N=64, T=12, S0=300, I0=300, rho=0.5, k=8)
+    ref = oracle.run(w)
+    s = B.Sim.from_workload(w)
+    s.set_group_threshold(group)
+    s.tune(warp)
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    pi, pn, ctr = s.stats()
+    s.close()
+    assert np.array_equal(counts, ref.counts)
+    assert np.all(phi == 1.0)
+    assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
+    assert ctr[0, 0] > 64 * 12 * 500                  # SSA-dense

@@ -262,3 +262,29 @@ def test_transfer_all_classes_is_multivariate_hypergeometric():
                 prob[a * (n_take + 1) + b] = (math.comb(int(comp[0]), a) * math.comb(int(comp[1]), b)
                                               * math.comb(int(rest), n_take - a - b)) / math.comb(int(total), n_take)
     assert _chisq_pvalue(np.bincount(cells, minlength=prob.size), prob) > 1e-4
+
+
+def test_synthetic_benchmark_instance_law():
+    # The Sec. 4.2 benchmark as generated: unit rates both ways, phi held at 1.
+    # Without transfers every node is an independent two-state population, so I_T
+    # follows the two-binomial law with c = gamma = 1.
+    S0 = I0 = 20
+    w = W.synthetic_sis(N=20_000, T=2, S0=S0, I0=I0, rho=0.0)
+    assert len(w.events) == 0
+    r = oracle.run(w)
+    assert np.all(r.phi == 1.0)
+    I_T = r.counts[0, 1]
+    pmf = _two_state_pmf(S0, I0, 1.0, 1.0, w.T)
+    assert _chisq_pvalue(np.bincount(I_T, minlength=S0 + I0 + 1), pmf) > 1e-4
+    # with transfers (one animal each, between different sub-domains) totals move
+    # only by the transfers
+    w = W.synthetic_sis(N=64, T=5, S0=S0, I0=I0, rho=1.0, k=8)
+    r = oracle.run(w)
+    tot = r.counts[0].sum(0)
+    ev = w.events
+    delta = np.zeros(w.N, np.int64)
+    np.add.at(delta, np.asarray(ev.node), -np.asarray(ev.count))
+    np.add.at(delta, np.asarray(ev.dest), np.asarray(ev.count))
+    assert np.array_equal(tot, S0 + I0 + delta)
+    dom = (np.arange(w.N) * 8) // w.N
+    assert np.all(dom[np.asarray(ev.node)] != dom[np.asarray(ev.dest)])
