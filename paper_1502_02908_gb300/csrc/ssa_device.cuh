@@ -246,6 +246,23 @@ __device__ __forceinline__ bool spec_constants(const DevParams& p, const double 
   return ok && herd < (1 << 22);
 }
 
+// State of a lane in the fixed-point iteration: the block's start x plus the
+// transitions the lanes before it (within its group of SEG lanes) currently
+// guess, counted with one ballot per transition kind (ch = 2*class + recovery;
+// negative = none).
+template <int NA, int SEG>
+__device__ __forceinline__ void prefix_state(const int32_t (&x)[2 * NA], int ch, int lane, int32_t (&xs)[2 * NA]) {
+  const uint32_t full = 0xffffffffu;
+  const uint32_t below = ((1u << lane) - 1u) & (SEG == 32 ? full : ~((1u << (lane & ~(SEG - 1))) - 1u));
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    const int inf = __popc(__ballot_sync(full, ch == 2 * j) & below);
+    const int rec = __popc(__ballot_sync(full, ch == 2 * j + 1) & below);
+    xs[2 * j] = x[2 * j] - inf + rec;
+    xs[2 * j + 1] = x[2 * j + 1] + inf - rec;
+  }
+}
+
 // binary32 selection thresholds of state x, in the specification's order and
 // rounding: a_inf,1, P_1, P_1 + a_inf,2, P_2, ...; a0~ = P_NA.  Returns whether
 // any rate is positive (exact, from the counts and constants).
@@ -436,21 +453,7 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
       // draws after e, which cannot matter.
       int ch = -3;
       for (int it = 0; it <= 32; ++it) {
-        const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
-        int32_t inc = enc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int32_t y = __shfl_up_sync(full, inc, o);
-          if (lane >= o) inc += y;
-        }
-        int32_t rest = inc - enc;                  // exclusive prefix
-#pragma unroll
-        for (int j = 0; j < NA; ++j) {
-          const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
-          rest = (rest - d) >> 10;
-          xs[2 * j] = x[2 * j] - d;
-          xs[2 * j + 1] = x[2 * j + 1] + d;
-        }
+        prefix_state<NA, 32>(x, ch, lane, xs);
         float T[2 * NA - 1], a0f;
         int nc = -2;
         const bool valid = thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f);
@@ -502,25 +505,11 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
       // it and decides its own draw there.  A lane whose predecessors' guesses are
       // right decides right, so each round confirms at least one more leading lane
       // and the iteration stops, after at most 33 rounds, with every guess equal to
-      // the sequential chain's choice.  Guesses are net infections per class,
-      // 10-bit fields of one int (|count| <= 32), summed by a warp scan.
+      // the sequential chain's choice.  The lanes' states come from ballots of the
+      // guesses (prefix_state).
       int ch = -3;                                 // -3: no guess yet, -2: a0 = 0 here
       for (int it = 0; it <= 32; ++it) {
-        const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
-        int32_t inc = enc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int32_t y = __shfl_up_sync(full, inc, o);
-          if (lane >= o) inc += y;
-        }
-        int32_t rest = inc - enc;                  // exclusive prefix
-#pragma unroll
-        for (int j = 0; j < NA; ++j) {
-          const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
-          rest = (rest - d) >> 10;
-          xs[2 * j] = x[2 * j] - d;
-          xs[2 * j + 1] = x[2 * j + 1] + d;
-        }
+        prefix_state<NA, 32>(x, ch, lane, xs);
         float T[2 * NA - 1], a0f;
         int nc = -2;
         if (thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f)) {
@@ -673,21 +662,7 @@ __device__ __forceinline__ int32_t ssa_seg_node_day(const DevParams& p, uint64_t
     bool valid = false;
     unsigned okb = 0;
     for (int it = 0; it <= SEG; ++it) {
-      const int32_t enc = ch >= 0 ? ((ch & 1) ? -1 : 1) * (1 << (10 * (ch >> 1))) : 0;
-      int32_t inc = enc;
-#pragma unroll
-      for (int o = 1; o < SEG; o <<= 1) {
-        const int32_t y = __shfl_up_sync(full, inc, o, SEG);
-        if (gl >= o) inc += y;
-      }
-      int32_t rest = inc - enc;
-#pragma unroll
-      for (int j = 0; j < NA; ++j) {
-        const int32_t d = (j + 1 < NA) ? ((int32_t)((uint32_t)rest << 22) >> 22) : rest;
-        rest = (rest - d) >> 10;
-        xs[2 * j] = s.x[2 * j] - d;
-        xs[2 * j + 1] = s.x[2 * j + 1] + d;
-      }
+      prefix_state<NA, SEG>(s.x, ch, lane, xs);
       float T[2 * NA - 1], a0f;
       int nc = -2;
       valid = !done && thresholds_f32<NA>(cpos, gpos, cinff, gamf, xs, T, a0f);
