@@ -253,6 +253,32 @@ enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3,
 enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 
+/* Replaces every replicate's parameters (same layout and checks as sim_create;
+ * invalid values: SIM_E_INVALID_ARG, nothing changed).  The state, events and
+ * statistics stay; the next sim_run_days uses the new values.  Synchronises the
+ * device.  (For parameter searches: no rebuild of the event schedule.) */
+sim_status sim_set_params(sim_handle* h, const sim_params* p);
+
+/* Region statistics of the parameter-fitting goal (Sec. 4.3, Eqs. (goal),
+ * (goalvariance), (goalsigma)).  sim_set_regions assigns every node a region
+ * (region_of_node [N] host, values in [0, n_regions); n_regions = 0 switches the
+ * statistics off); from then on, after each simulated day d, every replicate's
+ * region totals x_jc (sum over region j's nodes of compartment c) are added into
+ * s1[d][j][c] = sum over replicates of x_jc and s2[d][j][c] = sum of x_jc^2, exact
+ * uint64 (one extra launch per day; not with SIM_LAUNCH_PERSISTENT, which then
+ * fails with SIM_E_STATE; the split day step is off meanwhile).  sim_set_state at
+ * day D clears rows >= D; sim_reset clears all.
+ * sim_region_moments copies s1, s2 [max_days][n_regions][Nc] to host (either may
+ * be NULL).  sim_goal computes on the device, over days [day0, day0 + ndays),
+ * with R = the handle's replicates as trajectories and ref [ndays][n_regions][Nc]
+ * (host int64: a reference trajectory's region totals):
+ *   g2  = sum (s1 / R - ref)^2,   vg2 = sum (s2 - s1^2 / R) / (R - 1)
+ * (0 when R = 1), each difference and variance formed exactly in 128-bit integers
+ * and summed in a fixed order.  Both synchronise the device. */
+sim_status sim_set_regions(sim_handle* h, const int32_t* region_of_node, int32_t n_regions);
+sim_status sim_region_moments(sim_handle* h, uint64_t* s1, uint64_t* s2);
+sim_status sim_goal(sim_handle* h, const int64_t* ref, int32_t day0, int32_t ndays, double* g2, double* vg2);
+
 /* Batched and uneven runs: advances every listed handle (all on the current
  * device; any mix of models, node and replicate counts, horizons, events and
  * parameters) to day until[i] (NULL: each handle's max_days) in ONE persistent

@@ -88,6 +88,10 @@ def load_library(build_if_missing: bool = True):
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
             "sim_run_batch": [P(vp), i32, pi32, vp],
             "sim_set_option": [vp, i32, i64],
+            "sim_set_regions": [vp, pi32, i32],
+            "sim_set_params": [vp, vp],
+            "sim_region_moments": [vp, vp, vp],
+            "sim_goal": [vp, pi64, i32, i32, pd, pd],
             "sim_debug_batch_spin_limit": [i64],
             "sim_debug_batch_stall": [vp, i32, i64],
             "sim_profile_read": [vp, pd, pi64],
@@ -271,6 +275,41 @@ class Sim:
     def set_group_threshold(self, herd):
         """Herd size from which a node gets an 8-lane group (-1 automatic; results unchanged)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 6, int(herd)))
+
+    def set_params(self, params: W.Params):
+        """Replaces every replicate's parameters (state, events and statistics stay)."""
+        if params.upsilon.shape[0] != self.R:
+            raise ValueError("parameters for a different replicate count")
+        keep = [np.ascontiguousarray(x, np.float64) for x in
+                (params.upsilon, params.gamma, params.alpha, params.beta, params.epsilon)]
+        sp = SimParams(*[_p(a, ctypes.c_double) for a in keep])
+        _check(self.L, self.h, self.L.sim_set_params(self.h, ctypes.byref(sp)))
+        self._keep = keep
+
+    def set_regions(self, region_of_node, n_regions):
+        """Region statistics of the fitting goal (region_of_node [N], values < n_regions)."""
+        arr = np.ascontiguousarray(region_of_node, np.int32)
+        self.n_regions = int(n_regions)
+        _check(self.L, self.h, self.L.sim_set_regions(self.h, _p(arr, ctypes.c_int32), int(n_regions)))
+
+    def region_moments(self):
+        """(s1, s2) uint64 [max_days, n_regions, Nc]: sums over replicates of the
+        daily region totals and of their squares."""
+        shape = (self.max_days, self.n_regions, self.nc)
+        s1 = np.zeros(shape, np.uint64)
+        s2 = np.zeros(shape, np.uint64)
+        _check(self.L, self.h, self.L.sim_region_moments(self.h, ctypes.c_void_p(s1.ctypes.data),
+                                                         ctypes.c_void_p(s2.ctypes.data)))
+        return s1, s2
+
+    def goal(self, ref, day0, ndays):
+        """(G^2, VG^2) over days [day0, day0 + ndays) against ref [ndays, n_regions, Nc]."""
+        r = np.ascontiguousarray(ref, np.int64)
+        g2 = ctypes.c_double(0.0)
+        vg2 = ctypes.c_double(0.0)
+        _check(self.L, self.h, self.L.sim_goal(self.h, _p(r, ctypes.c_int64), int(day0), int(ndays),
+                                               ctypes.byref(g2), ctypes.byref(vg2)))
+        return g2.value, vg2.value
 
     def set_split(self, on):
         """Untouched herds' stochastic step alongside the previous day's events (results unchanged)."""

@@ -59,6 +59,15 @@ struct sim_handle {
   uint32_t* d_skip = nullptr;          // [max_days][ceil(N/32)] touched-herd bitmaps
   int32_t* d_tlist = nullptr;          // per day: touched herds, warp-path ones first, largest first
   cudaStream_t side = nullptr;         // stream of the untouched herds' step
+  // region statistics of the fitting goal
+  int32_t n_regions = 0;
+  int32_t* d_reg_nodes = nullptr;      // nodes sorted by region
+  int32_t* d_reg_off = nullptr;        // [J + 1]
+  unsigned long long* d_s1 = nullptr;  // [max_days][J][Nc]
+  unsigned long long* d_s2 = nullptr;
+  long long* d_ref = nullptr;          // scratch for sim_goal
+  double* d_goal = nullptr;
+  size_t ref_cap = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_phi0 = nullptr;
   // event schedule
@@ -166,8 +175,16 @@ void free_graph(sim_handle* h) {
   h->graph_d0 = h->graph_nd = -1;
 }
 
+void free_regions(sim_handle* h) {
+  cudaFree(h->d_reg_nodes); cudaFree(h->d_reg_off); cudaFree(h->d_s1); cudaFree(h->d_s2);
+  cudaFree(h->d_ref); cudaFree(h->d_goal);
+  h->d_reg_nodes = h->d_reg_off = nullptr; h->d_s1 = h->d_s2 = nullptr; h->d_ref = nullptr; h->d_goal = nullptr;
+  h->n_regions = 0; h->ref_cap = 0;
+}
+
 void free_all(sim_handle* h) {
   free_graph(h);
+  free_regions(h);
   free_split(h);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -187,6 +204,31 @@ size_t n_counts(const sim_handle* h) { return (size_t)h->cfg.n_replicates * h->n
 size_t n_phi(const sim_handle* h) { return (size_t)h->cfg.n_replicates * h->cfg.n_nodes; }
 
 // Initial state for every replicate and cleared accumulators (synchronous).
+// Per-replicate constants from the public struct, validated (finite, >= 0,
+// beta <= 1); errors are reported on handle eh (NULL: the creation error).
+sim_status fill_params(const sim_handle* h, sim_handle* eh, const sim_params* p, std::vector<DevParams>& out) {
+  const int R = h->cfg.n_replicates;
+  if (!p->upsilon || !p->gamma || !p->alpha || !p->beta || !p->epsilon)
+    return fail(eh, SIM_E_INVALID_ARG, "null parameter array");
+  for (int r = 0; r < R; ++r) {
+    DevParams& d = out[(size_t)r];
+    std::memset(&d, 0, sizeof d);
+    for (int j = 0; j < 3; ++j) {
+      d.ups[j] = p->upsilon[(size_t)r * 3 + j];
+      d.gam[j] = p->gamma[(size_t)r * 3 + j];
+    }
+    d.alpha = p->alpha[r];
+    for (int s2 = 0; s2 < 4; ++s2) d.beta[s2] = p->beta[(size_t)r * 4 + s2];
+    d.eps = p->epsilon[r];
+    bool ok = finite_nonneg(d.alpha) && finite_nonneg(d.eps);
+    for (int j = 0; j < 3; ++j) ok = ok && finite_nonneg(d.ups[j]) && finite_nonneg(d.gam[j]);
+    for (int s2 = 0; s2 < 4; ++s2) ok = ok && finite_nonneg(d.beta[s2]) && d.beta[s2] <= 1.0;
+    if (!ok)
+      return fail(eh, SIM_E_INVALID_ARG, "replicate %d: parameters must be finite, >= 0, and beta <= 1", r);
+  }
+  return SIM_OK;
+}
+
 sim_status reset_state(sim_handle* h) {
   const size_t cbytes = (size_t)h->nc * h->cfg.n_nodes * sizeof(int32_t);
   const size_t pbytes = (size_t)h->cfg.n_nodes * sizeof(double);
@@ -197,6 +239,11 @@ sim_status reset_state(sim_handle* h) {
   CK(h, cudaMemset(h->d_prev_n, 0, stats * 8), "clear stats");
   CK(h, cudaMemset(h->d_ctr, 0, (size_t)h->cfg.n_replicates * 4 * 8), "clear counters");
   CK(h, cudaMemset(h->d_err, 0, sizeof(int32_t)), "clear error");
+  if (h->n_regions > 0) {
+    const size_t rows = (size_t)std::max(1, h->cfg.max_days) * h->n_regions * h->nc;
+    CK(h, cudaMemset(h->d_s1, 0, rows * 8), "clear region statistics");
+    CK(h, cudaMemset(h->d_s2, 0, rows * 8), "clear region statistics");
+  }
   if (h->d_score) {
     CK(h, cudaMemset(h->d_score, 0, n_phi(h) * kScoreTerms * sizeof(double)), "clear score");
     CK(h, cudaMemset(h->d_tang, 0, n_phi(h) * 2 * sizeof(double)), "clear tangents");
@@ -760,24 +807,9 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     if (tot > (1 << 30)) { delete h; return fail(nullptr, SIM_E_INVALID_ARG, "node %d holds more than 2^30 animals", v); }
     if (!finite_nonneg(phi0[v])) { delete h; return fail(nullptr, SIM_E_INVALID_ARG, "phi0[%d] must be finite and >= 0", v); }
   }
-  for (int r = 0; r < R; ++r) {
-    DevParams& d = h->params[r];
-    std::memset(&d, 0, sizeof d);
-    for (int j = 0; j < 3; ++j) {
-      d.ups[j] = p->upsilon[(size_t)r * 3 + j];
-      d.gam[j] = p->gamma[(size_t)r * 3 + j];
-    }
-    d.alpha = p->alpha[r];
-    for (int s = 0; s < 4; ++s) d.beta[s] = p->beta[(size_t)r * 4 + s];
-    d.eps = p->epsilon[r];
-    bool ok = finite_nonneg(d.alpha) && finite_nonneg(d.eps);
-    for (int j = 0; j < 3; ++j) ok = ok && finite_nonneg(d.ups[j]) && finite_nonneg(d.gam[j]);
-    for (int s = 0; s < 4; ++s) ok = ok && finite_nonneg(d.beta[s]) && d.beta[s] <= 1.0;
-    if (!ok) {
-      delete h;
-      return fail(nullptr, SIM_E_INVALID_ARG,
-                  "replicate %d: parameters must be finite, >= 0, and beta <= 1", r);
-    }
+  {
+    const sim_status ps = fill_params(h, nullptr, p, h->params);
+    if (ps != SIM_OK) { delete h; return ps; }
   }
   cudaError_t e = cudaSuccess;
   {
@@ -955,7 +987,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   // stream as soon as day d's stochastic step is complete (alongside d's event
   // step), and the touched herds after the event step; the side launch is joined
   // before the event step of day d + 1.  Without events the day is one launch.
-  const bool split = h->split && !score && h->events_loaded && h->d_skip && h->d_tlist;
+  const bool split = h->split && !score && h->events_loaded && h->d_skip && h->d_tlist && h->n_regions == 0;
   const size_t words = ((size_t)h->cfg.n_nodes + 31) / 32;
   if (split && !h->side) {
     CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
@@ -1010,6 +1042,9 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
         CK(h, traced(h, 1, st, [&] { return launch_events_day(ev, h->n_age, st); }), "event step launch");
       }
     }
+    if (h->n_regions > 0)                            // region totals of the state after day d
+      CK(h, launch_region_day(h->d_counts, h->d_reg_nodes, h->d_reg_off, h->cfg.n_nodes, h->cfg.n_replicates,
+                              h->nc, h->n_regions, d, h->d_s1, h->d_s2, st), "region statistics launch");
   }
   a.day = d0 + ndays - 1;
   CK(h, traced(h, 2, st, [&] { return launch_finalize(a, h->n_age, score, st); }), "phi update launch");
@@ -1023,6 +1058,8 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   if (ndays == 0) return SIM_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t d0 = h->day;
+  if (h->launch_mode == 2 && !h->profiling && h->n_regions > 0)
+    return fail(h, SIM_E_STATE, "region statistics need the stream or graph launch mode");
   if (h->launch_mode == 2 && !h->profiling) {
     const int32_t until = d0 + ndays;
     sim_handle* one[1] = {h};
@@ -1124,6 +1161,11 @@ sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi
     CK(h, cudaMemset2DAsync(h->d_prev_i + day, pitch, 0, w, h->cfg.n_replicates, st), "clear stats");
     CK(h, cudaMemset2DAsync(h->d_prev_n + day, pitch, 0, w, h->cfg.n_replicates, st), "clear stats");
   }
+  if (h->n_regions > 0 && T > day) {
+    const size_t row = (size_t)h->n_regions * h->nc, bytes = (size_t)(T - day) * row * 8;
+    CK(h, cudaMemsetAsync(h->d_s1 + (size_t)day * row, 0, bytes, st), "clear region statistics");
+    CK(h, cudaMemsetAsync(h->d_s2 + (size_t)day * row, 0, bytes, st), "clear region statistics");
+  }
   if (h->d_score) {
     CK(h, cudaMemsetAsync(h->d_score, 0, n_phi(h) * kScoreTerms * 8, st), "clear score");
     CK(h, cudaMemsetAsync(h->d_tang, 0, n_phi(h) * 2 * 8, st), "clear tangents");
@@ -1187,6 +1229,86 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
   if (per_rep) CK(h, cudaMemcpyAsync(per_rep, h->d_per_rep, (size_t)h->cfg.n_replicates * kScoreTerms * 8, cudaMemcpyDeviceToHost, st), "copy scores");
   if (n_days > 0) CK(h, cudaMemcpyAsync(out, h->d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st), "copy moments");
   CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  return check_latched(h);
+}
+
+sim_status sim_set_params(sim_handle* h, const sim_params* p) {
+  if (!h || !p) return SIM_E_INVALID_ARG;
+  std::vector<DevParams> next((size_t)h->cfg.n_replicates);
+  const sim_status s = fill_params(h, h, p, next);
+  if (s != SIM_OK) return s;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  CK(h, cudaMemcpy(h->d_params, next.data(), next.size() * sizeof(DevParams), cudaMemcpyHostToDevice),
+     "parameter upload");
+  h->params.swap(next);
+  return SIM_OK;
+}
+
+sim_status sim_set_regions(sim_handle* h, const int32_t* region_of_node, int32_t n_regions) {
+  if (!h) return SIM_E_INVALID_ARG;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  free_regions(h);
+  free_graph(h);
+  if (n_regions == 0) return SIM_OK;
+  const int N = h->cfg.n_nodes;
+  if (n_regions < 0 || !region_of_node) return fail(h, SIM_E_INVALID_ARG, "n_regions must be >= 0 with a region array");
+  std::vector<int32_t> off((size_t)n_regions + 1, 0), nodes((size_t)N);
+  for (int v = 0; v < N; ++v) {
+    const int32_t j = region_of_node[v];
+    if (j < 0 || j >= n_regions) return fail(h, SIM_E_INVALID_ARG, "node %d: region %d out of range", v, j);
+    off[(size_t)j + 1]++;
+  }
+  for (int32_t j = 0; j < n_regions; ++j) off[(size_t)j + 1] += off[(size_t)j];
+  {
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int v = 0; v < N; ++v) nodes[(size_t)fill[(size_t)region_of_node[v]]++] = v;
+  }
+  const size_t rows = (size_t)std::max(1, h->cfg.max_days) * n_regions * h->nc;
+  cudaError_t e = dalloc(&h->d_reg_nodes, nodes.size());
+  if (e == cudaSuccess) e = dalloc(&h->d_reg_off, off.size());
+  if (e == cudaSuccess) e = dalloc(&h->d_s1, rows);
+  if (e == cudaSuccess) e = dalloc(&h->d_s2, rows);
+  if (e == cudaSuccess) e = dalloc(&h->d_goal, 2);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_reg_nodes, nodes.data(), nodes.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_reg_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->d_s1, 0, rows * 8);
+  if (e == cudaSuccess) e = cudaMemset(h->d_s2, 0, rows * 8);
+  if (e != cudaSuccess) { free_regions(h); return cuda_fail(h, e, "region statistics"); }
+  h->n_regions = n_regions;
+  return SIM_OK;
+}
+
+sim_status sim_region_moments(sim_handle* h, uint64_t* s1, uint64_t* s2) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (h->n_regions == 0) return fail(h, SIM_E_STATE, "no regions set");
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  const size_t rows = (size_t)h->cfg.max_days * h->n_regions * h->nc;
+  if (s1 && rows) CK(h, cudaMemcpy(s1, h->d_s1, rows * 8, cudaMemcpyDeviceToHost), "copy region statistics");
+  if (s2 && rows) CK(h, cudaMemcpy(s2, h->d_s2, rows * 8, cudaMemcpyDeviceToHost), "copy region statistics");
+  return check_latched(h);
+}
+
+sim_status sim_goal(sim_handle* h, const int64_t* ref, int32_t day0, int32_t ndays, double* g2, double* vg2) {
+  if (!h || !ref || !g2 || !vg2) return SIM_E_INVALID_ARG;
+  if (h->n_regions == 0) return fail(h, SIM_E_STATE, "no regions set");
+  if (day0 < 0 || ndays < 1 || (int64_t)day0 + ndays > h->cfg.max_days)
+    return fail(h, SIM_E_INVALID_ARG, "days [%d, %d + %d) outside [0, max_days)", day0, day0, ndays);
+  const size_t row = (size_t)h->n_regions * h->nc, count = (size_t)ndays * row;
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  if (h->ref_cap < count) {
+    cudaFree(h->d_ref);
+    h->d_ref = nullptr;
+    h->ref_cap = 0;
+    CK(h, dalloc(&h->d_ref, count), "goal reference allocation");
+    h->ref_cap = count;
+  }
+  CK(h, cudaMemcpy(h->d_ref, ref, count * 8, cudaMemcpyHostToDevice), "goal reference upload");
+  CK(h, launch_goal(h->d_s1, h->d_s2, h->d_ref, (long long)((size_t)day0 * row), (long long)count,
+                    h->cfg.n_replicates, h->d_goal, 0), "goal launch");
+  double out[2];
+  CK(h, cudaMemcpy(out, h->d_goal, 16, cudaMemcpyDeviceToHost), "goal copy");
+  *g2 = out[0];
+  *vg2 = out[1];
   return check_latched(h);
 }
 

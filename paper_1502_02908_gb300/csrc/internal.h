@@ -152,6 +152,13 @@ struct FinalizeArgs {
 };
 
 cudaError_t launch_ssa_day(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
+// Region totals of day `day` for every replicate, added (and squared) into s1 / s2
+// [max_days][J][Nc]; the goal terms over count entries of s1 / s2 from `first`.
+cudaError_t launch_region_day(const int32_t* counts, const int32_t* reg_nodes, const int32_t* reg_off, int N, int R,
+                              int Nc, int J, int day, unsigned long long* s1, unsigned long long* s2,
+                              cudaStream_t st);
+cudaError_t launch_goal(const unsigned long long* s1, const unsigned long long* s2, const long long* ref,
+                        long long first, long long count, int R, double* out, cudaStream_t st);
 cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
 // After the last day of a call: phi update (post-event mode) and statistics of day a.day.
 cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
