@@ -21,6 +21,8 @@ import numpy as np
 
 _HERE = pathlib.Path(__file__).resolve().parent
 _SRC = _HERE / "oracle.c"
+_SOURCES = [_HERE / "oracle.c", _HERE / "general.c"]
+_HEADERS = [_HERE / "oracle_rng.h"]
 _BUILD = _HERE / "_build"
 _LIB = None
 _LOCK = threading.Lock()
@@ -41,14 +43,36 @@ class OrcCounters(ctypes.Structure):
                 ("events_clamped", ctypes.c_int64), ("events_skipped", ctypes.c_int64)]
 
 
+GO_MAX_COMP, GO_MAX_TRANS, GO_MAX_CONT, GO_MAX_SELECT, GO_MAX_SHIFT = 16, 32, 4, 32, 32
+
+
+class GoModel(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int32), ("n_trans", ctypes.c_int32), ("n_cont", ctypes.c_int32),
+                ("n_select", ctypes.c_int32), ("n_shift", ctypes.c_int32), ("y_source", ctypes.c_int32),
+                ("stoich", ctypes.c_int32 * (GO_MAX_COMP * GO_MAX_TRANS)),
+                ("fa", ctypes.c_int32 * GO_MAX_TRANS), ("fb", ctypes.c_int32 * GO_MAX_TRANS),
+                ("fy", ctypes.c_int32 * GO_MAX_TRANS), ("pop", ctypes.c_uint32 * GO_MAX_TRANS),
+                ("num", ctypes.c_uint32 * GO_MAX_CONT), ("den", ctypes.c_uint32 * GO_MAX_CONT),
+                ("select", ctypes.c_uint32 * GO_MAX_SELECT),
+                ("shift", ctypes.c_int32 * (GO_MAX_SHIFT * GO_MAX_COMP))]
+
+
+class GoCfg(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("replicate", ctypes.c_int32),
+                ("underflow_error", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("rate", ctypes.c_double * GO_MAX_TRANS), ("alpha", ctypes.c_double * GO_MAX_CONT),
+                ("beta", (ctypes.c_double * 4) * GO_MAX_CONT), ("epsilon", ctypes.c_double * GO_MAX_CONT)]
+
+
 def build(force: bool = False) -> pathlib.Path:
     """Compiles oracle.c into _build/liboracle.so (gcc -O2, no FP contraction)."""
     _BUILD.mkdir(exist_ok=True)
     out = _BUILD / "liboracle.so"
-    if force or not out.exists() or out.stat().st_mtime < _SRC.stat().st_mtime:
+    newest = max(p.stat().st_mtime for p in _SOURCES + _HEADERS)
+    if force or not out.exists() or out.stat().st_mtime < newest:
         tmp = _BUILD / f"liboracle.{os.getpid()}.so"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                        "-o", str(tmp), str(_SRC), "-lm"], check=True)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-I", str(_HERE),
+                        "-o", str(tmp)] + [str(p) for p in _SOURCES] + ["-lm"], check=True)
         os.replace(tmp, out)
     return out
 
@@ -66,6 +90,9 @@ def load(path):
     L.orc_apply_events.restype = ctypes.c_int
     L.orc_apply_events.argtypes = [P(OrcCfg), P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_int64)] + \
                                   [P(ctypes.c_int32)] * 6 + [P(OrcCounters)]
+    L.go_run.restype = ctypes.c_int
+    L.go_run.argtypes = [P(GoModel), P(GoCfg), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int32,
+                         ctypes.c_int32, ctypes.c_int64] + [P(ctypes.c_int32)] * 7 + [P(OrcCounters)]
     L.orc_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
     L.orc_uniform.restype = ctypes.c_double
     L.orc_uniform.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -84,13 +111,14 @@ def load(path):
     return L
 
 
-def compile_variant(source_text, out_path):
-    """Compiles a modified copy of oracle.c (used by the tests that plant
-    mistakes in the oracle to show that its pins catch them)."""
+def compile_variant(source_text, out_path, which="oracle.c"):
+    """Compiles the oracle with a modified copy of one of its sources (used by
+    the tests that plant mistakes in the oracle to show that its pins catch them)."""
     src = pathlib.Path(out_path).with_suffix(".c")
     src.write_text(source_text)
-    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                    "-o", str(out_path), str(src), "-lm"], check=True)
+    others = [str(p) for p in _SOURCES if p.name != which]
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-I", str(_HERE),
+                    "-o", str(out_path), str(src)] + others + ["-lm"], check=True)
     return load(out_path)
 
 
@@ -195,3 +223,69 @@ def apply_events(w, counts, pos, events, replicate=0, underflow_error=False):
     L.orc_apply_events(ctypes.byref(cfg), _ptr(counts, ctypes.c_int32), len(pos), _ptr(pos, ctypes.c_int64),
                        *[_ptr(a, ctypes.c_int32) for a in arr], ctypes.byref(ctr))
     return (ctr.transitions, ctr.events_applied, ctr.events_clamped, ctr.events_skipped)
+
+
+def _go_model(m):
+    g = GoModel()
+    g.n_comp, g.n_trans, g.n_cont = m.nc, m.nt, m.ny
+    g.n_select, g.n_shift, g.y_source = int(m.select.size), int(m.shift.shape[0]), int(m.y_source)
+    for c in range(m.nc):
+        for j in range(m.nt):
+            g.stoich[c * m.nt + j] = int(m.stoich[c, j])
+    for j in range(m.nt):
+        g.fa[j], g.fb[j], g.fy[j], g.pop[j] = int(m.factor_a[j]), int(m.factor_b[j]), int(m.cont[j]), int(m.pop_mask[j])
+    for q in range(m.ny):
+        g.num[q], g.den[q] = int(m.num_mask[q]), int(m.den_mask[q])
+    for s in range(m.select.size):
+        g.select[s] = int(m.select[s])
+    for s in range(m.shift.shape[0]):
+        for c in range(m.nc):
+            g.shift[s * GO_MAX_COMP + c] = int(m.shift[s, c])
+    return g
+
+
+class GeneralResult:
+    """Per-replicate results: counts [R, Nc, N], y [R, Ny, N], counters [R, 4]."""
+
+    def __init__(self, counts, y, counters):
+        self.counts, self.y, self.counters = counts, y, counters
+
+
+def run_general(w, ndays=None, d0=0, replicates=None, counts=None, y=None, events=None, model=None,
+                lib_handle=None):
+    """Runs the general-model oracle for the workload ``w``
+    (paper_1502_02908_gb300.workloads.GeneralWorkload); ``counts`` [R', Nc, N] and
+    ``y`` [R', Ny, N] override the initial state, ``model`` the descriptor."""
+    m = w.model if model is None else model
+    ndays = w.T if ndays is None else ndays
+    reps = list(range(w.R)) if replicates is None else list(replicates)
+    ev = w.events if events is None else events
+    gm = _go_model(m)
+    arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (ev.day, ev.kind, ev.node, ev.dest, ev.count,
+                                                                ev.select, ev.shift)]
+    out_c = np.empty((len(reps), m.nc, w.N), np.int32)
+    out_y = np.empty((len(reps), m.ny, w.N), np.float64)
+    ctrs = np.zeros((len(reps), 4), np.int64)
+    L = lib_handle if lib_handle is not None else lib()
+    for i, r in enumerate(reps):
+        c = np.ascontiguousarray(w.u0 if counts is None else counts[i], dtype=np.int32).copy()
+        yy = np.ascontiguousarray(w.y0 if y is None else y[i], dtype=np.float64).reshape(m.ny, w.N).copy()
+        g = GoCfg()
+        g.n_nodes, g.replicate, g.underflow_error, g.seed = w.N, r, int(bool(w.underflow_error)), w.seed
+        for j in range(m.nt):
+            g.rate[j] = float(w.rates[r, j])
+        for q in range(m.ny):
+            g.alpha[q] = float(w.var_params[r, q, 0])
+            for s in range(4):
+                g.beta[q][s] = float(w.var_params[r, q, 1 + s])
+            g.epsilon[q] = float(w.var_params[r, q, 5])
+        ctr = OrcCounters()
+        rc = L.go_run(ctypes.byref(gm), ctypes.byref(g), _ptr(c, ctypes.c_int32),
+                      _ptr(yy if m.ny else np.zeros(1), ctypes.c_double), d0, ndays, len(ev),
+                      *[_ptr(a, ctypes.c_int32) for a in arrs], ctypes.byref(ctr))
+        if rc != 0:
+            raise ValueError("oracle rejected its arguments")
+        out_c[i] = c
+        out_y[i] = yy
+        ctrs[i] = (ctr.transitions, ctr.events_applied, ctr.events_clamped, ctr.events_skipped)
+    return GeneralResult(out_c, out_y, ctrs)

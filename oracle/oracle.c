@@ -44,6 +44,8 @@
 #include <string.h>
 #include <math.h>
 
+#include "oracle_rng.h"
+
 #define ORC_SISE  1
 #define ORC_SISE3 3
 
@@ -187,12 +189,6 @@ double orc_neglog(uint64_t j)
 }
 
 /* ------------------------------------------------------------ events RNG */
-typedef struct {
-    uint32_t key[2];
-    uint32_t ctr[4];
-    uint32_t buf[4];
-    uint32_t q;                /* next word index */
-} word_stream;
 
 static void ws_init(word_stream* s, const orc_cfg* c, int64_t ev_index, int32_t day)
 {
@@ -219,6 +215,15 @@ static uint32_t lemire(word_stream* ws, uint32_t s)
     }
     return (uint32_t)(m >> 32);
 }
+
+void orc_ws_start(word_stream* s, uint64_t seed, int32_t replicate, int64_t ev_index, int32_t day)
+{
+    orc_cfg c; memset(&c, 0, sizeof c);
+    c.seed = seed; c.replicate = replicate;
+    ws_init(s, &c, ev_index, day);
+}
+
+uint32_t orc_ws_lemire(word_stream* s, uint32_t bound) { return lemire(s, bound); }
 
 /* ---------------------------------------------------------------- model */
 static int n_age(const orc_cfg* c) { return c->model == ORC_SISE3 ? 3 : 1; }

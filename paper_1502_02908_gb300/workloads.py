@@ -347,3 +347,271 @@ def uneven_batch(n_inst=512, N_lo=100, N_hi=50_000, T_lo=90, T_hi=1460, events_p
                                   alp, bet, 1e-6)
         out.append(Workload(f"uneven_{i}", model, N, T, R, u0, np.zeros(N), params, ev, seed=1000 + i))
     return out
+
+
+# ------------------------------------------------------------------ general model
+# Inputs of the general compartment model (include/episim_general.h): a model
+# descriptor (stoichiometry, propensity factors, continuous variables, event
+# compartment masks and offsets), initial state, per-replicate constants and
+# events.  Descriptors are data; the arithmetic they describe lives in the
+# library and the oracle.
+
+Y_POST_EVENT, Y_PRE_EVENT, Y_MIDPOINT = 0, 1, 2
+
+
+@dataclasses.dataclass
+class GeneralModel:
+    """stoich [Nc, Nt] int32; per transition factor_a, factor_b (compartment or
+    -1), cont (continuous variable or -1), pop_mask (uint32, 0: no division);
+    per variable num_mask, den_mask; select [n_select] compartment masks;
+    shift [n_shift, Nc] compartment offsets; y_source Y_*."""
+    comps: tuple
+    stoich: np.ndarray
+    factor_a: np.ndarray
+    factor_b: np.ndarray
+    cont: np.ndarray
+    pop_mask: np.ndarray
+    num_mask: np.ndarray
+    den_mask: np.ndarray
+    select: np.ndarray
+    shift: np.ndarray
+    y_source: int = Y_POST_EVENT
+
+    @property
+    def nc(self):
+        return int(self.stoich.shape[0])
+
+    @property
+    def nt(self):
+        return int(self.stoich.shape[1])
+
+    @property
+    def ny(self):
+        return int(self.num_mask.size)
+
+
+def general_model(comps, transitions, variables=(), selects=(), shifts=(), y_source=Y_POST_EVENT):
+    """Builds a GeneralModel from names.  transitions: dicts with "change"
+    {compartment: delta}, optional "a", "b" (compartment names), "cont" (variable
+    index) and "pop" (compartment names).  variables: (numerator names,
+    denominator names).  selects: tuples of names.  shifts: {name: offset}."""
+    idx = {c: i for i, c in enumerate(comps)}
+    nc, nt = len(comps), len(transitions)
+
+    def mask(names):
+        m = 0
+        for n in names:
+            m |= 1 << idx[n]
+        return m
+
+    stoich = np.zeros((nc, nt), np.int32)
+    fa = np.full(nt, -1, np.int32); fb = np.full(nt, -1, np.int32); fy = np.full(nt, -1, np.int32)
+    pop = np.zeros(nt, np.uint32)
+    for j, t in enumerate(transitions):
+        for c, d in t["change"].items():
+            stoich[idx[c], j] = d
+        if "a" in t: fa[j] = idx[t["a"]]
+        if "b" in t: fb[j] = idx[t["b"]]
+        if "cont" in t: fy[j] = t["cont"]
+        if "pop" in t: pop[j] = mask(t["pop"])
+    num = np.array([mask(v[0]) for v in variables], np.uint32)
+    den = np.array([mask(v[1]) for v in variables], np.uint32)
+    sel = np.array([mask(s) for s in selects], np.uint32)
+    sh = np.zeros((len(shifts), nc), np.int32)
+    for s, offs in enumerate(shifts):
+        for c, o in offs.items():
+            sh[s, idx[c]] = o
+    return GeneralModel(tuple(comps), stoich, fa, fb, fy, pop, num, den, sel, sh, y_source)
+
+
+@dataclasses.dataclass
+class GeneralEvents:
+    """int32 structure of arrays: day, kind (EXIT/ENTER/INTERNAL/EXTERNAL), node,
+    dest (-1 unless EXTERNAL), count, select (mask index), shift (-1: none)."""
+    day: np.ndarray
+    kind: np.ndarray
+    node: np.ndarray
+    dest: np.ndarray
+    count: np.ndarray
+    select: np.ndarray
+    shift: np.ndarray
+
+    def __len__(self):
+        return int(self.day.size)
+
+    @staticmethod
+    def empty():
+        z = np.zeros(0, np.int32)
+        return GeneralEvents(*(z.copy() for _ in range(7)))
+
+    def take(self, mask):
+        return GeneralEvents(*(np.ascontiguousarray(getattr(self, f.name)[mask])
+                               for f in dataclasses.fields(self)))
+
+
+@dataclasses.dataclass
+class GeneralWorkload:
+    name: str
+    model: GeneralModel
+    N: int
+    T: int
+    R: int
+    u0: np.ndarray           # [Nc, N] int32
+    y0: np.ndarray           # [Ny, N] float64
+    rates: np.ndarray        # [R, Nt] float64
+    var_params: np.ndarray   # [R, Ny, 6]: alpha, beta[4], epsilon
+    events: GeneralEvents
+    seed: int
+    underflow_error: bool = False
+
+
+def _var_params(R, ny, alpha, beta, epsilon):
+    vp = np.zeros((R, ny, 6))
+    for q in range(ny):
+        b = np.atleast_1d(np.asarray(beta[q], float))
+        vp[:, q, 0] = alpha[q]
+        vp[:, q, 1:5] = b if b.size == 4 else b[0]
+        vp[:, q, 5] = epsilon[q]
+    return vp
+
+
+def _general_events(rng, N, T, n_events, spec):
+    """spec: list of (probability, kind, select choices, shift choices); day and
+    node uniform, dest uniform != node for EXTERNAL, 1-5 animals (stable by day)."""
+    p = np.array([s[0] for s in spec], float)
+    which = rng.choice(len(spec), size=n_events, p=p / p.sum())
+    day = rng.integers(0, T, size=n_events)
+    node = rng.integers(0, N, size=n_events)
+    dest = rng.integers(0, N - 1, size=n_events)
+    dest = dest + (dest >= node)
+    count = rng.integers(1, 6, size=n_events)
+    kind = np.array([s[1] for s in spec])[which]
+    sel = np.empty(n_events, np.int64); sh = np.empty(n_events, np.int64)
+    for i, (_, _, sels, shs) in enumerate(spec):
+        rows = np.nonzero(which == i)[0]
+        sel[rows] = np.asarray(sels)[rng.integers(0, len(sels), size=rows.size)]
+        sh[rows] = np.asarray(shs)[rng.integers(0, len(shs), size=rows.size)]
+    dest = np.where(kind == EXTERNAL, dest, -1)
+    order = np.argsort(day, kind="stable")
+    return GeneralEvents(*(a[order].astype(np.int32) for a in (day, kind, node, dest, count, sel, sh)))
+
+
+def sir_general(N=2000, T=60, n_events=10_000, R=1, freq=True, beta=0.4, gamma=0.1, seed=1, gen_seed=11,
+                herd_lo=20, herd_hi=200):
+    """The SIR example of Eq. (SIRstoich): S + I -> 2I at beta S I (divided by the
+    node's population when freq), I -> R at gamma I.  Events: exits of any
+    animal, entries of susceptibles, vaccination S -> R (an internal move by
+    offset +2), transfers of any animal."""
+    m = general_model(("S", "I", "R"),
+                      [dict(change={"S": -1, "I": 1}, a="S", b="I", **({"pop": ("S", "I", "R")} if freq else {})),
+                       dict(change={"I": -1, "R": 1}, a="I")],
+                      selects=[("S", "I", "R"), ("S",)], shifts=[{"S": 2}])
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    herd = rng.integers(herd_lo, herd_hi + 1, size=N)
+    i0 = _round_half_even(0.05 * herd)
+    u0 = np.stack([herd - i0, i0, np.zeros(N, np.int64)]).astype(np.int32)
+    spec = [(0.4, EXIT, [0], [-1]), (0.3, ENTER, [1], [-1]), (0.1, INTERNAL, [1], [0]), (0.2, EXTERNAL, [0], [-1])]
+    ev = _general_events(rng, N, T, n_events, spec) if n_events else GeneralEvents.empty()
+    rates = np.tile(np.array([beta, gamma]), (R, 1))
+    return GeneralWorkload("sir", m, N, T, R, u0, np.zeros((0, N)), rates, np.zeros((R, 0, 6)), ev, seed)
+
+
+def seirs_env(N=3000, T=90, n_events=30_000, R=2, y_source=Y_POST_EVENT, seed=1, gen_seed=13):
+    """SEIRS with two continuous variables: y0 an environmental load fed by the
+    prevalence I/N (as phi in Eq. siminfpressure), y1 an exposure pressure fed by
+    the count E with no division.  Transitions: S -> E at k0 y0 S, at k1 S I / N
+    and at k5 y1 S; E -> I at k2 E; I -> R at k3 I; R -> S at k4 R.  Events:
+    exits (any animal), entries (susceptibles), vaccination S -> R (offset +3),
+    transfers (any animal, or only S and E)."""
+    comps = ("S", "E", "I", "R")
+    allc = comps
+    m = general_model(comps,
+                      [dict(change={"S": -1, "E": 1}, a="S", cont=0),
+                       dict(change={"S": -1, "E": 1}, a="S", b="I", pop=allc),
+                       dict(change={"E": -1, "I": 1}, a="E"),
+                       dict(change={"I": -1, "R": 1}, a="I"),
+                       dict(change={"R": -1, "S": 1}, a="R"),
+                       dict(change={"S": -1, "E": 1}, a="S", cont=1)],
+                      variables=[(("I",), allc), (("E",), ())],
+                      selects=[allc, ("S",), ("S", "E")], shifts=[{"S": 3}], y_source=y_source)
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    herd = np.minimum(2000, np.maximum(1, _round_half_even(rng.lognormal(math.log(60.0), 1.0, size=N))))
+    e0 = _round_half_even(0.02 * herd); i0 = _round_half_even(0.03 * herd)
+    u0 = np.stack([herd - e0 - i0, e0, i0, np.zeros(N, np.int64)]).astype(np.int32)
+    y0 = np.stack([rng.uniform(0.0, 0.05, size=N), np.zeros(N)])
+    spec = [(0.35, EXIT, [0], [-1]), (0.3, ENTER, [1], [-1]), (0.1, INTERNAL, [1], [0]),
+            (0.25, EXTERNAL, [0, 2], [-1])]
+    ev = _general_events(rng, N, T, n_events, spec) if n_events else GeneralEvents.empty()
+    base = np.array([0.02, 0.3, 0.2, 0.1, 0.01, 1e-4])
+    rates = base[None, :] * np.exp(rng.uniform(-0.3, 0.3, size=(R, base.size)))
+    vp = _var_params(R, 2, alpha=(1.0, 0.5), beta=(vtec_beta(), 0.2), epsilon=(1e-6, 0.0))
+    return GeneralWorkload("seirs_env", m, N, T, R, u0, y0, rates, vp, ev, seed)
+
+
+def erlang_sis(N=1500, T=40, n_events=8_000, stages=8, R=1, seed=1, gen_seed=17):
+    """SIS-like model with an Erlang-distributed infectious period: S, I1..Ik, R.
+    Infection S -> I1 at k0 y0 S (y0 the prevalence-fed environment) and at
+    k1 S I1 / N; progression I_i -> I_(i+1) and Ik -> R at k2 per animal; loss
+    of immunity R -> S at k3 R.  k + 3 transitions (11 for k = 8)."""
+    comps = ("S",) + tuple(f"I{i + 1}" for i in range(stages)) + ("R",)
+    inf = comps[1:-1]
+    tr = [dict(change={"S": -1, "I1": 1}, a="S", cont=0),
+          dict(change={"S": -1, "I1": 1}, a="S", b="I1", pop=comps)]
+    for i in range(stages):
+        nxt = comps[i + 2]
+        tr.append(dict(change={comps[i + 1]: -1, nxt: 1}, a=comps[i + 1]))
+    tr.append(dict(change={"R": -1, "S": 1}, a="R"))
+    m = general_model(comps, tr, variables=[(inf, comps)], selects=[comps, ("S",)])
+    rng = np.random.Generator(np.random.PCG64(gen_seed))
+    herd = rng.integers(20, 400, size=N)
+    u0 = np.zeros((len(comps), N), np.int32)
+    i1 = _round_half_even(0.05 * herd)
+    u0[0] = herd - i1; u0[1] = i1
+    spec = [(0.4, EXIT, [0], [-1]), (0.3, ENTER, [1], [-1]), (0.3, EXTERNAL, [0], [-1])]
+    ev = _general_events(rng, N, T, n_events, spec) if n_events else GeneralEvents.empty()
+    rates = np.tile(np.array([0.05, 0.2] + [float(stages) / 10.0] * stages + [0.02]), (R, 1))
+    vp = _var_params(R, 1, alpha=(1.0,), beta=(0.1,), epsilon=(1e-6,))
+    return GeneralWorkload("erlang_sis", m, N, T, R, u0, np.zeros((1, N)), rates, vp, ev, seed)
+
+
+def sise_model(y_source=Y_POST_EVENT, n_age=1):
+    """SISe (n_age 1) or SISe3 (n_age 3) in the general form: per class j,
+    S_j -> I_j at upsilon_j phi S_j and I_j -> S_j at gamma_j I_j, transitions in
+    the order inf_1, rec_1, inf_2, ...; phi fed by sum I / sum (S + I).  Event
+    masks: 0 every compartment, 1 + j class j, 1 + n_age + j the S of class j;
+    offset row 0 moves a class up by one (aging)."""
+    comps = tuple(c for j in range(n_age) for c in (f"S{j + 1}", f"I{j + 1}"))
+    tr = []
+    for j in range(n_age):
+        s, i = f"S{j + 1}", f"I{j + 1}"
+        tr.append(dict(change={s: -1, i: 1}, a=s, cont=0))
+        tr.append(dict(change={i: -1, s: 1}, a=i))
+    sel = [comps] + [(f"S{j + 1}", f"I{j + 1}") for j in range(n_age)] + [(f"S{j + 1}",) for j in range(n_age)]
+    shifts = [{c: 2 for c in comps}] if n_age > 1 else []
+    infected = tuple(f"I{j + 1}" for j in range(n_age))
+    return general_model(comps, tr, variables=[(infected, comps)], selects=sel, shifts=shifts, y_source=y_source)
+
+
+def as_general(w, y_source=Y_POST_EVENT):
+    """An SISe / SISe3 workload in the general form (same counts, phi, constants
+    and events).  Event cls maps to the class mask (cls = -1: every compartment),
+    enter to the S of its class, aging to the class mask with offset row 0."""
+    na = 1 if w.model == SISE else 3
+    m = sise_model(y_source, na)
+    ev = w.events
+    cls = ev.cls.astype(np.int64)
+    sel = np.where(cls < 0, 0, 1 + cls)
+    sel = np.where(ev.kind == ENTER, 1 + na + np.maximum(cls, 0), sel)
+    sh = np.where(ev.kind == INTERNAL, 0, -1)
+    gev = GeneralEvents(ev.day.copy(), ev.kind.copy(), ev.node.copy(), ev.dest.copy(), ev.count.copy(),
+                        sel.astype(np.int32), sh.astype(np.int32))
+    rates = np.zeros((w.R, 2 * na))
+    for j in range(na):
+        rates[:, 2 * j] = w.params.upsilon[:, j]
+        rates[:, 2 * j + 1] = w.params.gamma[:, j]
+    vp = np.zeros((w.R, 1, 6))
+    vp[:, 0, 0] = w.params.alpha
+    vp[:, 0, 1:5] = w.params.beta
+    vp[:, 0, 5] = w.params.epsilon
+    return GeneralWorkload(w.name + "_general", m, w.N, w.T, w.R, w.u0.copy(), w.phi0[None, :].copy(), rates, vp,
+                           gev, w.seed)
