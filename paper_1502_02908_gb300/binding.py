@@ -45,6 +45,23 @@ class SimParams(ctypes.Structure):
                 ("epsilon", ctypes.POINTER(ctypes.c_double))]
 
 
+class GenModel(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int32), ("n_trans", ctypes.c_int32), ("n_cont", ctypes.c_int32),
+                ("n_select", ctypes.c_int32), ("n_shift", ctypes.c_int32), ("y_source", ctypes.c_int32),
+                ("stoich", ctypes.POINTER(ctypes.c_int32)), ("trans", ctypes.POINTER(ctypes.c_int32)),
+                ("vars", ctypes.POINTER(ctypes.c_uint32)), ("select", ctypes.POINTER(ctypes.c_uint32)),
+                ("shift", ctypes.POINTER(ctypes.c_int32))]
+
+
+class GenConfig(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_replicates", ctypes.c_int32), ("max_days", ctypes.c_int32),
+                ("underflow_policy", ctypes.c_int32), ("seed", ctypes.c_uint64), ("replicate_base", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+GEN_OPT_LAUNCH = 1
+
+
 def library_path() -> pathlib.Path:
     from .build import LIB
     return LIB
@@ -95,6 +112,14 @@ def load_library(build_if_missing: bool = True):
             "sim_debug_batch_spin_limit": [i64],
             "sim_debug_batch_stall": [vp, i32, i64],
             "sim_profile_read": [vp, pd, pi64],
+            "gen_model_check": [P(GenModel), P(ctypes.c_uint32)],
+            "gen_create": [P(GenModel), P(GenConfig), pi32, pd, pd, pd, P(vp)],
+            "gen_load_events": [vp, i64, pi32, pi32, pi32, pi32, pi32, pi32, pi32],
+            "gen_run_days": [vp, i32, vp],
+            "gen_state": [vp, vp, vp, pi32, i32, vp],
+            "gen_set_state": [vp, vp, vp, i32, i32, vp],
+            "gen_counters": [vp, pi64],
+            "gen_set_option": [vp, i32, i64],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -104,6 +129,10 @@ def load_library(build_if_missing: bool = True):
         L.sim_destroy.restype = None
         L.sim_last_error.argtypes = [vp]
         L.sim_last_error.restype = ctypes.c_char_p
+        L.gen_destroy.argtypes = [vp]
+        L.gen_destroy.restype = None
+        L.gen_last_error.argtypes = [vp]
+        L.gen_last_error.restype = ctypes.c_char_p
         L.sim_warp_nodes.argtypes = [vp]
         L.sim_warp_nodes.restype = ctypes.c_int32
         L.sim_debug_schedule_size.argtypes = [vp]
@@ -113,10 +142,13 @@ def load_library(build_if_missing: bool = True):
 
 
 def header_symbols():
-    """Names of the functions include/episim.h declares."""
+    """Names of the functions the headers under include/ declare."""
     import re
-    text = HEADER.read_text()
-    return sorted(set(re.findall(r"^\s*(?:sim_status|void|const char\*|int64_t)\s+(sim_\w+)\s*\(", text, re.M)))
+    names = set()
+    for hdr in sorted(HEADER.parent.glob("*.h")):
+        names |= set(re.findall(r"^\s*(?:sim_status|void|const char\*|int64_t|int32_t)\s+((?:sim|gen)_\w+)\s*\(",
+                                hdr.read_text(), re.M))
+    return sorted(names)
 
 
 def _p(a, ct):
@@ -369,3 +401,119 @@ def debug_neglog_f32(j_dev_ptr, out_dev_ptr, n):
     L = load_library()
     st = L.sim_debug_neglog_f32(ctypes.c_void_p(j_dev_ptr), ctypes.c_void_p(out_dev_ptr), int(n))
     _check(L, None, st)
+
+
+def _gen_model(m: W.GeneralModel):
+    """The gen_model struct of a GeneralModel, with the arrays it points to."""
+    stoich = np.ascontiguousarray(m.stoich, np.int32)
+    trans = np.zeros((max(m.nt, 1), 4), np.int32)
+    trans[:m.nt, 0], trans[:m.nt, 1], trans[:m.nt, 2] = m.factor_a, m.factor_b, m.cont
+    trans[:m.nt, 3] = m.pop_mask.astype(np.uint32).view(np.int32)
+    vars_ = np.zeros((max(m.ny, 1), 2), np.uint32)
+    vars_[:m.ny, 0], vars_[:m.ny, 1] = m.num_mask, m.den_mask
+    select = np.ascontiguousarray(m.select, np.uint32)
+    shift = np.ascontiguousarray(m.shift, np.int32)
+    keep = (stoich, trans, vars_, select, shift)
+    gm = GenModel(m.nc, m.nt, m.ny, int(select.size), int(shift.shape[0]), int(m.y_source),
+                  _p(stoich, ctypes.c_int32), _p(trans, ctypes.c_int32), _p(vars_, ctypes.c_uint32),
+                  _p(select if select.size else np.zeros(1, np.uint32), ctypes.c_uint32),
+                  _p(shift if shift.size else np.zeros(1, np.int32), ctypes.c_int32))
+    return gm, keep
+
+
+def gen_dependency(m: W.GeneralModel):
+    """Validates the model (host only) and returns its dependency graph: dep[n]
+    bit j set when firing transition n can change rate j."""
+    L = load_library()
+    gm, keep = _gen_model(m)
+    dep = np.zeros(max(m.nt, 1), np.uint32)
+    st = L.gen_model_check(ctypes.byref(gm), _p(dep, ctypes.c_uint32))
+    if st != SIM_OK:
+        msg = L.gen_last_error(None)
+        raise SimError(st, msg.decode() if msg else "")
+    return dep[:m.nt].copy()
+
+
+class GenSim:
+    """One handle of the general compartment model: R replicates on N nodes."""
+
+    def __init__(self, model: W.GeneralModel, u0, y0, rates, var_params, max_days, seed=1,
+                 underflow_error=False, replicate_base=0):
+        self.L = load_library()
+        u0 = np.ascontiguousarray(u0, np.int32)
+        self.nc, self.N = u0.shape
+        self.ny = model.ny
+        rates = np.ascontiguousarray(rates, np.float64)
+        self.R = rates.shape[0]
+        self.max_days = max_days
+        gm, keep = _gen_model(model)
+        cfg = GenConfig(self.N, self.R, max_days, 1 if underflow_error else 0, seed, int(replicate_base), 0)
+        y0 = np.ascontiguousarray(y0, np.float64).reshape(self.ny, self.N)
+        vp = np.ascontiguousarray(var_params, np.float64)
+        h = ctypes.c_void_p()
+        st = self.L.gen_create(ctypes.byref(gm), ctypes.byref(cfg), _p(u0, ctypes.c_int32),
+                               _p(y0 if y0.size else np.zeros(1), ctypes.c_double),
+                               _p(rates if rates.size else np.zeros(1), ctypes.c_double),
+                               _p(vp if vp.size else np.zeros(1), ctypes.c_double), ctypes.byref(h))
+        del keep
+        self._check(None, st)
+        self.h = h
+
+    def _check(self, h, st):
+        if st != SIM_OK:
+            msg = self.L.gen_last_error(h)
+            raise SimError(st, msg.decode() if msg else "")
+
+    @classmethod
+    def from_workload(cls, w: W.GeneralWorkload, events=True, max_days=None, **kw):
+        s = cls(w.model, w.u0, w.y0, w.rates, w.var_params, w.T if max_days is None else max_days, seed=w.seed,
+                underflow_error=w.underflow_error, **kw)
+        if events and len(w.events):
+            s.load_events(w.events)
+        return s
+
+    def load_events(self, ev: W.GeneralEvents):
+        arr = [np.ascontiguousarray(a, np.int32) for a in (ev.day, ev.kind, ev.node, ev.dest, ev.count, ev.select,
+                                                           ev.shift)]
+        self._check(self.h, self.L.gen_load_events(self.h, len(ev), *[_p(a, ctypes.c_int32) for a in arr]))
+
+    def set_launch(self, mode):
+        self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_LAUNCH, {"stream": 0, "graph": 1}[mode]))
+
+    def run(self, days, stream=None):
+        st = current_stream() if stream is None else ctypes.c_void_p(stream)
+        self._check(self.h, self.L.gen_run_days(self.h, int(days), st))
+
+    def state(self, stream=None):
+        counts = np.empty((self.R, self.nc, self.N), np.int32)
+        y = np.empty((self.R, self.ny, self.N), np.float64)
+        day = ctypes.c_int32()
+        st = current_stream() if stream is None else ctypes.c_void_p(stream)
+        self._check(self.h, self.L.gen_state(self.h, counts.ctypes.data_as(ctypes.c_void_p),
+                                             y.ctypes.data_as(ctypes.c_void_p) if y.size else None,
+                                             ctypes.byref(day), SIM_HOST, st))
+        return counts, y, day.value
+
+    def set_state(self, counts, y, day, stream=None):
+        counts = np.ascontiguousarray(counts, np.int32)
+        y = np.ascontiguousarray(y, np.float64)
+        st = current_stream() if stream is None else ctypes.c_void_p(stream)
+        self._check(self.h, self.L.gen_set_state(self.h, counts.ctypes.data_as(ctypes.c_void_p),
+                                                 y.ctypes.data_as(ctypes.c_void_p) if y.size else None,
+                                                 int(day), SIM_HOST, st))
+
+    def counters(self):
+        out = np.zeros((self.R, 4), np.int64)
+        self._check(self.h, self.L.gen_counters(self.h, _p(out, ctypes.c_int64)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gen_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

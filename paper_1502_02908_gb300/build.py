@@ -11,7 +11,8 @@ HERE = pathlib.Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 BUILD = HERE / "_build"
 LIB = BUILD / "libepisim.so"
-SOURCES = ["ssa.cu", "events.cu", "batch.cu", "noalloc.cu", "regions.cu", "host.cpp"]
+SOURCES = ["ssa.cu", "events.cu", "batch.cu", "noalloc.cu", "regions.cu", "general.cu", "host.cpp",
+           "general_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I", str(HERE.parent / "include")]
@@ -31,7 +32,7 @@ def _stale(out: pathlib.Path, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> pathlib.Path:
     BUILD.mkdir(exist_ok=True)
-    headers = list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + [HERE.parent / "include" / "episim.h"]
+    headers = list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + list((HERE.parent / "include").glob("*.h"))
     objs = []
     jobs = []
     for src in SOURCES:

@@ -1,0 +1,161 @@
+"""GPU: the general compartment model through the C ABI (gen_*) against the
+general-model oracle, bit for bit on counts, continuous variables and counters:
+the SIR example (frequency-dependent and mass-action), an SEIRS model with two
+continuous variables under the three update sources, an Erlang-staged model with
+11 transitions (the wide kernel), SISe3 in the general form on a national-shaped
+network, the ERROR policy, CUDA-graph launches, split runs and state round
+trips, one node, no events, no transitions."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_02908_gb300 import binding as B
+from paper_1502_02908_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load_library()
+
+
+def _run(w, launch="stream", splits=None):
+    s = B.GenSim.from_workload(w)
+    s.set_launch(launch)
+    for nd in (splits or [w.T]):
+        s.run(nd)
+    counts, y, day = s.state()
+    ctr = s.counters()
+    s.close()
+    assert day == sum(splits or [w.T])
+    return counts, y, ctr
+
+
+def _same(w, got, ref=None):
+    ref = oracle.run_general(w) if ref is None else ref
+    counts, y, ctr = got
+    assert np.array_equal(counts, ref.counts)
+    assert np.array_equal(y, ref.y)
+    assert np.array_equal(ctr, ref.counters)
+    return ref
+
+
+@pytest.mark.parametrize("freq", [True, False])
+def test_sir_bitexact(freq):
+    w = W.sir_general(N=2000 + 37, T=60, n_events=12_000, R=2, freq=freq, beta=0.4 if freq else 0.004)
+    w.rates[1] *= np.array([1.2, 0.9])
+    ref = _same(w, _run(w))
+    assert ref.counters[:, 0].min() > 10_000 and ref.counters[:, 2].sum() > 0
+
+
+@pytest.mark.parametrize("source", [W.Y_POST_EVENT, W.Y_PRE_EVENT, W.Y_MIDPOINT])
+def test_seirs_two_variables_bitexact(source):
+    w = W.seirs_env(N=3000 + 5, T=60, n_events=30_000, R=2, y_source=source)
+    ref = _same(w, _run(w))
+    assert ref.counters[:, 0].min() > 100_000
+
+
+def test_erlang_eleven_transitions_bitexact():
+    w = W.erlang_sis(N=1500 + 3, T=40, n_events=8000, R=2)
+    w.rates[1] *= 1.5
+    ref = _same(w, _run(w))
+    assert ref.counters[:, 0].min() > 1_000_000
+
+
+def test_sise3_general_national_shape_bitexact():
+    w = W.as_general(W.sise3_national(N=3000, T=60, n_events=40_000, R=2))
+    w.rates[1] *= 1.4
+    ref = _same(w, _run(w))
+    assert ref.counters[:, 1].min() > 1000
+
+
+def test_sise_general_matches_the_sise_kernels():
+    # SISe in the general form is the same model as the SISe path
+    w = W.sise_plain(N=1200, T=50, n_events=9000)
+    s = B.Sim.from_workload(w)
+    s.run(w.T)
+    counts, phi, _ = s.state()
+    _, _, ctr = s.stats()
+    s.close()
+    g_counts, g_y, g_ctr = _run(W.as_general(w))
+    assert np.array_equal(counts, g_counts) and np.array_equal(phi, g_y[:, 0, :])
+    assert np.array_equal(ctr, g_ctr)
+
+
+def test_graph_launch_and_split_runs_bitexact():
+    w = W.seirs_env(N=1000, T=40, n_events=8000, R=1, y_source=W.Y_MIDPOINT)
+    ref = oracle.run_general(w)
+    _same(w, _run(w, launch="graph"), ref)
+    _same(w, _run(w, splits=[7, 1, 20, 12]), ref)
+    _same(w, _run(w, launch="graph", splits=[13, 27]), ref)
+
+
+def test_set_state_round_trip_continues_bitexact():
+    w = W.sir_general(N=700, T=30, n_events=3000, R=1)
+    ref = oracle.run_general(w)
+    s = B.GenSim.from_workload(w)
+    s.run(12)
+    c12, y12, _ = s.state()
+    s.run(18)
+    s.set_state(c12, y12, 12)
+    s.run(18)
+    counts, y, day = s.state()
+    s.close()
+    assert day == 30 and np.array_equal(counts, ref.counts)
+
+
+def test_error_policy_latches_underflow():
+    w = W.sir_general(N=300, T=20, n_events=4000, R=1)
+    w.events.count[:] = w.events.count * 40
+    w.underflow_error = True
+    ref = oracle.run_general(w)
+    assert ref.counters[0, 3] > 0
+    s = B.GenSim.from_workload(w)
+    s.run(w.T)
+    with pytest.raises(B.SimError) as e:
+        s.state()
+    assert e.value.status == B.SIM_E_UNDERFLOW
+    counts, y, _ = s.state()                       # latched once, then cleared
+    assert np.array_equal(counts, ref.counts)
+    assert np.array_equal(s.counters(), ref.counters)
+    s.close()
+
+
+def test_one_node_no_events_no_transitions():
+    w = W.seirs_env(N=1, T=25, n_events=0, R=3)
+    _same(w, _run(w))
+    m = W.general_model(("A", "B"), [], variables=[(("A",), ("A", "B"))], selects=[("A",)])
+    g = W.GeneralWorkload("static", m, 50, 10, 1, np.full((2, 50), 3, np.int32), np.zeros((1, 50)),
+                          np.zeros((1, 0)), W._var_params(1, 1, (0.5,), (0.1,), (0.0,)), W.GeneralEvents.empty(), 3)
+    _same(g, _run(g))
+
+
+def test_replicate_base_shifts_streams():
+    w = W.sir_general(N=400, T=20, n_events=2000, R=3)
+    ref = oracle.run_general(w)
+    s = B.GenSim(w.model, w.u0, w.y0, w.rates[1:], w.var_params[1:], w.T, seed=w.seed, replicate_base=1)
+    s.load_events(w.events)
+    s.run(w.T)
+    counts, _, _ = s.state()
+    s.close()
+    assert np.array_equal(counts, ref.counts[1:])
+
+
+def test_rejects_bad_events():
+    w = W.sir_general(N=50, T=5, n_events=100)
+    s = B.GenSim.from_workload(w, events=False)
+    bad = w.events.take(np.arange(len(w.events)))
+    bad.kind[0] = W.INTERNAL
+    bad.select[0] = 0                   # mask {S, I, R} with offset +2: S -> R lands in the mask
+    bad.shift[0] = 0
+    with pytest.raises(B.SimError):
+        s.load_events(bad)
+    bad = w.events.take(np.arange(len(w.events)))
+    bad.day[3] = 5
+    with pytest.raises(B.SimError):
+        s.load_events(bad)
+    s.close()
