@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-synthetic", action="store_true")
     ap.add_argument("--no-fitting", action="store_true")
+    ap.add_argument("--no-general", action="store_true")
     return ap.parse_args()
 
 
@@ -227,6 +228,66 @@ def synthetic_leg(args, B, W, torch, oracle_check):
                                       "phi_equal": bool(np.array_equal(p[0], ref.phi[0]))}
         line["oracle_transitions_per_s"] = int(ref.counters[0, 0]) / dt
     return line
+
+
+def general_leg(args, B, W, torch, oracle_check):
+    """The general compartment model (product-form propensities, sparse dependency
+    graph, event masks and offsets) on national-size networks: SISe3 written in the
+    general form on the national network (the same instance as the main line), and
+    an SEIRS model with two continuous variables under the midpoint update on 37,000
+    nodes.  CUDA-graph day loop; bit-exactness against the general oracle over a
+    prefix of each horizon."""
+    out = {}
+    cases = (("sise3_national_general", W.as_general(W.sise3_national()), 365),
+             ("seirs_midpoint", W.seirs_env(N=37_000, T=365, n_events=1_000_000, R=1, y_source=W.Y_MIDPOINT), 60))
+    from paper_1502_02908_gb300 import autotune
+    for name, w, check_days in cases:
+        w.T = min(args.days, w.T)
+        thr = -1
+        if not args.no_tune:
+            thr, _ = autotune.autotune_general(w, days=max(10, w.T // 8))
+        sim = B.GenSim.from_workload(w)
+        sim.set_launch("graph")
+        n_warp = sim.set_warp_threshold(thr)
+        u0 = w.u0[None]; y0 = w.y0[None]
+        steps, warm = 2, 1
+        times = []
+        c0 = sim.counters()
+        for i in range(warm + steps):
+            sim.set_state(u0, y0, 0)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(); sim.run(w.T); e1.record()
+            torch.cuda.synchronize()
+            if i >= warm:
+                times.append(e0.elapsed_time(e1))
+        c1 = sim.counters()
+        sim.close()
+        ms = sum(times) / steps
+        trans = int(c1[0, 0] - c0[0, 0]) // (warm + steps)
+        m = w.model
+        line = {"workload": f"{name}: {w.N} nodes x {w.T} days, {len(w.events)} events, "
+                            f"{m.nc} compartments, {m.nt} transitions, {m.ny} continuous variables",
+                "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "transitions_per_s": trans / (ms / 1000),
+                "transitions_per_step": trans, "ms_per_step": ms, "steps": steps, "warmup": warm,
+                "gpu_launches_per_step": w.T * (2 + (1 if m.ny and m.y_source != W.Y_PRE_EVENT else 0)),
+                "warp_threshold": thr, "warp_nodes": n_warp}
+        if oracle_check:
+            import oracle
+            oracle.build()
+            days = min(check_days, w.T)
+            t0 = time.perf_counter()
+            ref = oracle.run_general(w, ndays=days)
+            dt = time.perf_counter() - t0
+            chk = B.GenSim.from_workload(w)
+            chk.run(days)
+            c, y, _ = chk.state()
+            chk.close()
+            line["bitexact_vs_oracle"] = {"days": days, "counts_equal": bool(np.array_equal(c, ref.counts)),
+                                          "y_equal": bool(np.array_equal(y, ref.y))}
+            line["oracle_node_days_per_s"] = w.N * days / dt
+        out[name] = line
+    return out
 
 
 def fitting_leg(args, B, W, torch):
@@ -422,6 +483,8 @@ def main():
         line["synthetic"] = synthetic_leg(args, B, W, torch, not args.no_cpu_baseline)
     if not args.no_fitting and rank == 0:
         line["fitting"] = fitting_leg(args, B, W, torch)
+    if not args.no_general and rank == 0:
+        line["general"] = general_leg(args, B, W, torch, not args.no_cpu_baseline)
     if rank == 0 and not args.no_cpu_baseline:
         days = min(365, T)
         base, ref = oracle_baseline(w, days, "national SISe3")

@@ -125,7 +125,8 @@ sim_status gen_create(const gen_model* m, const gen_config* cfg, const int32_t* 
                       const double* rates, const double* var_params, gen_handle** out);
 
 /* Loads the scheduled events (Sec. 3.2 Eq. (event)), n host int32 arrays in
- * input order: day in [0, max_days); kind SIM_EXIT / SIM_ENTER / SIM_INTERNAL /
+ * input order: day >= 0 (events on days >= max_days are kept but never reached);
+ * kind SIM_EXIT / SIM_ENTER / SIM_INTERNAL /
  * SIM_EXTERNAL; node (and dest for SIM_EXTERNAL, != node) in [0, N); count >= 0;
  * select in [0, n_select); shift in [-1, n_shift) (-1: no offset).
  *   EXIT      removes count animals drawn uniformly without replacement from the
@@ -158,10 +159,18 @@ sim_status gen_set_state(gen_handle* h, const int32_t* counts, const double* y, 
 /* Host int64 [R][4]: transitions fired, events applied, clamped, skipped. */
 sim_status gen_counters(gen_handle* h, int64_t* counters);
 
-/* Launch mode of gen_run_days (option 1): 0 stream launches, 1 the day loop as a
- * CUDA graph (captured once per (first day, ndays)). */
-enum { GEN_OPT_LAUNCH = 1 };
+/* Options (results never depend on them):
+ *   GEN_OPT_LAUNCH: launch mode of gen_run_days, 0 stream launches, 1 the day loop
+ *       as a CUDA graph (captured once per (first day, ndays));
+ *   GEN_OPT_WARP_THRESHOLD: nodes whose initial population (sum of u0) is at least
+ *       this run the stochastic step one per warp, 32 draws at a time with a
+ *       fixed-point iteration over the lanes; the others one per thread
+ *       (-1: automatic, 300). */
+enum { GEN_OPT_LAUNCH = 1, GEN_OPT_WARP_THRESHOLD = 2 };
 sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value);
+
+/* Nodes the stochastic step runs one per warp (-1 for a NULL handle). */
+int32_t gen_warp_nodes(const gen_handle* h);
 
 void gen_destroy(gen_handle* h);
 

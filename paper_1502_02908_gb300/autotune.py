@@ -70,3 +70,45 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
         sim.close()
     thr, gthr, mode, _ = min(table, key=lambda x: x[3])
     return {"warp_threshold": thr, "group_threshold": gthr, "launch": mode}, table
+
+
+GENERAL_WARP_THRESHOLDS = (1 << 30, 1000, 600, 300, 150)
+
+
+def autotune_general(workload, days=None, thresholds=GENERAL_WARP_THRESHOLDS, repeats=1):
+    """The general model's warp threshold (initial node population from which the
+    stochastic step takes a warp per node): times each candidate over a prefix of
+    the horizon with the CUDA-graph day loop, checks that all end in the
+    bit-identical state and counters, and returns (best threshold, table
+    [(threshold, warp nodes, ms)])."""
+    import torch
+    w = workload
+    nd = min(w.T, days if days is not None else max(10, w.T // 10))
+    sim = B.GenSim.from_workload(w)
+    sim.set_launch("graph")
+    u0 = np.repeat(w.u0[None], w.R, 0)
+    y0 = np.repeat(w.y0[None], w.R, 0)
+    ref = None
+    table = []
+    try:
+        for thr in thresholds:
+            nb = sim.set_warp_threshold(thr)
+            best = float("inf")
+            for rep in range(repeats + 1):
+                sim.set_state(u0, y0, 0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.run(nd)
+                c, y, _ = sim.state()
+                dt = (time.perf_counter() - t0) * 1e3
+                if rep:
+                    best = min(best, dt)
+            fp = (c.tobytes(), y.tobytes())
+            if ref is None:
+                ref = fp
+            elif fp != ref:
+                raise AssertionError(f"warp threshold {thr} changed the results")
+            table.append((thr, nb, best))
+    finally:
+        sim.close()
+    return min(table, key=lambda x: x[2])[0], table

@@ -59,7 +59,7 @@ class GenConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-GEN_OPT_LAUNCH = 1
+GEN_OPT_LAUNCH, GEN_OPT_WARP_THRESHOLD = 1, 2
 
 
 def library_path() -> pathlib.Path:
@@ -133,6 +133,8 @@ def load_library(build_if_missing: bool = True):
         L.gen_destroy.restype = None
         L.gen_last_error.argtypes = [vp]
         L.gen_last_error.restype = ctypes.c_char_p
+        L.gen_warp_nodes.argtypes = [vp]
+        L.gen_warp_nodes.restype = ctypes.c_int32
         L.sim_warp_nodes.argtypes = [vp]
         L.sim_warp_nodes.restype = ctypes.c_int32
         L.sim_debug_schedule_size.argtypes = [vp]
@@ -479,6 +481,11 @@ class GenSim:
 
     def set_launch(self, mode):
         self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_LAUNCH, {"stream": 0, "graph": 1}[mode]))
+
+    def set_warp_threshold(self, population):
+        """Nodes with at least this initial population run one per warp (-1: automatic)."""
+        self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_WARP_THRESHOLD, int(population)))
+        return self.L.gen_warp_nodes(self.h)
 
     def run(self, days, stream=None):
         st = current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -10,6 +10,7 @@
 #include "../../include/episim_general.h"
 #include "devmath.cuh"
 #include "general.h"
+#include "softdiv.cuh"
 
 namespace episim {
 
@@ -23,6 +24,15 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, int n16) {
 
 __device__ __forceinline__ double ll_to_double(long long n) { return __ll2double_rn(n); }
 
+// Exact binary64 of 0 <= n < 2^53 on the integer pipe.
+__device__ __forceinline__ double u2d_exact(long long n) {
+  if (n <= 0) return 0.0;
+  const uint64_t u = (uint64_t)n;
+  const int top = 63 - __clzll(u);
+  const uint64_t mant = (u << (52 - top)) & ((1ull << 52) - 1);
+  return bits_to_double(((uint64_t)(1023 + top) << 52) | mant);
+}
+
 __device__ __forceinline__ long long mask_sum(const int32_t* x, int stride, uint32_t mask, int nc) {
   long long s = 0;
   for (int c = 0; c < nc; ++c)
@@ -30,22 +40,19 @@ __device__ __forceinline__ long long mask_sum(const int32_t* x, int stride, uint
   return s;
 }
 
-__device__ __forceinline__ double pick(const double (&y)[kGenMaxCont], int q) {
-  return q == 0 ? y[0] : q == 1 ? y[1] : q == 2 ? y[2] : y[3];
-}
-
-// a_j = k_j [* y_q] [* x_a] [* x_b] [/ P], left to right.
-__device__ __forceinline__ double gen_rate(const GenModelDev& m, const GenRepParams& p, const int32_t* x,
-                                           int stride, const double (&y)[kGenMaxCont], int j) {
+// a_j = k_j [* y_q] [* x_a] [* x_b] [/ P], left to right (IEEE products; the
+// quotient by the integer-pipe division, bit-identical to IEEE).
+__device__ __forceinline__ double gen_rate(const GenModelDev& m, const GenRepParams& p, const int32_t* x, int stride,
+                                        const double* y, int j) {
   double a = p.rate[j];
   const int q = m.fy[j], fa = m.fa[j], fb = m.fb[j];
   const uint32_t pm = m.pop[j];
-  if (q >= 0) a = __dmul_rn(a, pick(y, q));
+  if (q >= 0) a = __dmul_rn(a, y[q]);
   if (fa >= 0) a = __dmul_rn(a, i2d_exact(x[fa * stride]));
   if (fb >= 0) a = __dmul_rn(a, i2d_exact(x[fb * stride]));
   if (pm) {
     const long long P = mask_sum(x, stride, pm, m.nc);
-    a = P > 0 ? __ddiv_rn(a, ll_to_double(P)) : 0.0;
+    a = (P > 0 && pos(a)) ? div_pos(a, u2d_exact(P)) : 0.0;
   }
   return a;
 }
@@ -59,119 +66,242 @@ __device__ __forceinline__ double gen_y_next(const GenModelDev& m, const GenRepP
   return __dadd_rn(__dadd_rn(__dmul_rn(y, omb), mid), p.eps[q]);
 }
 
-// Direct method of one node-day (Eqs. (sampling), (sampling2)); x is the node's
-// counts in shared memory (stride = threads per block).
-template <int NT>
+// Per-thread rate storage in shared memory: rate j of the thread at a[j * stride],
+// its left-to-right partial sum at P[j * stride] (rolled loops keep the kernel
+// small enough for the instruction cache).
+struct RateRow {
+  double* a;
+  double* P;
+  int stride;
+};
+
+// P_j = P_{j-1} + a_j for j >= j0 (P_0 = a_0, which equals 0 + a_0 for a_0 >= 0);
+// returns a0 = P_{nt-1}.
+__device__ __forceinline__ double prefix_from(const RateRow& R, int nt, int j0) {
+  double run = j0 > 0 ? R.P[(j0 - 1) * R.stride] : 0.0;
+  for (int j = j0; j < nt; ++j) {
+    run = j == 0 ? R.a[0] : __dadd_rn(run, R.a[j * R.stride]);
+    R.P[j * R.stride] = run;
+  }
+  return nt > 0 ? R.P[(nt - 1) * R.stride] : 0.0;
+}
+
+// Eq. (sampling2): the first j with a_j > 0 and r <= P_j, else the last j with a_j > 0.
+__device__ __forceinline__ int select_transition(const RateRow& R, int nt, double r) {
+  int last = -1;
+  for (int j = 0; j < nt; ++j)
+    if (pos(R.a[j * R.stride])) {
+      last = j;
+      if (le_nonneg(r, R.P[j * R.stride])) return j;
+    }
+  return last;
+}
+
+__device__ __forceinline__ void apply_changes(const GenModelDev& m, int32_t* x, int stride, int n, int times) {
+  for (int q = m.chg_off[n]; q < m.chg_off[n + 1]; ++q) {
+    const uint32_t c = m.chg[q];
+    x[(c & 0xffu) * stride] += times * ((int32_t)c >> 8);
+  }
+}
+
+// Direct method of one node-day by one thread (Eqs. (sampling), (sampling2));
+// x is the node's counts in shared memory (stride = threads per block).  After a
+// firing only the rates of its dependency graph are recomputed, and the partial
+// sums from the first of them on.
 __device__ __forceinline__ uint32_t gen_node_day(const GenModelDev& m, const GenRepParams& p, int32_t* x,
-                                                 int stride, const double (&y)[kGenMaxCont], uint32_t v,
+                                                 int stride, const RateRow& R, const double* y, uint32_t v,
                                                  uint32_t day, uint32_t rep, uint32_t k0, uint32_t k1) {
   const int nt = m.nt;
-  double a[NT];
-#pragma unroll
-  for (int j = 0; j < NT; ++j) a[j] = (j < nt) ? gen_rate(m, p, x, stride, y, j) : 0.0;
+  for (int j = 0; j < nt; ++j) R.a[j * R.stride] = gen_rate(m, p, x, stride, y, j);
+  double a0 = prefix_from(R, nt, 0);
   double t = 0.0;
   uint32_t fired = 0;
-  for (uint32_t k = 0;; ++k) {
-    double a0 = 0.0;
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-      if (j < nt) a0 = __dadd_rn(a0, a[j]);
-    if (!pos(a0)) break;
+  for (uint32_t k = 0; pos(a0); ++k) {
     const uint4 w = philox10(make_uint4(v, day, k, rep), k0, k1);
     const double E = neglog_u((((uint64_t)w.y << 32) | w.x) >> 12);
     const double u2 = uniform_open(w.z, w.w);
-    const double tn = __dadd_rn(t, __ddiv_rn(E, a0));
+    const double tn = __dadd_rn(t, div_pos(E, a0));
     if (le_nonneg(1.0, tn)) break;
     t = tn;
-    const double r = __dmul_rn(a0, u2);
-    double P = 0.0;
-    int chosen = -1, last = -1;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      if (j < nt && chosen < 0) {
-        P = __dadd_rn(P, a[j]);
-        if (pos(a[j])) {
-          last = j;
-          if (le_nonneg(r, P)) chosen = j;
-        }
-      }
+    const int chosen = select_transition(R, nt, __dmul_rn(a0, u2));
+    apply_changes(m, x, stride, chosen, 1);
+    uint32_t dm = m.dep[chosen];
+    const int j0 = dm ? __ffs(dm) - 1 : nt;
+    while (dm) {
+      const int j = __ffs(dm) - 1;
+      dm &= dm - 1u;
+      R.a[j * R.stride] = gen_rate(m, p, x, stride, y, j);
     }
-    if (chosen < 0) chosen = last;
-    for (int q = m.chg_off[chosen]; q < m.chg_off[chosen + 1]; ++q) {
-      const uint32_t c = m.chg[q];
-      x[(c & 0xffu) * stride] += (int32_t)c >> 8;
-    }
-    const uint32_t dm = m.dep[chosen];
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-      if (dm >> j & 1u) a[j] = gen_rate(m, p, x, stride, y, j);
+    a0 = prefix_from(R, nt, j0);
     ++fired;
   }
   return fired;
 }
 
-template <int NT>
+// Direct method of one node-day by a warp, 32 draws per round.  Lane l takes
+// draw k + l.  Its state is the round's base state plus the transitions the
+// lanes before it choose; the choices are found by a fixed-point iteration (each
+// lane chooses at the state the current choices of the lanes before it imply;
+// lane 0's choice is final after one pass, and each pass fixes at least one more
+// lane, so the choices settle within 32 passes).  The clock then runs over the
+// lanes in draw order with the binary64 sums of the sequential method, so the
+// result is that method's.  xl: this lane's counts (shared memory, stride as in
+// the thread method); base: the warp's counts at the start of the round; ctau,
+// cch: the warp's 32 clock increments and choices.
+__device__ __forceinline__ uint32_t gen_warp_node_day(const GenModelDev& m, const GenRepParams& p, int32_t* xl,
+                                                      int32_t* base, int stride, const RateRow& R, double* ctau,
+                                                      int32_t* cch, const double* y, uint32_t v, uint32_t day,
+                                                      uint32_t rep, uint32_t k0, uint32_t k1, int lane) {
+  const int nt = m.nt, nc = m.nc;
+  const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
+  double t = 0.0;
+  uint32_t fired = 0;
+  for (uint32_t kb = 0; nt > 0; kb += 32) {
+    const uint4 w = philox10(make_uint4(v, day, kb + (uint32_t)lane, rep), k0, k1);
+    const double E = neglog_u((((uint64_t)w.y << 32) | w.x) >> 12);
+    const double u2 = uniform_open(w.z, w.w);
+    int choice = -1;
+    double tau = 0.0;
+    for (int pass = 0; pass <= 32; ++pass) {
+      for (int c = 0; c < nc; ++c) xl[c * stride] = base[c];
+      for (int j = 0; j < nt; ++j) {
+        const int cnt = __popc(__ballot_sync(full, choice == j) & below);
+        if (cnt) apply_changes(m, xl, stride, j, cnt);
+      }
+      for (int j = 0; j < nt; ++j) R.a[j * R.stride] = gen_rate(m, p, xl, stride, y, j);
+      const double a0 = prefix_from(R, nt, 0);
+      int next = -1;
+      if (pos(a0)) {
+        next = select_transition(R, nt, __dmul_rn(a0, u2));
+        tau = div_pos(E, a0);
+      }
+      const bool changed = __any_sync(full, next != choice);
+      choice = next;
+      if (!changed) break;
+    }
+    ctau[lane] = tau;
+    cch[lane] = choice;
+    __syncwarp();
+    // clock over the lanes in draw order (every lane runs the same sums)
+    int stop = 32;
+    for (int l = 0; l < 32; ++l) {
+      if (cch[l] < 0) { stop = l; break; }
+      const double tn = __dadd_rn(t, ctau[l]);
+      if (le_nonneg(1.0, tn)) { stop = l; break; }
+      t = tn;
+    }
+    const unsigned fired_lanes = stop == 32 ? full : ((1u << stop) - 1u);
+    for (int j = 0; j < nt; ++j) {
+      const int cnt = __popc(__ballot_sync(full, choice == j) & fired_lanes);
+      if (cnt && lane == 0) apply_changes(m, base, 1, j, cnt);
+    }
+    __syncwarp();
+    fired += (uint32_t)stop;
+    if (stop < 32) break;
+  }
+  return fired;
+}
+
 __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   extern __shared__ int4 smem4[];
   GenModelDev& m = *reinterpret_cast<GenModelDev*>(smem4);
-  GenRepParams& p = *reinterpret_cast<GenRepParams*>(reinterpret_cast<char*>(smem4) + sizeof(GenModelDev));
-  int32_t* xs = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(smem4) + sizeof(GenModelDev) +
-                                           sizeof(GenRepParams));
+  char* sp = reinterpret_cast<char*>(smem4) + sizeof(GenModelDev);
+  GenRepParams& p = *reinterpret_cast<GenRepParams*>(sp);
+  sp += sizeof(GenRepParams);
+  double* ctau = reinterpret_cast<double*>(sp);                 // [warps][32]
+  sp += (kGenThreads / 32) * 32 * sizeof(double);
   const int r = blockIdx.y;
   copy16(&m, a.model, (int)(sizeof(GenModelDev) / 16));
   copy16(&p, a.params + r, (int)(sizeof(GenRepParams) / 16));
   __syncthreads();
-  const int nc = m.nc, ny = m.ny, N = a.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = m.nc, nt = m.nt, ny = m.ny, N = a.N;
+  double* rates = reinterpret_cast<double*>(sp);                // [nt][threads], then partial sums
+  sp += (size_t)2 * nt * kGenThreads * sizeof(double);
+  int32_t* wbase = reinterpret_cast<int32_t*>(sp);              // [warps][kGenMaxComp]
+  sp += (kGenThreads / 32) * kGenMaxComp * sizeof(int32_t);
+  int32_t* cch = reinterpret_cast<int32_t*>(sp);                // [warps][32]
+  sp += (kGenThreads / 32) * 32 * sizeof(int32_t);
+  int32_t* xs = reinterpret_cast<int32_t*>(sp);                 // [nc][threads]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int stride = blockDim.x;
-  int32_t* x = xs + threadIdx.x;
+  const bool warp_unit = (int)blockIdx.x < a.warp_blocks;
+  int v = -1;
+  if (warp_unit) {
+    const int u = (int)blockIdx.x * (kGenThreads / 32) + warp;
+    if (u < a.n_big) v = a.order[u];
+  } else {
+    const int i = a.n_big + ((int)blockIdx.x - a.warp_blocks) * kGenThreads + (int)threadIdx.x;
+    if (i < N) v = a.order[i];
+  }
   uint32_t fired = 0;
-  if (i < N) {
-    const int v = a.order[i];
+  if (v >= 0) {
+    int32_t* x = xs + threadIdx.x;
+    int32_t* base = wbase + warp * kGenMaxComp;
+    const RateRow R{rates + threadIdx.x, rates + (size_t)nt * kGenThreads + threadIdx.x, kGenThreads};
     int32_t* X = a.counts + (size_t)r * nc * N;
-    for (int c = 0; c < nc; ++c) x[c * stride] = X[(size_t)c * N + v];
-    double y[kGenMaxCont] = {0.0, 0.0, 0.0, 0.0};
-    double* Y = a.y + (size_t)r * ny * N;
-#pragma unroll
-    for (int q = 0; q < kGenMaxCont; ++q)
-      if (q < ny) y[q] = Y[(size_t)q * N + v];
-    if (m.y_source == kGenYMidpoint) {
+    if (warp_unit) {
+      for (int c = lane; c < nc; c += 32) base[c] = X[(size_t)c * N + v];
+      __syncwarp();
+    } else {
+      for (int c = 0; c < nc; ++c) x[c * stride] = X[(size_t)c * N + v];
+    }
+    // the node's counts at the start of the day, as this lane sees them
+    const int32_t* x0 = warp_unit ? base : x;
+    const int s0 = warp_unit ? 1 : stride;
+    double y[kGenMaxCont];
+    const double* Y = a.y + (size_t)r * ny * N;
+    for (int q = 0; q < ny; ++q) y[q] = Y[(size_t)q * N + v];
+    const bool writer = !warp_unit || lane == 0;
+    if (m.y_source == kGenYMidpoint && writer) {
       for (int q = 0; q < ny; ++q) {
         double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
-        M[v] = ll_to_double(mask_sum(x, stride, m.num[q], nc));
-        M[(size_t)N + v] = ll_to_double(mask_sum(x, stride, m.den[q], nc));
+        M[v] = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
+        M[(size_t)N + v] = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
       }
     }
-    const uint32_t rep = (uint32_t)(a.rep_base + r);
-    fired = gen_node_day<NT>(m, p, x, stride, y, (uint32_t)v, (uint32_t)a.day, rep, (uint32_t)a.seed,
-                             (uint32_t)(a.seed >> 32));
-    for (int c = 0; c < nc; ++c) X[(size_t)c * N + v] = x[c * stride];
-    if (m.y_source == kGenYPreEvent) {
-#pragma unroll
-      for (int q = 0; q < kGenMaxCont; ++q)
-        if (q < ny) {
-          const double U = ll_to_double(mask_sum(x, stride, m.num[q], nc));
-          const double D = ll_to_double(mask_sum(x, stride, m.den[q], nc));
-          Y[(size_t)q * N + v] = gen_y_next(m, p, q, a.day, y[q], U, D);
+    const uint32_t rep = (uint32_t)(a.rep_base + r), k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    if (warp_unit)
+      fired = gen_warp_node_day(m, p, x, base, stride, R, ctau + warp * 32, cch + warp * 32, y, (uint32_t)v,
+                                (uint32_t)a.day, rep, k0, k1, lane);
+    else
+      fired = gen_node_day(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1);
+    if (writer) {
+      for (int c = 0; c < nc; ++c) X[(size_t)c * N + v] = x0[c * s0];
+      if (m.y_source == kGenYPreEvent) {
+        double* Yw = a.y + (size_t)r * ny * N;
+        for (int q = 0; q < ny; ++q) {
+          const double U = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
+          const double D = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
+          Yw[(size_t)q * N + v] = gen_y_next(m, p, q, a.day, y[q], U, D);
         }
+      }
     }
+    if (warp_unit && lane != 0) fired = 0;
   }
   const uint32_t tot = __reduce_add_sync(0xffffffffu, fired);
-  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(a.ctr + (size_t)r * 4, (unsigned long long)tot);
+  if (lane == 0 && tot) atomicAdd(a.ctr + (size_t)r * 4, (unsigned long long)tot);
 }
 
 // One thread per component of the day's transfer graph: its events in input
-// order (no other thread touches its nodes this day).
+// order (no other thread touches its nodes this day).  The counts of the node an
+// event samples from stay in a shared-memory row across consecutive events at
+// that node; transfers add to the destination in global memory (a destination is
+// never the node in the row, and the row is written back before another node is
+// loaded).
 __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
   __shared__ GenModelDev m;
+  __shared__ int32_t cache[kGenMaxComp * kGenThreads];
   copy16(&m, a.model, (int)(sizeof(GenModelDev) / 16));
   __syncthreads();
   const int r = blockIdx.y, nc = m.nc, N = a.N;
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t* cc = cache + threadIdx.x;
+  const int S = kGenThreads;
   uint32_t applied = 0, clamped = 0, skipped = 0;
   if (ci < a.ncomp) {
     int32_t* X = a.counts + (size_t)r * nc * N;
     const uint32_t rep = (uint32_t)(a.rep_base + r), k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    int cur = -1;
     const int p1 = a.comp_off[a.comp0 + ci + 1];
     for (int pi = a.comp_off[a.comp0 + ci]; pi < p1; ++pi) {
       const int e = a.comp_ev[pi];
@@ -180,15 +310,21 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
       const int kind = rec.w & 0xff, sel = (rec.w >> 8) & 0xff, sh = (rec.w >> 16) & 0xff;
       const uint32_t mask = m.select[sel];
       const int8_t* off = m.shift[sh];
+      if (node != cur) {
+        if (cur >= 0)
+          for (int c = 0; c < nc; ++c) X[(size_t)c * N + cur] = cc[c * S];
+        for (int c = 0; c < nc; ++c) cc[c * S] = X[(size_t)c * N + node];
+        cur = node;
+      }
       if (kind == SIM_ENTER) {
         const int c0 = __ffs(mask) - 1;
-        X[(size_t)(c0 + off[c0]) * N + node] += n;
+        cc[(c0 + off[c0]) * S] += n;
         ++applied;
         continue;
       }
       long long avail = 0;
       for (int c = 0; c < nc; ++c)
-        if (mask >> c & 1u) avail += X[(size_t)c * N + node];
+        if (mask >> c & 1u) avail += cc[c * S];
       int take = n;
       if ((long long)n > avail) {
         if (a.underflow_error) {
@@ -212,16 +348,18 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
         int got = 0;
         for (int c = 0; c < nc; ++c) {
           if (!(mask >> c & 1u)) continue;
-          const uint32_t have = (uint32_t)X[(size_t)c * N + node];
+          const uint32_t have = (uint32_t)cc[c * S];
           if (slot < have) { got = c; break; }
           slot -= have;
         }
-        X[(size_t)got * N + node] -= 1;
-        if (kind == SIM_INTERNAL) X[(size_t)(got + off[got]) * N + node] += 1;
+        cc[got * S] -= 1;
+        if (kind == SIM_INTERNAL) cc[(got + off[got]) * S] += 1;
         else if (kind == SIM_EXTERNAL) X[(size_t)(got + off[got]) * N + dest] += 1;
       }
       ++applied;
     }
+    if (cur >= 0)
+      for (int c = 0; c < nc; ++c) X[(size_t)c * N + cur] = cc[c * S];
   }
   const uint32_t sa = __reduce_add_sync(0xffffffffu, applied);
   const uint32_t sc = __reduce_add_sync(0xffffffffu, clamped);
@@ -261,15 +399,21 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_cont(GenContArgs a) {
 
 }  // namespace
 
-size_t gen_ssa_smem_bytes(int nc) {
-  return sizeof(GenModelDev) + sizeof(GenRepParams) + (size_t)nc * kGenThreads * sizeof(int32_t);
+size_t gen_ssa_smem_bytes(int nc, int nt) {
+  return sizeof(GenModelDev) + sizeof(GenRepParams) + (kGenThreads / 32) * 32 * sizeof(double) +
+         (size_t)2 * nt * kGenThreads * sizeof(double) + (kGenThreads / 32) * (kGenMaxComp + 32) * sizeof(int32_t) +
+         (size_t)nc * kGenThreads * sizeof(int32_t);
 }
 
-cudaError_t launch_gen_ssa(const GenSsaArgs& a, int nt, int nc, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.N + kGenThreads - 1) / kGenThreads), (unsigned)a.R);
-  const size_t smem = gen_ssa_smem_bytes(nc);
-  if (nt <= 8) k_gen_ssa<8><<<grid, kGenThreads, smem, st>>>(a);
-  else k_gen_ssa<kGenMaxTrans><<<grid, kGenThreads, smem, st>>>(a);
+cudaError_t launch_gen_ssa(GenSsaArgs a, int nt, int nc, cudaStream_t st) {
+  a.warp_blocks = (a.n_big + kGenThreads / 32 - 1) / (kGenThreads / 32);
+  const dim3 grid((unsigned)(a.warp_blocks + (a.N - a.n_big + kGenThreads - 1) / kGenThreads), (unsigned)a.R);
+  const size_t smem = gen_ssa_smem_bytes(nc, nt);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_gen_ssa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_gen_ssa<<<grid, kGenThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

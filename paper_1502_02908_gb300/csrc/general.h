@@ -46,6 +46,8 @@ struct GenSsaArgs {
   unsigned long long* ctr;      // [R][4]
   uint64_t seed;
   int32_t rep_base, N, R, day;
+  int32_t n_big;                // leading nodes of the order simulated one per warp
+  int32_t warp_blocks;          // blocks holding them (set by the launcher)
 };
 
 // Event record, 16 bytes: {node, dest, count, kind | select << 8 | shift row << 16}.
@@ -71,8 +73,8 @@ struct GenContArgs {
   int32_t N, R, day;
 };
 
-size_t gen_ssa_smem_bytes(int nc);
-cudaError_t launch_gen_ssa(const GenSsaArgs& a, int nt, int nc, cudaStream_t st);
+size_t gen_ssa_smem_bytes(int nc, int nt);
+cudaError_t launch_gen_ssa(GenSsaArgs a, int nt, int nc, cudaStream_t st);
 cudaError_t launch_gen_events(const GenEvArgs& a, cudaStream_t st);
 cudaError_t launch_gen_cont(const GenContArgs& a, cudaStream_t st);
 

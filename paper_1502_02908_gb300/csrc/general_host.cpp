@@ -6,6 +6,7 @@
 #include "general.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -37,6 +38,9 @@ struct gen_handle {
   std::vector<int32_t> day_comp;    // [max_days + 1] first component of each day
   int32_t day = 0;
   int32_t launch_mode = 0;          // 0 stream, 1 CUDA graph
+  std::vector<int64_t> pop_sorted;  // initial node populations in the node order (descending)
+  int32_t warp_threshold = -1;      // initial population from which a node gets a warp (-1: automatic)
+  int32_t n_big = 0;                // nodes simulated one per warp
   cudaGraphExec_t graph_exec = nullptr;
   int32_t graph_d0 = -1, graph_nd = -1;
   std::string err;
@@ -169,13 +173,22 @@ sim_status latched(gen_handle* h) {
   return SIM_OK;
 }
 
+constexpr int32_t kAutoWarpThreshold = 300;
+
+void set_n_big(gen_handle* h) {
+  const int64_t thr = h->warp_threshold < 0 ? kAutoWarpThreshold : h->warp_threshold;
+  int32_t n = 0;
+  while (n < (int32_t)h->pop_sorted.size() && h->pop_sorted[n] >= thr) ++n;
+  h->n_big = n;
+}
+
 sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) {
   const int N = h->cfg.n_nodes, R = h->cfg.n_replicates;
   for (int32_t d = d0; d < d0 + nd; ++d) {
     GenSsaArgs s{};
     s.counts = h->d_counts; s.y = h->d_y; s.mid = h->d_mid; s.model = h->d_model; s.params = h->d_params;
     s.order = h->d_order; s.ctr = h->d_ctr; s.seed = h->cfg.seed; s.rep_base = h->cfg.replicate_base;
-    s.N = N; s.R = R; s.day = d;
+    s.N = N; s.R = R; s.day = d; s.n_big = h->n_big;
     GCK(h, launch_gen_ssa(s, h->nt, h->nc, st), "stochastic step launch");
     const int32_t c0 = h->day_comp[d], c1 = h->day_comp[d + 1];
     if (c1 > c0) {
@@ -264,6 +277,9 @@ sim_status gen_create(const gen_model* m, const gen_config* cfg, const int32_t* 
   std::vector<int32_t> order((size_t)N);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return tot[a] > tot[b]; });
+  h->pop_sorted.resize((size_t)N);
+  for (int i = 0; i < N; ++i) h->pop_sorted[i] = tot[order[i]];
+  set_n_big(h);
   const size_t ncount = (size_t)R * nc * N, ncy = (size_t)R * ny * N;
   cudaError_t e = galloc(&h->d_counts, ncount);
   if (e == cudaSuccess) e = galloc(&h->d_y, ncy);
@@ -303,7 +319,7 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
   const int N = h->cfg.n_nodes, T = h->cfg.max_days, nc = h->nc;
   const GenModelDev& m = h->model;
   for (int64_t e = 0; e < n; ++e) {
-    if (day[e] < 0 || day[e] >= T) return gfail(h, SIM_E_INVALID_ARG, "event %lld: day %d outside [0, %d)", (long long)e, day[e], T);
+    if (day[e] < 0) return gfail(h, SIM_E_INVALID_ARG, "event %lld: day %d < 0", (long long)e, day[e]);
     if (kind[e] < SIM_EXIT || kind[e] > SIM_EXTERNAL) return gfail(h, SIM_E_INVALID_ARG, "event %lld: kind %d", (long long)e, kind[e]);
     if (node[e] < 0 || node[e] >= N) return gfail(h, SIM_E_INVALID_ARG, "event %lld: node %d", (long long)e, node[e]);
     if (kind[e] == SIM_EXTERNAL && (dest[e] < 0 || dest[e] >= N || dest[e] == node[e]))
@@ -328,18 +344,22 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
   }
   free_graph(h);
   free_events(h);
-  if (n == 0) return SIM_OK;
-  // day-stable order
+  // day-stable order of the events before the horizon (those after it come later
+  // in that order, so dropping them leaves every position unchanged)
   std::vector<int64_t> first((size_t)T + 1, 0);
-  for (int64_t e = 0; e < n; ++e) first[day[e] + 1]++;
+  for (int64_t e = 0; e < n; ++e)
+    if (day[e] < T) first[day[e] + 1]++;
   for (int d = 0; d < T; ++d) first[d + 1] += first[d];
-  std::vector<int32_t> order((size_t)n);
+  const int64_t nk = first[T];
+  if (nk == 0) return SIM_OK;
+  std::vector<int32_t> order((size_t)nk);
   {
     std::vector<int64_t> fill(first.begin(), first.end() - 1);
-    for (int64_t e = 0; e < n; ++e) order[fill[day[e]]++] = (int32_t)e;
+    for (int64_t e = 0; e < n; ++e)
+      if (day[e] < T) order[fill[day[e]]++] = (int32_t)e;
   }
-  std::vector<int4> rec((size_t)n);
-  for (int64_t s = 0; s < n; ++s) {
+  std::vector<int4> rec((size_t)nk);
+  for (int64_t s = 0; s < nk; ++s) {
     const int32_t e = order[s];
     const int row = shift[e] < 0 ? kGenNoShift : shift[e];
     rec[s] = make_int4(node[e], kind[e] == SIM_EXTERNAL ? dest[e] : -1, count[e],
@@ -387,10 +407,10 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
   }
   h->day_comp[T] = (int32_t)comp_off.size();
   comp_off.push_back((int32_t)comp_ev.size());
-  cudaError_t e = galloc(&h->d_rec, (size_t)n);
+  cudaError_t e = galloc(&h->d_rec, (size_t)nk);
   if (e == cudaSuccess) e = galloc(&h->d_comp_ev, comp_ev.size());
   if (e == cudaSuccess) e = galloc(&h->d_comp_off, comp_off.size());
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_rec, rec.data(), (size_t)n * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_rec, rec.data(), (size_t)nk * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_comp_ev, comp_ev.data(), comp_ev.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_comp_off, comp_off.data(), comp_off.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -486,8 +506,17 @@ sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value) {
     h->launch_mode = (int32_t)value;
     return SIM_OK;
   }
+  if (option == GEN_OPT_WARP_THRESHOLD) {
+    if (value < -1 || value > INT32_MAX) return gfail(h, SIM_E_INVALID_ARG, "warp threshold %lld", (long long)value);
+    free_graph(h);
+    h->warp_threshold = (int32_t)value;
+    set_n_big(h);
+    return SIM_OK;
+  }
   return gfail(h, SIM_E_INVALID_ARG, "option %d unknown", option);
 }
+
+int32_t gen_warp_nodes(const gen_handle* h) { return h ? h->n_big : -1; }
 
 void gen_destroy(gen_handle* h) {
   if (!h) return;

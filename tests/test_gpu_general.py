@@ -23,9 +23,10 @@ def _cuda():
     B.load_library()
 
 
-def _run(w, launch="stream", splits=None):
+def _run(w, launch="stream", splits=None, warp=-1):
     s = B.GenSim.from_workload(w)
     s.set_launch(launch)
+    s.set_warp_threshold(warp)
     for nd in (splits or [w.T]):
         s.run(nd)
     counts, y, day = s.state()
@@ -59,17 +60,33 @@ def test_seirs_two_variables_bitexact(source):
     assert ref.counters[:, 0].min() > 100_000
 
 
-def test_erlang_eleven_transitions_bitexact():
+# warp per node for every node (0), for none (2^30), for the largest (default)
+@pytest.mark.parametrize("warp", [0, 1 << 30, -1, 100])
+def test_warp_method_bitexact(warp):
+    w = W.seirs_env(N=2000 + 11, T=40, n_events=20_000, R=2, y_source=W.Y_MIDPOINT)
+    _same(w, _run(w, warp=warp))
+
+
+@pytest.mark.parametrize("warp", [0, 1 << 30, -1])
+def test_erlang_eleven_transitions_bitexact(warp):
     w = W.erlang_sis(N=1500 + 3, T=40, n_events=8000, R=2)
     w.rates[1] *= 1.5
-    ref = _same(w, _run(w))
+    ref = _same(w, _run(w, warp=warp))
     assert ref.counters[:, 0].min() > 1_000_000
 
 
-def test_sise3_general_national_shape_bitexact():
+@pytest.mark.parametrize("freq,warp", [(True, 0), (False, 0), (True, 60)])
+def test_sir_warp_bitexact(freq, warp):
+    # SIR nodes run out of transitions (a0 = 0) inside a round
+    w = W.sir_general(N=900, T=40, n_events=3000, R=1, freq=freq, beta=0.6 if freq else 0.01)
+    _same(w, _run(w, warp=warp))
+
+
+@pytest.mark.parametrize("warp", [-1, 0])
+def test_sise3_general_national_shape_bitexact(warp):
     w = W.as_general(W.sise3_national(N=3000, T=60, n_events=40_000, R=2))
     w.rates[1] *= 1.4
-    ref = _same(w, _run(w))
+    ref = _same(w, _run(w, warp=warp))
     assert ref.counters[:, 1].min() > 1000
 
 
@@ -91,7 +108,7 @@ def test_graph_launch_and_split_runs_bitexact():
     ref = oracle.run_general(w)
     _same(w, _run(w, launch="graph"), ref)
     _same(w, _run(w, splits=[7, 1, 20, 12]), ref)
-    _same(w, _run(w, launch="graph", splits=[13, 27]), ref)
+    _same(w, _run(w, launch="graph", splits=[13, 27], warp=0), ref)
 
 
 def test_set_state_round_trip_continues_bitexact():
@@ -155,7 +172,17 @@ def test_rejects_bad_events():
     with pytest.raises(B.SimError):
         s.load_events(bad)
     bad = w.events.take(np.arange(len(w.events)))
-    bad.day[3] = 5
+    bad.day[3] = -1
     with pytest.raises(B.SimError):
         s.load_events(bad)
     s.close()
+
+
+def test_events_past_the_horizon_are_never_reached():
+    w = W.seirs_env(N=800, T=40, n_events=6000, R=1)
+    ref = oracle.run_general(w, ndays=25)
+    s = B.GenSim.from_workload(w, max_days=25)     # days 25..39 stay unreached
+    s.run(25)
+    counts, y, _ = s.state()
+    s.close()
+    assert np.array_equal(counts, ref.counts) and np.array_equal(y, ref.y)
