@@ -249,9 +249,25 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
     const int32_t* x0 = warp_unit ? base : x;
     const int s0 = warp_unit ? 1 : stride;
     double y[kGenMaxCont];
-    const double* Y = a.y + (size_t)r * ny * N;
+    double* Y = a.y + (size_t)r * ny * N;
     for (int q = 0; q < ny; ++q) y[q] = Y[(size_t)q * N + v];
     const bool writer = !warp_unit || lane == 0;
+    if (a.prologue) {
+      // day - 1's continuous update from its post-event counts (and, for the
+      // midpoint, the sums saved at its start), then frozen for this day
+      for (int q = 0; q < ny; ++q) {
+        double U = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
+        double D = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
+        if (m.y_source == kGenYMidpoint) {
+          const double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
+          U = __dmul_rn(0.5, __dadd_rn(M[v], U));
+          D = __dmul_rn(0.5, __dadd_rn(M[(size_t)N + v], D));
+        }
+        y[q] = gen_y_next(m, p, q, a.day - 1, y[q], U, D);
+        if (writer) Y[(size_t)q * N + v] = y[q];
+      }
+      if (warp_unit) __syncwarp();
+    }
     if (m.y_source == kGenYMidpoint && writer) {
       for (int q = 0; q < ny; ++q) {
         double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
@@ -268,11 +284,10 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
     if (writer) {
       for (int c = 0; c < nc; ++c) X[(size_t)c * N + v] = x0[c * s0];
       if (m.y_source == kGenYPreEvent) {
-        double* Yw = a.y + (size_t)r * ny * N;
         for (int q = 0; q < ny; ++q) {
           const double U = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
           const double D = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
-          Yw[(size_t)q * N + v] = gen_y_next(m, p, q, a.day, y[q], U, D);
+          Y[(size_t)q * N + v] = gen_y_next(m, p, q, a.day, y[q], U, D);
         }
       }
     }
@@ -303,9 +318,14 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
     const uint32_t rep = (uint32_t)(a.rep_base + r), k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     int cur = -1;
     const int p1 = a.comp_off[a.comp0 + ci + 1];
-    for (int pi = a.comp_off[a.comp0 + ci]; pi < p1; ++pi) {
-      const int e = a.comp_ev[pi];
-      const int4 rec = a.rec[e];
+    int pi = a.comp_off[a.comp0 + ci];
+    int e_next = 0;
+    int4 rec_next = make_int4(0, 0, 0, 0);
+    if (pi < p1) { e_next = __ldg(a.comp_ev + pi); rec_next = __ldg(a.rec + pi); }
+    for (; pi < p1; ++pi) {
+      const int e = e_next;
+      const int4 rec = rec_next;
+      if (pi + 1 < p1) { e_next = __ldg(a.comp_ev + pi + 1); rec_next = __ldg(a.rec + pi + 1); }
       const int node = rec.x, dest = rec.y, n = rec.z;
       const int kind = rec.w & 0xff, sel = (rec.w >> 8) & 0xff, sh = (rec.w >> 16) & 0xff;
       const uint32_t mask = m.select[sel];
@@ -372,8 +392,9 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
   }
 }
 
-// Continuous update from the post-event counts, or the midpoint with the sums
-// the stochastic step saved.
+// Continuous update of a run's last day from the post-event counts, or the
+// midpoint with the sums the stochastic step saved (earlier days' updates run in
+// the next day's stochastic-step prologue).
 __global__ void __launch_bounds__(kGenThreads) k_gen_cont(GenContArgs a) {
   __shared__ GenModelDev m;
   __shared__ GenRepParams p;

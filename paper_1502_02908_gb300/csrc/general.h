@@ -48,13 +48,14 @@ struct GenSsaArgs {
   int32_t rep_base, N, R, day;
   int32_t n_big;                // leading nodes of the order simulated one per warp
   int32_t warp_blocks;          // blocks holding them (set by the launcher)
+  int32_t prologue;             // 1: first apply day - 1's continuous update (post-event or midpoint)
 };
 
 // Event record, 16 bytes: {node, dest, count, kind | select << 8 | shift row << 16}.
 struct GenEvArgs {
   int32_t* counts;
-  const int4* rec;              // [n_events] in day-stable order (index = Philox position)
-  const int32_t* comp_ev;       // positions grouped by (day, component), input order inside
+  const int4* rec;              // records grouped by (day, component), input order inside
+  const int32_t* comp_ev;       // their positions in the day-stable order (Philox counter word 0)
   const int32_t* comp_off;      // [n_components + 1]
   int32_t comp0, ncomp;         // the day's components
   const GenModelDev* model;

@@ -189,6 +189,7 @@ sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) 
     s.counts = h->d_counts; s.y = h->d_y; s.mid = h->d_mid; s.model = h->d_model; s.params = h->d_params;
     s.order = h->d_order; s.ctr = h->d_ctr; s.seed = h->cfg.seed; s.rep_base = h->cfg.replicate_base;
     s.N = N; s.R = R; s.day = d; s.n_big = h->n_big;
+    s.prologue = (d > d0 && h->ny > 0 && h->model.y_source != GEN_Y_PRE_EVENT) ? 1 : 0;
     GCK(h, launch_gen_ssa(s, h->nt, h->nc, st), "stochastic step launch");
     const int32_t c0 = h->day_comp[d], c1 = h->day_comp[d + 1];
     if (c1 > c0) {
@@ -199,12 +200,13 @@ sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) 
       e.underflow_error = h->cfg.underflow_policy == SIM_UNDERFLOW_ERROR;
       GCK(h, launch_gen_events(e, st), "event step launch");
     }
-    if (h->ny > 0 && h->model.y_source != GEN_Y_PRE_EVENT) {
-      GenContArgs c{};
-      c.counts = h->d_counts; c.y = h->d_y; c.mid = h->d_mid; c.model = h->d_model; c.params = h->d_params;
-      c.N = N; c.R = R; c.day = d;
-      GCK(h, launch_gen_cont(c, st), "continuous update launch");
-    }
+  }
+  // the last day's continuous update (earlier days' run in the next day's prologue)
+  if (nd > 0 && h->ny > 0 && h->model.y_source != GEN_Y_PRE_EVENT) {
+    GenContArgs c{};
+    c.counts = h->d_counts; c.y = h->d_y; c.mid = h->d_mid; c.model = h->d_model; c.params = h->d_params;
+    c.N = N; c.R = R; c.day = d0 + nd - 1;
+    GCK(h, launch_gen_cont(c, st), "continuous update launch");
   }
   return SIM_OK;
 }
@@ -407,10 +409,13 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
   }
   h->day_comp[T] = (int32_t)comp_off.size();
   comp_off.push_back((int32_t)comp_ev.size());
-  cudaError_t e = galloc(&h->d_rec, (size_t)nk);
+  // records in component order beside their positions: each thread streams its list
+  std::vector<int4> rec_c(comp_ev.size());
+  for (size_t i = 0; i < comp_ev.size(); ++i) rec_c[i] = rec[comp_ev[i]];
+  cudaError_t e = galloc(&h->d_rec, rec_c.size());
   if (e == cudaSuccess) e = galloc(&h->d_comp_ev, comp_ev.size());
   if (e == cudaSuccess) e = galloc(&h->d_comp_off, comp_off.size());
-  if (e == cudaSuccess) e = cudaMemcpy(h->d_rec, rec.data(), (size_t)nk * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_rec, rec_c.data(), rec_c.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_comp_ev, comp_ev.data(), comp_ev.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->d_comp_off, comp_off.data(), comp_off.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
