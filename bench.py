@@ -45,15 +45,19 @@ FP64_PER_NODE_DAY = {3: 34, 1: 24}
 SSA_PROFILE = os.path.join(ROOT, "profiles", "k_node_day_dealt_national_day300.md")
 
 
+# what the stochastic-step kernel and its launch shape are built from
+SSA_SOURCES = ("ssa.cu", "ssa_device.cuh", "devmath.cuh", "softdiv.cuh", "neglog_table.h", "internal.h",
+               "host.cpp")
+
+
 def kernel_sources_digest():
     import hashlib
     d = os.path.join(ROOT, "paper_1502_02908_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in SSA_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
@@ -270,7 +274,7 @@ def general_leg(args, B, W, torch, oracle_check):
                             f"{m.nc} compartments, {m.nt} transitions, {m.ny} continuous variables",
                 "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "transitions_per_s": trans / (ms / 1000),
                 "transitions_per_step": trans, "ms_per_step": ms, "steps": steps, "warmup": warm,
-                "gpu_launches_per_step": w.T * (2 + (1 if m.ny and m.y_source != W.Y_PRE_EVENT else 0)),
+                "gpu_launches_per_step": 2 * w.T + (1 if m.ny and m.y_source != W.Y_PRE_EVENT else 0),
                 "warp_threshold": thr, "warp_nodes": n_warp}
         if oracle_check:
             import oracle
