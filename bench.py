@@ -159,9 +159,10 @@ def batched_leg(args, B, W, torch, plain_value):
     w = W.sise3_batched(R=256, T=365)
     # the persistent kernel is for uneven batches; on one handle its per-replicate
     # level-scheduled event step loses to the daily launches over a long horizon
-    best, _ = autotune.autotune(w, days=20, thresholds=(1 << 30,), modes=("stream", "graph"), repeats=1)
+    best, _ = autotune.autotune(w, days=20, thresholds=(1 << 30,), modes=("stream", "graph"), repeats=1,
+                                groups=(1 << 30, 800))
     sim = B.Sim.from_workload(w)
-    sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
+    sim.set_group_threshold(best["group_threshold"]); sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
     u0 = np.repeat(w.u0[None], w.R, 0); phi0 = np.repeat(w.phi0[None], w.R, 0)
     steps, warm = 2, 1
     times = []
