@@ -22,8 +22,6 @@ __device__ __forceinline__ void copy16(void* dst, const void* src, int n16) {
   for (int i = threadIdx.x; i < n16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-__device__ __forceinline__ double ll_to_double(long long n) { return __ll2double_rn(n); }
-
 // Exact binary64 of 0 <= n < 2^53 on the integer pipe.
 __device__ __forceinline__ double u2d_exact(long long n) {
   if (n <= 0) return 0.0;
@@ -407,8 +405,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_cont(GenContArgs a) {
   const int32_t* X = a.counts + (size_t)r * nc * N + v;
   double* Y = a.y + (size_t)r * ny * N + v;
   for (int q = 0; q < ny; ++q) {
-    double U = ll_to_double(mask_sum(X, N, m.num[q], nc));
-    double D = ll_to_double(mask_sum(X, N, m.den[q], nc));
+    double U = u2d_exact(mask_sum(X, N, m.num[q], nc));
+    double D = u2d_exact(mask_sum(X, N, m.den[q], nc));
     if (m.y_source == kGenYMidpoint) {
       const double* M = a.mid + ((size_t)r * ny + q) * 2 * N + v;
       U = __dmul_rn(0.5, __dadd_rn(M[0], U));
