@@ -186,3 +186,31 @@ def test_events_past_the_horizon_are_never_reached():
     counts, y, _ = s.state()
     s.close()
     assert np.array_equal(counts, ref.counts) and np.array_equal(y, ref.y)
+
+
+@pytest.mark.parametrize("warp", [0, 1 << 30])
+def test_largest_model_bitexact(warp):
+    # 16 compartments and 32 transitions (the limits): a ring C_i -> C_(i+1) at
+    # k C_i and C_i -> C_(i+2) at k' C_i C_(i+1) / N, four continuous variables;
+    # the stochastic step then needs more than 48 KB of shared memory per block
+    comps = tuple(f"C{i}" for i in range(16))
+    tr = []
+    for i in range(16):
+        tr.append(dict(change={comps[i]: -1, comps[(i + 1) % 16]: 1}, a=comps[i], cont=i % 4))
+    for i in range(16):
+        tr.append(dict(change={comps[i]: -1, comps[(i + 2) % 16]: 1}, a=comps[i], b=comps[(i + 1) % 16], pop=comps))
+    variables = [((comps[q],), comps) for q in range(3)] + [((comps[3], comps[4]), ())]
+    m = W.general_model(comps, tr, variables=variables, selects=[comps, comps[:4]], shifts=[{c: 4 for c in comps[:4]}],
+                        y_source=W.Y_MIDPOINT)
+    assert m.nc == 16 and m.nt == 32
+    N, T, R = 700, 12, 2
+    rng = np.random.default_rng(8)
+    u0 = rng.integers(0, 40, size=(16, N)).astype(np.int32)
+    y0 = rng.uniform(0.5, 1.5, size=(4, N))
+    rates = rng.uniform(0.01, 0.2, size=(R, 32))
+    vp = W._var_params(R, 4, (1.0, 0.5, 0.2, 0.01), (0.1, 0.2, 0.3, 0.05), (1e-3, 0.0, 0.0, 1e-4))
+    ev = W._general_events(rng, N, T, 3000, [(0.3, W.EXIT, [0, 1], [-1]), (0.2, W.ENTER, [1], [-1, 0]),
+                                             (0.2, W.INTERNAL, [1], [0]), (0.3, W.EXTERNAL, [0, 1], [-1, 0])])
+    w = W.GeneralWorkload("ring16", m, N, T, R, u0, y0, rates, vp, ev, 21)
+    ref = _same(w, _run(w, warp=warp))
+    assert ref.counters[:, 0].min() > 10_000
