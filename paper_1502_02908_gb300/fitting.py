@@ -156,3 +156,89 @@ def hooke_jeeves(f, x0, step, iterations=20, shrink=0.5, min_step=0.0):
         if np.all(s < min_step):
             break
     return SearchResult(base, fb, it, len(cache), history)
+
+
+# ------------------------------------------------------------- gradient-based variant
+# The goal above compares region totals of a few trajectories and is searched
+# without derivatives.  The score-function gradient of the library (d E[f] /
+# d theta = E[f s], s = d log p(path) / d theta, see gradient.py) gives a
+# gradient-based variant on the daily national prevalence f_d = I_d / N_d:
+#   G_f(x)^2 = sum_d (E[f_d](theta(x)) - f*_d)^2,  theta(x) = (upsilon e^{x_0},
+# gamma e^{x_1}) with the age-class ratios kept, searched in log scale.
+
+
+def scaled_params(params: W.Params, x):
+    """params with upsilon scaled by e^{x_0} and gamma by e^{x_1} (every class)."""
+    x = np.asarray(x, np.float64)
+    return W.Params(params.upsilon * np.exp(x[0]), params.gamma * np.exp(x[1]), params.alpha.copy(),
+                    params.beta.copy(), params.epsilon.copy())
+
+
+def prevalence_curve(w: W.Workload, days, x=(0.0, 0.0), seed_offset=0):
+    """E[f_d] over w.R replicates at log scales x (replicate streams of seed w.seed + seed_offset)."""
+    from . import gradient as GR
+    wx = dataclasses.replace(w, params=scaled_params(w.params, x), seed=w.seed + seed_offset)
+    m, R, _ = GR.run_moments(GR.GradientSpec(wx, np.asarray(days, np.int32)))
+    return m[:, 0] / R
+
+
+class PrevalenceGoal:
+    """G_f(x)^2 and its score-function gradient in x (log scales of upsilon and
+    gamma) for the workload's R replicates against a target curve f*."""
+
+    def __init__(self, w: W.Workload, days, target, chunk=1024):
+        self.w, self.days, self.target, self.chunk = w, np.asarray(days, np.int32), np.asarray(target), chunk
+        self.evaluations = 0
+
+    def __call__(self, x):
+        """(G_f^2, gradient [2], standard error of the gradient [2])."""
+        from . import gradient as GR
+        wx = dataclasses.replace(self.w, params=scaled_params(self.w.params, x))
+        spec = GR.GradientSpec(wx, self.days, self.chunk)
+        m, R, (f, s) = GR.run_moments(spec, per_replicate=True)
+        mean_f, grad, _ = GR.estimate(m, R, spec.class_ratios())    # d E[f_d] / d (upsilon_1, gamma_1, ...)
+        self.evaluations += 1
+        diff = mean_f - self.target
+        th = spec.theta()
+        # d theta_i / d x_i = theta_i for theta = theta_0 e^{x}
+        dth = np.array([th[0], th[1]])
+        g = 2.0 * (diff @ grad[:, :2]) * dth
+        # standard error of g from the replicates' centred contributions
+        ru, rg = spec.class_ratios()
+        na = ru.size
+        s_up = s[:, :na] @ ru                                      # score of upsilon_1 with ratios kept
+        s_ga = s[:, 3:3 + na] @ rg
+        fc = (f - f.mean(0)) @ diff                                # [R]
+        contrib = 2.0 * np.stack([fc * (s_up - s_up.mean()), fc * (s_ga - s_ga.mean())], 1) * dth
+        g_se = contrib.std(0, ddof=1) / np.sqrt(R)
+        return float(diff @ diff), g, g_se
+
+
+def gradient_descent(fg, x0, step, iterations=20, shrink=0.5, grow=1.5, min_step=0.0):
+    """Normalised gradient descent with an acceptance test, for a goal whose
+    gradient is an estimate: from x try x - step g / |g|; keep it when the goal
+    decreases (and lengthen the step by `grow`), otherwise shorten the step by
+    `shrink`.  fg(x) returns (value, gradient, ...).  Stops after `iterations`
+    trials or when the step falls below min_step."""
+    x = np.array(x0, np.float64)
+    fx, gx = fg(x)[:2]
+    s = float(step)
+    history = [(0, x.copy(), fx)]
+    evaluations = 1
+    it = 0
+    for it in range(1, iterations + 1):
+        n = float(np.linalg.norm(gx))
+        if n == 0.0:
+            break
+        y = x - s * gx / n
+        fy, gy = fg(y)[:2]
+        evaluations += 1
+        if fy < fx:
+            x, fx, gx = y, fy, gy
+            s *= grow
+        else:
+            s *= shrink
+        history.append((it, x.copy(), fx))
+        if s < min_step:
+            break
+    return SearchResult(x, fx, it, evaluations, history)

@@ -117,3 +117,18 @@ def test_pattern_search_reduces_goal_from_1_6_k_star():
         assert goal.evaluations >= res.evaluations
     finally:
         goal.close()
+
+
+def test_gradient_fit_recovers_scales():
+    # prevalence goal with the score-function gradient: from (1.5 upsilon*, 0.7 gamma*)
+    # back to (upsilon*, gamma*); the target curve comes from independent streams
+    w = W.sise_plain(N=400, T=60, n_events=2000, R=256)
+    days = np.arange(2, 60, 3)
+    target = F.prevalence_curve(w, days, seed_offset=101)
+    goal = F.PrevalenceGoal(w, days, target)
+    x0 = np.log([1.5, 0.7])
+    g0, grad0, se0 = goal(x0)
+    assert np.all(np.abs(grad0) > 3 * se0)             # the estimate resolves the gradient here
+    r = F.gradient_descent(goal, x0, step=0.2, iterations=25)
+    assert r.f < 0.01 * g0
+    assert np.all(np.abs(r.x) < 0.08), r.x
