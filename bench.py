@@ -248,12 +248,13 @@ def general_leg(args, B, W, torch, oracle_check):
     from paper_1502_02908_gb300 import autotune
     for name, w, check_days in cases:
         w.T = min(args.days, w.T)
-        thr = -1
+        thr, gthr = -1, -1
         if not args.no_tune:
-            thr, _ = autotune.autotune_general(w, days=max(10, w.T // 8))
+            (thr, gthr), _ = autotune.autotune_general(w, days=max(10, w.T // 8))
         sim = B.GenSim.from_workload(w)
         sim.set_launch("graph")
         n_warp = sim.set_warp_threshold(thr)
+        n_group = sim.set_group_threshold(gthr)
         u0 = w.u0[None]; y0 = w.y0[None]
         steps, warm = 2, 1
         times = []
@@ -276,7 +277,7 @@ def general_leg(args, B, W, torch, oracle_check):
                 "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "transitions_per_s": trans / (ms / 1000),
                 "transitions_per_step": trans, "ms_per_step": ms, "steps": steps, "warmup": warm,
                 "gpu_launches_per_step": 2 * w.T + (1 if m.ny and m.y_source != W.Y_PRE_EVENT else 0),
-                "warp_threshold": thr, "warp_nodes": n_warp}
+                "warp_threshold": thr, "warp_nodes": n_warp, "group_threshold": gthr, "group_nodes": n_group}
         if oracle_check:
             import oracle
             oracle.build()

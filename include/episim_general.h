@@ -164,13 +164,16 @@ sim_status gen_counters(gen_handle* h, int64_t* counters);
  *       as a CUDA graph (captured once per (first day, ndays));
  *   GEN_OPT_WARP_THRESHOLD: nodes whose initial population (sum of u0) is at least
  *       this run the stochastic step one per warp, 32 draws at a time with a
- *       fixed-point iteration over the lanes; the others one per thread
- *       (-1: automatic, 300). */
-enum { GEN_OPT_LAUNCH = 1, GEN_OPT_WARP_THRESHOLD = 2 };
+ *       fixed-point iteration over the lanes (-1: automatic, 600);
+ *   GEN_OPT_GROUP_THRESHOLD: nodes below the warp threshold whose initial
+ *       population is at least this run four per warp, 8 lanes and 8 draws at a
+ *       time each (-1: automatic, 150); the rest one per thread. */
+enum { GEN_OPT_LAUNCH = 1, GEN_OPT_WARP_THRESHOLD = 2, GEN_OPT_GROUP_THRESHOLD = 3 };
 sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value);
 
-/* Nodes the stochastic step runs one per warp (-1 for a NULL handle). */
+/* Nodes the stochastic step runs one per warp, and four per warp (-1 for a NULL handle). */
 int32_t gen_warp_nodes(const gen_handle* h);
+int32_t gen_group_nodes(const gen_handle* h);
 
 void gen_destroy(gen_handle* h);
 

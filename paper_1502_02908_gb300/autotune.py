@@ -72,15 +72,17 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
     return {"warp_threshold": thr, "group_threshold": gthr, "launch": mode}, table
 
 
-GENERAL_WARP_THRESHOLDS = (1 << 30, 1000, 600, 300, 150)
+GENERAL_WARP_THRESHOLDS = (1 << 30, 1000, 600, 300)
+GENERAL_GROUP_THRESHOLDS = (1 << 30, 300, 150, 100)
 
 
-def autotune_general(workload, days=None, thresholds=GENERAL_WARP_THRESHOLDS, repeats=1):
-    """The general model's warp threshold (initial node population from which the
-    stochastic step takes a warp per node): times each candidate over a prefix of
-    the horizon with the CUDA-graph day loop, checks that all end in the
-    bit-identical state and counters, and returns (best threshold, table
-    [(threshold, warp nodes, ms)])."""
+def autotune_general(workload, days=None, thresholds=GENERAL_WARP_THRESHOLDS, groups=GENERAL_GROUP_THRESHOLDS,
+                     repeats=1):
+    """The general model's warp and group thresholds (initial node populations from
+    which the stochastic step takes a warp, or an 8-lane segment, per node): times
+    each pair (group below warp) over a prefix of the horizon with the CUDA-graph
+    day loop, checks that all end in the bit-identical state, and returns (best
+    (warp, group), table [(warp, group, warp nodes, group nodes, ms)])."""
     import torch
     w = workload
     nd = min(w.T, days if days is not None else max(10, w.T // 10))
@@ -91,8 +93,11 @@ def autotune_general(workload, days=None, thresholds=GENERAL_WARP_THRESHOLDS, re
     ref = None
     table = []
     try:
-        for thr in thresholds:
+        for thr, gthr in itertools.product(thresholds, groups):
+            if gthr >= thr and gthr != groups[0]:
+                continue
             nb = sim.set_warp_threshold(thr)
+            ng = sim.set_group_threshold(gthr)
             best = float("inf")
             for rep in range(repeats + 1):
                 sim.set_state(u0, y0, 0)
@@ -107,8 +112,9 @@ def autotune_general(workload, days=None, thresholds=GENERAL_WARP_THRESHOLDS, re
             if ref is None:
                 ref = fp
             elif fp != ref:
-                raise AssertionError(f"warp threshold {thr} changed the results")
-            table.append((thr, nb, best))
+                raise AssertionError(f"thresholds ({thr}, {gthr}) changed the results")
+            table.append((thr, gthr, nb, ng, best))
     finally:
         sim.close()
-    return min(table, key=lambda x: x[2])[0], table
+    b = min(table, key=lambda x: x[4])
+    return (b[0], b[1]), table

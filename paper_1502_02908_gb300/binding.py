@@ -59,7 +59,7 @@ class GenConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-GEN_OPT_LAUNCH, GEN_OPT_WARP_THRESHOLD = 1, 2
+GEN_OPT_LAUNCH, GEN_OPT_WARP_THRESHOLD, GEN_OPT_GROUP_THRESHOLD = 1, 2, 3
 
 
 def library_path() -> pathlib.Path:
@@ -135,6 +135,8 @@ def load_library(build_if_missing: bool = True):
         L.gen_last_error.restype = ctypes.c_char_p
         L.gen_warp_nodes.argtypes = [vp]
         L.gen_warp_nodes.restype = ctypes.c_int32
+        L.gen_group_nodes.argtypes = [vp]
+        L.gen_group_nodes.restype = ctypes.c_int32
         L.sim_warp_nodes.argtypes = [vp]
         L.sim_warp_nodes.restype = ctypes.c_int32
         L.sim_debug_schedule_size.argtypes = [vp]
@@ -486,6 +488,12 @@ class GenSim:
         """Nodes with at least this initial population run one per warp (-1: automatic)."""
         self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_WARP_THRESHOLD, int(population)))
         return self.L.gen_warp_nodes(self.h)
+
+    def set_group_threshold(self, population):
+        """Nodes below the warp threshold with at least this initial population run
+        four per warp (-1: automatic); returns how many."""
+        self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_GROUP_THRESHOLD, int(population)))
+        return self.L.gen_group_nodes(self.h)
 
     def run(self, days, stream=None):
         st = current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -136,69 +136,92 @@ __device__ __forceinline__ uint32_t gen_node_day(const GenModelDev& m, const Gen
   return fired;
 }
 
-// Direct method of one node-day by a warp, 32 draws per round.  Lane l takes
-// draw k + l.  Its state is the round's base state plus the transitions the
-// lanes before it choose; the choices are found by a fixed-point iteration (each
-// lane chooses at the state the current choices of the lanes before it imply;
-// lane 0's choice is final after one pass, and each pass fixes at least one more
-// lane, so the choices settle within 32 passes).  The clock then runs over the
-// lanes in draw order with the binary64 sums of the sequential method, so the
-// result is that method's.  xl: this lane's counts (shared memory, stride as in
-// the thread method); base: the warp's counts at the start of the round; ctau,
-// cch: the warp's 32 clock increments and choices.
-__device__ __forceinline__ uint32_t gen_warp_node_day(const GenModelDev& m, const GenRepParams& p, int32_t* xl,
-                                                      int32_t* base, int stride, const RateRow& R, double* ctau,
-                                                      int32_t* cch, const double* y, uint32_t v, uint32_t day,
-                                                      uint32_t rep, uint32_t k0, uint32_t k1, int lane) {
+// Direct method of one node-day by a segment of SEG lanes (a whole warp, SEG =
+// 32, or a quarter, SEG = 8, four nodes to a warp), SEG draws per round.  Lane l
+// of the segment takes draw k + l.  Its state is the round's base state plus the
+// transitions the segment's lanes before it choose; the choices are found by a
+// fixed-point iteration (each lane chooses at the state the current choices of
+// the lanes before it imply; lane 0's choice is final after one pass, and each
+// pass fixes at least one more lane, so the choices settle within SEG passes).
+// The clock then runs over the segment's lanes in draw order with the binary64
+// sums of the sequential method, so the result is that method's.  Every lane of
+// the warp takes part in its collectives; lanes of a segment without a node
+// (live = false) only vote.  xl: this lane's counts (shared memory, stride as in
+// the thread method); base: the segment's counts at the start of the round;
+// ctau, cch: the segment's SEG clock increments and choices; sl, sb: the lane's
+// index in its segment and the segment's first lane in the warp.
+template <int SEG>
+__device__ __forceinline__ uint32_t gen_seg_node_day(const GenModelDev& m, const GenRepParams& p, int32_t* xl,
+                                                     int32_t* base, int stride, const RateRow& R, double* ctau,
+                                                     int32_t* cch, const double* y, uint32_t v, uint32_t day,
+                                                     uint32_t rep, uint32_t k0, uint32_t k1, int sl, int sb,
+                                                     bool live) {
   const int nt = m.nt, nc = m.nc;
-  const unsigned full = 0xffffffffu, below = (1u << lane) - 1u;
+  const unsigned full = 0xffffffffu;
+  const unsigned seg = SEG == 32 ? full : (((1u << SEG) - 1u) << sb);
+  const unsigned below = ((1u << sl) - 1u) << sb;
+  live = live && nt > 0;
   double t = 0.0;
   uint32_t fired = 0;
-  for (uint32_t kb = 0; nt > 0; kb += 32) {
-    const uint4 w = philox10(make_uint4(v, day, kb + (uint32_t)lane, rep), k0, k1);
-    const double E = neglog_u((((uint64_t)w.y << 32) | w.x) >> 12);
-    const double u2 = uniform_open(w.z, w.w);
+  for (uint32_t kb = 0; __any_sync(full, live); kb += SEG) {
+    double E = 0.0, u2 = 0.0;
+    if (live) {
+      const uint4 w = philox10(make_uint4(v, day, kb + (uint32_t)sl, rep), k0, k1);
+      E = neglog_u((((uint64_t)w.y << 32) | w.x) >> 12);
+      u2 = uniform_open(w.z, w.w);
+    }
     int choice = -1;
     double tau = 0.0;
-    for (int pass = 0; pass <= 32; ++pass) {
-      for (int c = 0; c < nc; ++c) xl[c * stride] = base[c];
+    for (int pass = 0; pass <= SEG; ++pass) {
+      if (live)
+        for (int c = 0; c < nc; ++c) xl[c * stride] = base[c];
       for (int j = 0; j < nt; ++j) {
-        const int cnt = __popc(__ballot_sync(full, choice == j) & below);
+        const int cnt = __popc(__ballot_sync(full, live && choice == j) & below);
         if (cnt) apply_changes(m, xl, stride, j, cnt);
       }
-      for (int j = 0; j < nt; ++j) R.a[j * R.stride] = gen_rate(m, p, xl, stride, y, j);
-      const double a0 = prefix_from(R, nt, 0);
       int next = -1;
-      if (pos(a0)) {
-        next = select_transition(R, nt, __dmul_rn(a0, u2));
-        tau = div_pos(E, a0);
+      if (live) {
+        for (int j = 0; j < nt; ++j) R.a[j * R.stride] = gen_rate(m, p, xl, stride, y, j);
+        const double a0 = prefix_from(R, nt, 0);
+        if (pos(a0)) {
+          next = select_transition(R, nt, __dmul_rn(a0, u2));
+          tau = div_pos(E, a0);
+        }
       }
-      const bool changed = __any_sync(full, next != choice);
+      const bool changed = __any_sync(full, live && next != choice);
       choice = next;
       if (!changed) break;
     }
-    ctau[lane] = tau;
-    cch[lane] = choice;
-    __syncwarp();
-    // clock over the lanes in draw order (every lane runs the same sums)
-    int stop = 32;
-    for (int l = 0; l < 32; ++l) {
-      if (cch[l] < 0) { stop = l; break; }
-      const double tn = __dadd_rn(t, ctau[l]);
-      if (le_nonneg(1.0, tn)) { stop = l; break; }
-      t = tn;
+    if (live) {
+      ctau[sl] = tau;
+      cch[sl] = choice;
     }
-    const unsigned fired_lanes = stop == 32 ? full : ((1u << stop) - 1u);
+    __syncwarp();
+    // clock over the segment's lanes in draw order (every lane of it runs the same sums)
+    int stop = SEG;
+    if (live)
+      for (int l = 0; l < SEG; ++l) {
+        if (cch[l] < 0) { stop = l; break; }
+        const double tn = __dadd_rn(t, ctau[l]);
+        if (le_nonneg(1.0, tn)) { stop = l; break; }
+        t = tn;
+      }
+    const unsigned fired_lanes = stop == SEG ? seg : (((1u << stop) - 1u) << sb);
     for (int j = 0; j < nt; ++j) {
-      const int cnt = __popc(__ballot_sync(full, choice == j) & fired_lanes);
-      if (cnt && lane == 0) apply_changes(m, base, 1, j, cnt);
+      const int cnt = __popc(__ballot_sync(full, live && choice == j) & fired_lanes);
+      if (cnt && live && sl == 0) apply_changes(m, base, 1, j, cnt);
     }
     __syncwarp();
-    fired += (uint32_t)stop;
-    if (stop < 32) break;
+    if (live) {
+      fired += (uint32_t)stop;
+      if (stop < SEG) live = false;
+    }
   }
   return fired;
 }
+
+constexpr int kGenSeg = 8;                          // lanes per node of the group method
+constexpr int kGenWarps = kGenThreads / 32;
 
 __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   extern __shared__ int4 smem4[];
@@ -206,8 +229,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   char* sp = reinterpret_cast<char*>(smem4) + sizeof(GenModelDev);
   GenRepParams& p = *reinterpret_cast<GenRepParams*>(sp);
   sp += sizeof(GenRepParams);
-  double* ctau = reinterpret_cast<double*>(sp);                 // [warps][32]
-  sp += (kGenThreads / 32) * 32 * sizeof(double);
+  double* ctau = reinterpret_cast<double*>(sp);                 // [threads]: per lane
+  sp += kGenThreads * sizeof(double);
   const int r = blockIdx.y;
   copy16(&m, a.model, (int)(sizeof(GenModelDev) / 16));
   copy16(&p, a.params + r, (int)(sizeof(GenRepParams) / 16));
@@ -215,68 +238,88 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   const int nc = m.nc, nt = m.nt, ny = m.ny, N = a.N;
   double* rates = reinterpret_cast<double*>(sp);                // [nt][threads], then partial sums
   sp += (size_t)2 * nt * kGenThreads * sizeof(double);
-  int32_t* wbase = reinterpret_cast<int32_t*>(sp);              // [warps][kGenMaxComp]
-  sp += (kGenThreads / 32) * kGenMaxComp * sizeof(int32_t);
-  int32_t* cch = reinterpret_cast<int32_t*>(sp);                // [warps][32]
-  sp += (kGenThreads / 32) * 32 * sizeof(int32_t);
+  int32_t* sbase = reinterpret_cast<int32_t*>(sp);              // [warps][4 segments][kGenMaxComp]
+  sp += kGenWarps * (32 / kGenSeg) * kGenMaxComp * sizeof(int32_t);
+  int32_t* cch = reinterpret_cast<int32_t*>(sp);                // [threads]: per lane
+  sp += kGenThreads * sizeof(int32_t);
   int32_t* xs = reinterpret_cast<int32_t*>(sp);                 // [nc][threads]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int stride = blockDim.x;
-  const bool warp_unit = (int)blockIdx.x < a.warp_blocks;
+  const int b = (int)blockIdx.x;
+  // units: warp nodes (one per warp), group nodes (four per warp), thread nodes
+  const int kind = b < a.warp_blocks ? 0 : (b < a.warp_blocks + a.group_blocks ? 1 : 2);
+  const int sl = kind == 0 ? lane : (kind == 1 ? (lane & (kGenSeg - 1)) : 0);
+  const int sb = kind == 1 ? (lane & ~(kGenSeg - 1)) : 0;
   int v = -1;
-  if (warp_unit) {
-    const int u = (int)blockIdx.x * (kGenThreads / 32) + warp;
+  if (kind == 0) {
+    const int u = b * kGenWarps + warp;
     if (u < a.n_big) v = a.order[u];
+  } else if (kind == 1) {
+    const int g = ((b - a.warp_blocks) * kGenWarps + warp) * (32 / kGenSeg) + (lane / kGenSeg);
+    if (g < a.n_mid) v = a.order[a.n_big + g];
   } else {
-    const int i = a.n_big + ((int)blockIdx.x - a.warp_blocks) * kGenThreads + (int)threadIdx.x;
+    const int i = a.n_big + a.n_mid + (b - a.warp_blocks - a.group_blocks) * kGenThreads + (int)threadIdx.x;
     if (i < N) v = a.order[i];
   }
+  const bool coop = kind != 2;
+  // a cooperative warp runs when any of its segments has a node; a thread when it has one
+  const bool run = coop ? __any_sync(0xffffffffu, v >= 0) : v >= 0;
   uint32_t fired = 0;
-  if (v >= 0) {
+  if (run) {
+    const bool has = v >= 0;
     int32_t* x = xs + threadIdx.x;
-    int32_t* base = wbase + warp * kGenMaxComp;
+    int32_t* base = sbase + (warp * (32 / kGenSeg) + (kind == 1 ? lane / kGenSeg : 0)) * kGenMaxComp;
     const RateRow R{rates + threadIdx.x, rates + (size_t)nt * kGenThreads + threadIdx.x, kGenThreads};
     int32_t* X = a.counts + (size_t)r * nc * N;
-    if (warp_unit) {
-      for (int c = lane; c < nc; c += 32) base[c] = X[(size_t)c * N + v];
+    if (coop) {
+      if (has)
+        for (int c = sl; c < nc; c += (kind == 0 ? 32 : kGenSeg)) base[c] = X[(size_t)c * N + v];
       __syncwarp();
     } else {
       for (int c = 0; c < nc; ++c) x[c * stride] = X[(size_t)c * N + v];
     }
     // the node's counts at the start of the day, as this lane sees them
-    const int32_t* x0 = warp_unit ? base : x;
-    const int s0 = warp_unit ? 1 : stride;
+    const int32_t* x0 = coop ? base : x;
+    const int s0 = coop ? 1 : stride;
     double y[kGenMaxCont];
     double* Y = a.y + (size_t)r * ny * N;
-    for (int q = 0; q < ny; ++q) y[q] = Y[(size_t)q * N + v];
-    const bool writer = !warp_unit || lane == 0;
-    if (a.prologue) {
-      // day - 1's continuous update from its post-event counts (and, for the
-      // midpoint, the sums saved at its start), then frozen for this day
-      for (int q = 0; q < ny; ++q) {
-        double U = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
-        double D = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
-        if (m.y_source == kGenYMidpoint) {
-          const double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
-          U = __dmul_rn(0.5, __dadd_rn(M[v], U));
-          D = __dmul_rn(0.5, __dadd_rn(M[(size_t)N + v], D));
+    const bool writer = has && (!coop || sl == 0);
+    if (has) {
+      for (int q = 0; q < ny; ++q) y[q] = Y[(size_t)q * N + v];
+      if (a.prologue) {
+        // day - 1's continuous update from its post-event counts (and, for the
+        // midpoint, the sums saved at its start), then frozen for this day
+        for (int q = 0; q < ny; ++q) {
+          double U = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
+          double D = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
+          if (m.y_source == kGenYMidpoint) {
+            const double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
+            U = __dmul_rn(0.5, __dadd_rn(M[v], U));
+            D = __dmul_rn(0.5, __dadd_rn(M[(size_t)N + v], D));
+          }
+          y[q] = gen_y_next(m, p, q, a.day - 1, y[q], U, D);
         }
-        y[q] = gen_y_next(m, p, q, a.day - 1, y[q], U, D);
-        if (writer) Y[(size_t)q * N + v] = y[q];
       }
-      if (warp_unit) __syncwarp();
     }
-    if (m.y_source == kGenYMidpoint && writer) {
-      for (int q = 0; q < ny; ++q) {
-        double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
-        M[v] = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
-        M[(size_t)N + v] = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
-      }
+    if (coop) __syncwarp();
+    if (writer) {
+      if (a.prologue)
+        for (int q = 0; q < ny; ++q) Y[(size_t)q * N + v] = y[q];
+      if (m.y_source == kGenYMidpoint)
+        for (int q = 0; q < ny; ++q) {
+          double* M = a.mid + ((size_t)r * ny + q) * 2 * N;
+          M[v] = u2d_exact(mask_sum(x0, s0, m.num[q], nc));
+          M[(size_t)N + v] = u2d_exact(mask_sum(x0, s0, m.den[q], nc));
+        }
     }
     const uint32_t rep = (uint32_t)(a.rep_base + r), k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-    if (warp_unit)
-      fired = gen_warp_node_day(m, p, x, base, stride, R, ctau + warp * 32, cch + warp * 32, y, (uint32_t)v,
-                                (uint32_t)a.day, rep, k0, k1, lane);
+    const uint32_t vv = (uint32_t)(has ? v : 0);
+    if (kind == 0)
+      fired = gen_seg_node_day<32>(m, p, x, base, stride, R, ctau + warp * 32, cch + warp * 32, y, vv,
+                                   (uint32_t)a.day, rep, k0, k1, sl, sb, has);
+    else if (kind == 1)
+      fired = gen_seg_node_day<kGenSeg>(m, p, x, base, stride, R, ctau + warp * 32 + sb, cch + warp * 32 + sb, y,
+                                        vv, (uint32_t)a.day, rep, k0, k1, sl, sb, has);
     else
       fired = gen_node_day(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1);
     if (writer) {
@@ -289,7 +332,7 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
         }
       }
     }
-    if (warp_unit && lane != 0) fired = 0;
+    if (coop && !writer) fired = 0;
   }
   const uint32_t tot = __reduce_add_sync(0xffffffffu, fired);
   if (lane == 0 && tot) atomicAdd(a.ctr + (size_t)r * 4, (unsigned long long)tot);
@@ -419,14 +462,18 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_cont(GenContArgs a) {
 }  // namespace
 
 size_t gen_ssa_smem_bytes(int nc, int nt) {
-  return sizeof(GenModelDev) + sizeof(GenRepParams) + (kGenThreads / 32) * 32 * sizeof(double) +
-         (size_t)2 * nt * kGenThreads * sizeof(double) + (kGenThreads / 32) * (kGenMaxComp + 32) * sizeof(int32_t) +
+  return sizeof(GenModelDev) + sizeof(GenRepParams) + kGenThreads * sizeof(double) +
+         (size_t)2 * nt * kGenThreads * sizeof(double) +
+         (size_t)(kGenThreads / 32) * (32 / 8) * kGenMaxComp * sizeof(int32_t) + kGenThreads * sizeof(int32_t) +
          (size_t)nc * kGenThreads * sizeof(int32_t);
 }
 
 cudaError_t launch_gen_ssa(GenSsaArgs a, int nt, int nc, cudaStream_t st) {
-  a.warp_blocks = (a.n_big + kGenThreads / 32 - 1) / (kGenThreads / 32);
-  const dim3 grid((unsigned)(a.warp_blocks + (a.N - a.n_big + kGenThreads - 1) / kGenThreads), (unsigned)a.R);
+  a.warp_blocks = (a.n_big + kGenWarps - 1) / kGenWarps;
+  const int per_block = kGenWarps * (32 / kGenSeg);
+  a.group_blocks = (a.n_mid + per_block - 1) / per_block;
+  const int rest = a.N - a.n_big - a.n_mid;
+  const dim3 grid((unsigned)(a.warp_blocks + a.group_blocks + (rest + kGenThreads - 1) / kGenThreads), (unsigned)a.R);
   const size_t smem = gen_ssa_smem_bytes(nc, nt);
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(k_gen_ssa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -47,7 +47,9 @@ struct GenSsaArgs {
   uint64_t seed;
   int32_t rep_base, N, R, day;
   int32_t n_big;                // leading nodes of the order simulated one per warp
-  int32_t warp_blocks;          // blocks holding them (set by the launcher)
+  int32_t n_mid;                // next nodes of the order, four per warp (8-lane segments)
+  int32_t warp_blocks;          // blocks holding the warp nodes (set by the launcher)
+  int32_t group_blocks;         // blocks holding the group nodes (set by the launcher)
   int32_t prologue;             // 1: first apply day - 1's continuous update (post-event or midpoint)
 };
 

@@ -40,7 +40,9 @@ struct gen_handle {
   int32_t launch_mode = 0;          // 0 stream, 1 CUDA graph
   std::vector<int64_t> pop_sorted;  // initial node populations in the node order (descending)
   int32_t warp_threshold = -1;      // initial population from which a node gets a warp (-1: automatic)
+  int32_t group_threshold = -1;     // ... an 8-lane segment (-1: automatic)
   int32_t n_big = 0;                // nodes simulated one per warp
+  int32_t n_mid = 0;                // nodes simulated four per warp
   cudaGraphExec_t graph_exec = nullptr;
   int32_t graph_d0 = -1, graph_nd = -1;
   std::string err;
@@ -173,13 +175,19 @@ sim_status latched(gen_handle* h) {
   return SIM_OK;
 }
 
-constexpr int32_t kAutoWarpThreshold = 300;
+constexpr int32_t kAutoWarpThreshold = 600;
+constexpr int32_t kAutoGroupThreshold = 150;
 
 void set_n_big(gen_handle* h) {
   const int64_t thr = h->warp_threshold < 0 ? kAutoWarpThreshold : h->warp_threshold;
+  const int64_t gthr = h->group_threshold < 0 ? kAutoGroupThreshold : h->group_threshold;
+  const int32_t N = (int32_t)h->pop_sorted.size();
   int32_t n = 0;
-  while (n < (int32_t)h->pop_sorted.size() && h->pop_sorted[n] >= thr) ++n;
+  while (n < N && h->pop_sorted[n] >= thr) ++n;
+  int32_t g = n;
+  while (g < N && h->pop_sorted[g] >= gthr) ++g;
   h->n_big = n;
+  h->n_mid = g - n;
 }
 
 sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) {
@@ -188,7 +196,7 @@ sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) 
     GenSsaArgs s{};
     s.counts = h->d_counts; s.y = h->d_y; s.mid = h->d_mid; s.model = h->d_model; s.params = h->d_params;
     s.order = h->d_order; s.ctr = h->d_ctr; s.seed = h->cfg.seed; s.rep_base = h->cfg.replicate_base;
-    s.N = N; s.R = R; s.day = d; s.n_big = h->n_big;
+    s.N = N; s.R = R; s.day = d; s.n_big = h->n_big; s.n_mid = h->n_mid;
     s.prologue = (d > d0 && h->ny > 0 && h->model.y_source != GEN_Y_PRE_EVENT) ? 1 : 0;
     GCK(h, launch_gen_ssa(s, h->nt, h->nc, st), "stochastic step launch");
     const int32_t c0 = h->day_comp[d], c1 = h->day_comp[d + 1];
@@ -518,10 +526,19 @@ sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value) {
     set_n_big(h);
     return SIM_OK;
   }
+  if (option == GEN_OPT_GROUP_THRESHOLD) {
+    if (value < -1 || value > INT32_MAX) return gfail(h, SIM_E_INVALID_ARG, "group threshold %lld", (long long)value);
+    free_graph(h);
+    h->group_threshold = (int32_t)value;
+    set_n_big(h);
+    return SIM_OK;
+  }
   return gfail(h, SIM_E_INVALID_ARG, "option %d unknown", option);
 }
 
 int32_t gen_warp_nodes(const gen_handle* h) { return h ? h->n_big : -1; }
+
+int32_t gen_group_nodes(const gen_handle* h) { return h ? h->n_mid : -1; }
 
 void gen_destroy(gen_handle* h) {
   if (!h) return;

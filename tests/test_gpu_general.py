@@ -23,10 +23,11 @@ def _cuda():
     B.load_library()
 
 
-def _run(w, launch="stream", splits=None, warp=-1):
+def _run(w, launch="stream", splits=None, warp=-1, group=-1):
     s = B.GenSim.from_workload(w)
     s.set_launch(launch)
     s.set_warp_threshold(warp)
+    s.set_group_threshold(group)
     for nd in (splits or [w.T]):
         s.run(nd)
     counts, y, day = s.state()
@@ -67,11 +68,25 @@ def test_warp_method_bitexact(warp):
     _same(w, _run(w, warp=warp))
 
 
-@pytest.mark.parametrize("warp", [0, 1 << 30, -1])
-def test_erlang_eleven_transitions_bitexact(warp):
+# four nodes per warp (8-lane segments) for every node (group 0), for the middle
+# tier, and mixed with a warp tier; the tail warp holds fewer than four nodes
+@pytest.mark.parametrize("warp,group", [(1 << 30, 0), (1 << 30, 60), (300, 80), (-1, -1)])
+def test_group_method_bitexact(warp, group):
+    w = W.seirs_env(N=2000 + 7, T=40, n_events=20_000, R=2, y_source=W.Y_MIDPOINT)
+    _same(w, _run(w, warp=warp, group=group))
+
+
+@pytest.mark.parametrize("freq", [True, False])
+def test_group_method_sir_runs_out_of_transitions(freq):
+    w = W.sir_general(N=900 + 2, T=40, n_events=3000, R=1, freq=freq, beta=0.6 if freq else 0.01)
+    _same(w, _run(w, warp=1 << 30, group=0))
+
+
+@pytest.mark.parametrize("warp,group", [(0, 0), (1 << 30, 0), (-1, -1)])
+def test_erlang_eleven_transitions_bitexact(warp, group):
     w = W.erlang_sis(N=1500 + 3, T=40, n_events=8000, R=2)
     w.rates[1] *= 1.5
-    ref = _same(w, _run(w, warp=warp))
+    ref = _same(w, _run(w, warp=warp, group=group))
     assert ref.counters[:, 0].min() > 1_000_000
 
 
@@ -188,8 +203,8 @@ def test_events_past_the_horizon_are_never_reached():
     assert np.array_equal(counts, ref.counts) and np.array_equal(y, ref.y)
 
 
-@pytest.mark.parametrize("warp", [0, 1 << 30])
-def test_largest_model_bitexact(warp):
+@pytest.mark.parametrize("warp,group", [(0, 0), (1 << 30, 0), (1 << 30, 1 << 30)])
+def test_largest_model_bitexact(warp, group):
     # 16 compartments and 32 transitions (the limits): a ring C_i -> C_(i+1) at
     # k C_i and C_i -> C_(i+2) at k' C_i C_(i+1) / N, four continuous variables;
     # the stochastic step then needs more than 48 KB of shared memory per block
@@ -212,5 +227,5 @@ def test_largest_model_bitexact(warp):
     ev = W._general_events(rng, N, T, 3000, [(0.3, W.EXIT, [0, 1], [-1]), (0.2, W.ENTER, [1], [-1, 0]),
                                              (0.2, W.INTERNAL, [1], [0]), (0.3, W.EXTERNAL, [0, 1], [-1, 0])])
     w = W.GeneralWorkload("ring16", m, N, T, R, u0, y0, rates, vp, ev, 21)
-    ref = _same(w, _run(w, warp=warp))
+    ref = _same(w, _run(w, warp=warp, group=group))
     assert ref.counters[:, 0].min() > 10_000
