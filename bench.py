@@ -30,9 +30,14 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "node-days/sec and SSA events/sec (batched vs plain, bit-exact to oracle)"
-# FP64 pipe peak for the roofline: the nominal 1.25 TFLOP/s FP64 of GB300 counts an FMA
-# as two flops, so the pipe retires 6.25e11 FP64 instruction-lanes per second.
-FP64_PEAK_LANE_OPS = 6.25e11
+# FP64 pipe peak for the roofline, from unit counts and the clock: each SM sub-partition
+# (4 per SM) retires one 32-lane FP64 instruction per 64 cycles, so the GPU retires
+# SMs x 4 x 32 / 64 lanes per cycle (152 SMs at 2.07 GHz: 6.29e11 lane-ops/s, the
+# nominal 1.25 TFLOP/s FP64 with an FMA counted as two flops).
+FP64_LANES_PER_SM_CYCLE = 4 * 32 / 64
+# algorithmic HBM bytes of the stochastic step per node-day (SISe3: counts read and
+# written 24 + 24 B, phi read and written 8 + 8 B)
+SSA_BYTES_PER_NODE_DAY = {3: 64, 1: 32}
 # FP64 instruction-lanes the specification costs on the FP64 pipe (IEEE add / mul = 1,
 # IEEE divide = 7: its measured throughput is 1/7 of DFMA's on GB300), SISe3:
 #   per fired transition: 2 (P sums) + 7 (tau) + 1 (t + tau) + 1 (r) + 1 (threshold)
@@ -48,6 +53,14 @@ SSA_PROFILE = os.path.join(ROOT, "profiles", "k_node_day_dealt_national_day300.m
 # what the stochastic-step kernel and its launch shape are built from
 SSA_SOURCES = ("ssa.cu", "ssa_device.cuh", "devmath.cuh", "softdiv.cuh", "neglog_table.h", "internal.h",
                "host.cpp")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def kernel_sources_digest():
@@ -488,10 +501,20 @@ def main():
     fp64_ops = FP64_PER_TRANSITION[w.model] * transitions + FP64_PER_NODE_DAY[w.model] * N * T
     ssa_avg_s = ssa_ms / 1000 / max(ssa_n, 1)
     achieved = fp64_ops / ssa_n / ssa_avg_s if ssa_n else 0.0
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = sms * FP64_LANES_PER_SM_CYCLE * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    hbm_achieved = SSA_BYTES_PER_NODE_DAY[w.model] * N / ssa_avg_s / 1e9 if ssa_n else 0.0
     roofline = {"kernel": "k_node_day_dealt (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
-                "peak": FP64_PEAK_LANE_OPS / 1e9, "unit": "G FP64 lane-ops/s",
-                "frac": achieved / FP64_PEAK_LANE_OPS, "traffic": profiled_traffic(SSA_PROFILE),
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s / 2 (an FMA counts two flops)",
+                "peak": fp64_peak / 1e9, "unit": "G FP64 lane-ops/s",
+                "frac": achieved / fp64_peak, "traffic": profiled_traffic(SSA_PROFILE),
+                "peak_source": f"unit counts: {sms} SMs x 4 sub-partitions x one 32-lane FP64 instruction per 64 "
+                               f"cycles x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz (MEASURED_PEAKS sm_max_mhz); "
+                               "the nominal 1.25 TFLOP/s FP64 / 2",
+                "hbm": {"achieved": hbm_achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                        "frac": hbm_achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                        "bytes_per_launch": SSA_BYTES_PER_NODE_DAY[w.model] * N,
+                        "note": "algorithmic bytes; the state stays in L2 within a step"},
                 "kernel_share": {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k},
                 "avg_launch_us": {"ssa": 1000 * ssa_ms / max(ssa_n, 1), "events": 1000 * ev_ms / max(ev_n, 1)}}
 
