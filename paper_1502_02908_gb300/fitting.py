@@ -17,6 +17,9 @@ host-side driver: the super-parameters k_j = upsilon_j delta_j (Eq.
 Jeeves, J. ACM 8 (1961) 212-229).  Every evaluation of G reuses one simulation
 handle (new parameters, same events, same random streams: common random numbers,
 so G is a deterministic function of k).
+
+A gradient-based variant (PrevalenceGoal, gradient_descent) fits the daily
+national prevalence curve with the library's score-function gradient instead.
 """
 from __future__ import annotations
 
