@@ -55,6 +55,7 @@ __device__ __forceinline__ double phi_step(const SsaArgs& a, const DevParams& p,
   return next;
 }
 
+// Sum over the warp's lanes; the total lands in lane 0.
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -406,9 +407,17 @@ __device__ __forceinline__ uint64_t q62_of_f64(double x) {
   return sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
 }
 
+// Rounds of the binary32 clock whose choices a warp logs, so that a day end too
+// close to call resumes with the binary64 clock from that round instead of
+// rerunning the node-day.
+constexpr int kReplayRounds = 128;
+
+// Returns the transitions fired, or -1.  kb0, tq0, fired0: resume at draw kb0
+// (a multiple of 32) with the clock tq0 (Q62) and fired0 transitions behind.
 template <int NA, int CLOCK>
 __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_t seed, uint32_t rep, int v, int day,
-                                                     double phi, uint64_t margin, NodeState<NA>& s) {
+                                                     double phi, uint64_t margin, NodeState<NA>& s,
+                                                     uint32_t kb0 = 0, uint64_t tq0 = 0, int32_t fired0 = 0) {
   constexpr int NC = 2 * NA;
   const int lane = threadIdx.x & 31;
   const uint32_t full = 0xffffffffu;
@@ -424,9 +433,15 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
   for (int j = 0; j < NA; ++j) { cpos[j] = pos(cinf[j]); gpos[j] = pos(p.gam[j]); }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   double t = 0.0;
-  uint64_t tq = 0;
-  int32_t fired = 0;
-  for (uint32_t kb = 0;; kb += 32) {
+  uint64_t tq = tq0;
+  int32_t fired = fired0;
+  // binary32 clock: the day's start state and each continuing round's choice of
+  // this lane, for a resume with the binary64 clock
+  int32_t xday[NC];
+  uint8_t chlog[CLOCK == 2 ? kReplayRounds : 1];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) xday[c] = s.x[c];
+  for (uint32_t kb = kb0;; kb += 32) {
     if (CLOCK > 0 && kb >= kSpecMaxSteps) return -1;
     // 1. draws of this block
     const uint4 w = philox10(make_uint4((uint32_t)v, (uint32_t)day, kb + (uint32_t)lane, rep), k0, k1);
@@ -478,12 +493,49 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
         }
         if (e < 32) {
           const unsigned ok = __ballot_sync(full, !valid || sl >= kQ62One + margin);
-          if (!((ok >> e) & 1u)) return -1;         // too close to call
+          if (!((ok >> e) & 1u)) {                  // too close to call
+            const uint32_t rounds = kb >> 5;
+            if (rounds > (uint32_t)kReplayRounds) return -1;
+            // the binary64 clock's Q62 sum through the earlier rounds, from their
+            // logged choices (every one a continue), then that clock from here on
+            uint64_t tqx = 0;
+            int32_t xr[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) xr[c] = xday[c];
+            for (uint32_t r = 0; r < rounds; ++r) {
+              const uint4 wr = philox10(make_uint4((uint32_t)v, (uint32_t)day, (r << 5) + (uint32_t)lane, rep), k0, k1);
+              const double Er = neglog_u(((((uint64_t)wr.y) << 32) | wr.x) >> 12);
+              const int chr = chlog[r];
+              int32_t xsr[NC];
+              prefix_state<NA, 32>(xr, chr, lane, xsr);
+              double P = 0.0;
+#pragma unroll
+              for (int j = 0; j < NA; ++j) {
+                const double ainf = __dmul_rn(cinf[j], i2d_exact(xsr[2 * j]));
+                const double arec = __dmul_rn(p.gam[j], i2d_exact(xsr[2 * j + 1]));
+                const double A = __dadd_rn(ainf, arec);
+                P = (j == 0) ? A : __dadd_rn(P, A);
+              }
+              const double taur = div_pos(Er, P);
+              tqx += __shfl_sync(full, warp_sum(q62_of_f64(le_nonneg(taur, 1.5) ? taur : 1.5)), 0);
+              int32_t aft[NC];
+#pragma unroll
+              for (int j = 0; j < NA; ++j) {
+                const int dj = ((chr >> 1) == j) ? ((chr & 1) ? -1 : 1) : 0;
+                aft[2 * j] = xsr[2 * j] - dj;
+                aft[2 * j + 1] = xsr[2 * j + 1] + dj;
+              }
+#pragma unroll
+              for (int c = 0; c < NC; ++c) xr[c] = __shfl_sync(full, aft[c], 31);
+            }
+            return ssa_warp_node_day<NA, 1>(p, seed, rep, v, day, phi, 0, s, kb, tqx, fired);
+          }
 #pragma unroll
           for (int c = 0; c < NC; ++c) s.x[c] = __shfl_sync(full, xs[c], e);
           return fired + e;
         }
         tq = __shfl_sync(full, sl, 31);
+        if ((kb >> 5) < (uint32_t)kReplayRounds) chlog[kb >> 5] = (uint8_t)ch;
         break;
       }
       // the whole block continues: the state after lane 31's draw
