@@ -263,7 +263,8 @@ def general_leg(args, B, W, torch, oracle_check):
         w.T = min(args.days, w.T)
         thr, gthr = -1, -1
         if not args.no_tune:
-            (thr, gthr), _ = autotune.autotune_general(w, days=max(10, w.T // 8))
+            # a third of the horizon: the early days of an epidemic do not rank the thresholds
+            (thr, gthr), _ = autotune.autotune_general(w, days=max(10, w.T // 3))
         sim = B.GenSim.from_workload(w)
         sim.set_launch("graph")
         n_warp = sim.set_warp_threshold(thr)
