@@ -441,6 +441,13 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
   uint8_t chlog[CLOCK == 2 ? kReplayRounds : 1];
 #pragma unroll
   for (int c = 0; c < NC; ++c) xday[c] = s.x[c];
+  // more than two rounds a day expected at the start state (a0 > 64): the clock
+  // once per round (below)
+  bool dense = false;
+  if (CLOCK == 2) {
+    float T0[2 * NA - 1], a00;
+    dense = thresholds_f32<NA>(cpos, gpos, cinff, gamf, s.x, T0, a00) && a00 > 64.0f;
+  }
   for (uint32_t kb = kb0;; kb += 32) {
     if (CLOCK > 0 && kb >= kSpecMaxSteps) return -1;
     // 1. draws of this block
@@ -475,6 +482,12 @@ __device__ __forceinline__ int32_t ssa_warp_node_day(const DevParams& p, uint64_
         if (valid) {
           nc = choice_count_f32<NA>(T, __fmul_rn(a0f, u2f));
           if (nc < 0) nc = exact_choice<NA>(cinf, p, xs, u2);
+        }
+        // a dense node-day (many rounds) almost never ends inside a round: settle
+        // every lane's choice first and take the clock once
+        if (dense && it < 32 && __ballot_sync(full, nc != ch)) {
+          ch = nc;
+          continue;
         }
         uint64_t sc = valid ? q62_of(fminf(__fdividef(Ef, a0f), 1.5f)) : 0ull;
 #pragma unroll
