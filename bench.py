@@ -50,9 +50,8 @@ FP64_PER_NODE_DAY = {3: 34, 1: 24}
 SSA_PROFILE = os.path.join(ROOT, "profiles", "k_node_day_dealt_national_day300.md")
 
 
-# what the stochastic-step kernel and its launch shape are built from
-SSA_SOURCES = ("ssa.cu", "ssa_device.cuh", "devmath.cuh", "softdiv.cuh", "neglog_table.h", "internal.h",
-               "host.cpp")
+# the device sources the stochastic-step kernel is compiled from
+SSA_SOURCES = ("ssa.cu", "ssa_device.cuh", "devmath.cuh", "softdiv.cuh", "neglog_table.h", "internal.h")
 
 
 def measured_peaks():

@@ -96,6 +96,19 @@ typedef struct sim_handle sim_handle;
 sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,
                       const sim_params* params, sim_handle** out);
 
+/* As sim_create, with the live state in the caller's device memory (e.g. the
+ * storage of framework tensors): dev_counts int32 [R][Nc][N] and dev_phi double
+ * [R][N], 16-byte aligned, on the current device.  The call synchronises
+ * `stream` (so the caller's earlier work on the buffers is done), writes the
+ * initial state into them, and from then on every step reads and writes them in
+ * place; sim_state / sim_set_state still copy.  The library never frees them:
+ * they must stay allocated until sim_destroy.  Errors as sim_create, and
+ * SIM_E_INVALID_ARG for a buffer that is not aligned device memory of the
+ * current device. */
+sim_status sim_create_on(const sim_config* cfg, const int32_t* u0, const double* phi0,
+                         const sim_params* params, int32_t* dev_counts, double* dev_phi, void* stream,
+                         sim_handle** out);
+
 /* Loads the scheduled events (Sec. 3.2 Eq. (event)): n host int32 arrays in
  * input order.  kind: SIM_EXIT / SIM_ENTER / SIM_INTERNAL (aging: class cls to
  * cls+1 of the same node) / SIM_EXTERNAL (node -> dest).  cls: age class, or -1

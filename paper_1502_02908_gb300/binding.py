@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
         pi32, pi64, pd = P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double)
         sigs = {
             "sim_create": [P(SimConfig), pi32, pd, P(SimParams), P(vp)],
+            "sim_create_on": [P(SimConfig), pi32, pd, P(SimParams), vp, vp, vp, P(vp)],
             "sim_load_events": [vp, i64, pi32, pi32, pi32, pi32, pi32, pi32],
             "sim_run_days": [vp, i32, vp],
             "sim_sync": [vp, vp],
@@ -186,11 +187,13 @@ def schedule_events(events: W.Events, n_nodes: int, model: int, max_days: int):
 
 
 class Sim:
-    """One simulation handle: R replicates of one model on N nodes."""
+    """One simulation handle: R replicates of one model on N nodes.  With
+    ``state=(counts, phi)`` (device tensors int32 [R, Nc, N] and float64 [R, N],
+    contiguous) the live state is those tensors' storage (sim_create_on)."""
 
     def __init__(self, model, u0, phi0, params: W.Params, max_days, seed=1,
                  underflow_error=False, phi_pre_event=False, score=False, replicate_base=0,
-                 score_reverse=False):
+                 score_reverse=False, state=None):
         self.L = load_library()
         u0 = np.ascontiguousarray(u0, np.int32)
         self.nc, self.N = u0.shape
@@ -206,8 +209,23 @@ class Sim:
         sp = SimParams(*[_p(a, ctypes.c_double) for a in self._keep])
         h = ctypes.c_void_p()
         phi0 = np.ascontiguousarray(phi0, np.float64)
-        _check(self.L, None, self.L.sim_create(ctypes.byref(cfg), _p(u0, ctypes.c_int32), _p(phi0, ctypes.c_double),
-                                               ctypes.byref(sp), ctypes.byref(h)))
+        if state is None:
+            _check(self.L, None, self.L.sim_create(ctypes.byref(cfg), _p(u0, ctypes.c_int32),
+                                                   _p(phi0, ctypes.c_double), ctypes.byref(sp), ctypes.byref(h)))
+        else:
+            counts_t, phi_t = state
+            if tuple(counts_t.shape) != (self.R, self.nc, self.N) or tuple(phi_t.shape) != (self.R, self.N) or \
+                    not counts_t.is_contiguous() or not phi_t.is_contiguous():
+                raise ValueError("state tensors must be contiguous [R, Nc, N] int32 and [R, N] float64")
+            import torch
+            if counts_t.dtype != torch.int32 or phi_t.dtype != torch.float64:
+                raise ValueError("state tensors must be int32 and float64")
+            self._state = state                      # keep the storage alive with the handle
+            _check(self.L, None, self.L.sim_create_on(ctypes.byref(cfg), _p(u0, ctypes.c_int32),
+                                                      _p(phi0, ctypes.c_double), ctypes.byref(sp),
+                                                      ctypes.c_void_p(counts_t.data_ptr()),
+                                                      ctypes.c_void_p(phi_t.data_ptr()), current_stream(),
+                                                      ctypes.byref(h)))
         self.h = h
 
     @classmethod

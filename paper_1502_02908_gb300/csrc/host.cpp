@@ -20,6 +20,7 @@ using namespace episim;
 
 struct sim_handle {
   sim_config cfg{};
+  bool owns_state = true;           // false: counts and phi are the caller's device buffers (sim_create_on)
   int n_age = 1, nc = 2;
   std::vector<int32_t> u0;          // [Nc][N]
   std::vector<double> phi0;         // [N]
@@ -192,7 +193,8 @@ void free_all(sim_handle* h) {
   h->side = nullptr; h->ev_fork = h->ev_join = nullptr;
   free_profile(h);
   free_events(h);
-  cudaFree(h->d_counts); cudaFree(h->d_phi); cudaFree(h->d_params); cudaFree(h->d_prev_i);
+  if (h->owns_state) { cudaFree(h->d_counts); cudaFree(h->d_phi); }
+  cudaFree(h->d_params); cudaFree(h->d_prev_i);
   cudaFree(h->d_prev_n); cudaFree(h->d_ctr); cudaFree(h->d_err); cudaFree(h->d_score);
   cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0); cudaFree(h->d_order);
   cudaFree(h->d_traj); cudaFree(h->d_per_rep); cudaFree(h->d_moments); cudaFree(h->d_days);
@@ -768,8 +770,43 @@ sim_status handle_cuda_fail(sim_handle* h, cudaError_t e, const char* what) { re
 
 extern "C" {
 
+namespace {
+
+// Caller device memory for the state: on the current device, 16-byte aligned.
+bool usable_device_buffer(const void* ptr) {
+  if (!ptr || ((uintptr_t)ptr & 15u)) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+sim_status create_impl(const sim_config* cfg, const int32_t* u0, const double* phi0, const sim_params* p,
+                       int32_t* dev_counts, double* dev_phi, sim_handle** out);
+
+}  // namespace
+
 sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,
                       const sim_params* p, sim_handle** out) {
+  return create_impl(cfg, u0, phi0, p, nullptr, nullptr, out);
+}
+
+sim_status sim_create_on(const sim_config* cfg, const int32_t* u0, const double* phi0, const sim_params* p,
+                         int32_t* dev_counts, double* dev_phi, void* stream, sim_handle** out) {
+  if (!dev_counts || !dev_phi) return fail(nullptr, SIM_E_INVALID_ARG, "dev_counts and dev_phi are required");
+  if (!usable_device_buffer(dev_counts) || !usable_device_buffer(dev_phi))
+    return fail(nullptr, SIM_E_INVALID_ARG, "dev_counts / dev_phi must be 16-byte aligned device memory of the current device");
+  // the caller's earlier work on its buffers completes before the library writes them
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronize");
+  return create_impl(cfg, u0, phi0, p, dev_counts, dev_phi, out);
+}
+
+namespace {
+
+sim_status create_impl(const sim_config* cfg, const int32_t* u0, const double* phi0, const sim_params* p,
+                       int32_t* dev_counts, double* dev_phi, sim_handle** out) {
   if (!cfg || !u0 || !phi0 || !p || !out) return fail(nullptr, SIM_E_INVALID_ARG, "null argument");
   if (cfg->model != SIM_SISE && cfg->model != SIM_SISE3)
     return fail(nullptr, SIM_E_INVALID_ARG, "model must be SIM_SISE (1) or SIM_SISE3 (3)");
@@ -819,8 +856,14 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
     h->sm_count = sms > 0 ? sms : 1;
   }
   const size_t stats = (size_t)R * (cfg->max_days > 0 ? cfg->max_days : 1);
-  if (e == cudaSuccess) e = dalloc(&h->d_counts, n_counts(h));
-  if (e == cudaSuccess) e = dalloc(&h->d_phi, n_phi(h));
+  if (dev_counts) {
+    h->owns_state = false;
+    h->d_counts = dev_counts;
+    h->d_phi = dev_phi;
+  } else {
+    if (e == cudaSuccess) e = dalloc(&h->d_counts, n_counts(h));
+    if (e == cudaSuccess) e = dalloc(&h->d_phi, n_phi(h));
+  }
   if (e == cudaSuccess) e = dalloc(&h->d_params, (size_t)R);
   if (e == cudaSuccess) e = dalloc(&h->d_prev_i, stats);
   if (e == cudaSuccess) e = dalloc(&h->d_prev_n, stats);
@@ -855,6 +898,8 @@ sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* ph
   *out = h;
   return SIM_OK;
 }
+
+}  // namespace
 
 sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const int32_t* kind,
                            const int32_t* node, const int32_t* dest, const int32_t* count,

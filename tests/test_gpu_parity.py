@@ -358,3 +358,31 @@ def test_synthetic_benchmark_bitexact(warp, group):
     assert np.all(phi == 1.0)
     assert np.array_equal(ctr, ref.counters) and np.array_equal(pi, ref.prev_i)
     assert ctr[0, 0] > 64 * 12 * 500                  # SSA-dense
+
+
+def test_state_in_caller_tensors_bitexact():
+    # sim_create_on: the live counts and phi are the caller's tensors, updated in place;
+    # they outlive the handle
+    import torch
+    w = W.sise3_national(N=2000, T=30, n_events=20_000, R=2)
+    counts_t = torch.empty((w.R, w.nc, w.N), dtype=torch.int32, device="cuda")
+    phi_t = torch.empty((w.R, w.N), dtype=torch.float64, device="cuda")
+    s = B.Sim.from_workload(w, state=(counts_t, phi_t))
+    s.run(w.T)
+    s.sync()
+    counts, phi, _ = s.state()
+    s.close()
+    torch.cuda.synchronize()
+    ref = oracle.run(w)
+    assert np.array_equal(counts_t.cpu().numpy(), ref.counts) and np.array_equal(counts, ref.counts)
+    np.testing.assert_allclose(phi_t.cpu().numpy(), ref.phi, rtol=1e-12, atol=0)
+    counts_t += 1                                   # still the caller's memory after sim_destroy
+    assert int(counts_t.sum().item()) == int(ref.counts.sum()) + counts_t.numel()
+
+
+def test_state_in_caller_tensors_rejects_host_memory():
+    import torch
+    w = W.sise_plain(N=64, T=5, n_events=0)
+    with pytest.raises((B.SimError, ValueError)):
+        B.Sim.from_workload(w, state=(torch.empty((1, 2, 64), dtype=torch.int32),
+                                      torch.empty((1, 64), dtype=torch.float64)))
