@@ -111,3 +111,26 @@ def test_autotuner_keeps_results_and_picks_a_setting():
     best, table = autotune.autotune(w, days=20, thresholds=(1 << 30, 200), repeats=1, groups=(1 << 30, 100))
     assert len(table) == 12 and best["launch"] in autotune.LAUNCH_MODES
     assert best["group_threshold"] in (1 << 30, 100)
+
+
+def test_batch_and_graph_on_caller_tensors():
+    # handles whose state lives in caller tensors (sim_create_on): the persistent
+    # batch kernel and the CUDA-graph day loop update the tensors in place
+    import torch
+    ws = W.uneven_batch(n_inst=5, N_lo=100, N_hi=2000, T_lo=20, T_hi=70, seed=11)
+    tensors = [(torch.zeros((w.R, w.nc, w.N), dtype=torch.int32, device="cuda"),
+                torch.zeros((w.R, w.N), dtype=torch.float64, device="cuda")) for w in ws]
+    sims = [B.Sim.from_workload(w, state=t) for w, t in zip(ws, tensors)]
+    B.run_batch(sims[:3])
+    for s, w in zip(sims[3:], ws[3:]):
+        s.set_launch("graph")
+        s.run(w.T // 2)
+        s.run(w.T - w.T // 2)
+    for s in sims:
+        s.sync()
+    torch.cuda.synchronize()
+    for w, (ct, pt), s in zip(ws, tensors, sims):
+        ref = oracle.run(w)
+        assert np.array_equal(ct.cpu().numpy(), ref.counts), w.name
+        np.testing.assert_allclose(pt.cpu().numpy(), ref.phi, rtol=1e-12, atol=0)
+        s.close()
