@@ -114,7 +114,8 @@ typedef struct gen_handle gen_handle;
 sim_status gen_model_check(const gen_model* m, uint32_t* dep);
 
 /* Creates a simulation at day 0 on the current device.
- *   u0: host int32 [n_comp][N] initial counts (>= 0), the same for every replicate;
+ *   u0: host int32 [n_comp][N] initial counts (>= 0, at most 2^30 animals a node),
+ *       the same for every replicate;
  *   y0: host double [n_cont][N] initial continuous variables (finite, >= 0);
  *   rates: host double [R][n_trans] rate constants k_j (finite, >= 0);
  *   var_params: host double [R][n_cont][6] = {alpha, beta[4], epsilon} per

@@ -254,6 +254,11 @@ sim_status gen_create(const gen_model* m, const gen_config* cfg, const int32_t* 
     return gfail(nullptr, SIM_E_INVALID_ARG, "state too large");
   for (int64_t i = 0; i < (int64_t)nc * N; ++i)
     if (u0[i] < 0) return gfail(nullptr, SIM_E_INVALID_ARG, "u0[%lld] < 0", (long long)i);
+  for (int v = 0; v < N; ++v) {
+    int64_t tot = 0;
+    for (int c = 0; c < nc; ++c) tot += u0[(size_t)c * N + v];
+    if (tot > (1 << 30)) return gfail(nullptr, SIM_E_INVALID_ARG, "node %d holds more than 2^30 animals", v);
+  }
   for (int64_t i = 0; i < (int64_t)ny * N; ++i)
     if (!finite_nonneg(y0[i])) return gfail(nullptr, SIM_E_INVALID_ARG, "y0[%lld] must be finite and >= 0", (long long)i);
   std::vector<GenRepParams> params((size_t)R);

@@ -79,3 +79,27 @@ def test_model_limits():
     too_many = W.general_model(("A", "B"), [dict(change={"A": -1, "B": 1}, a="A")] * 33)
     with pytest.raises(B.SimError):
         B.gen_dependency(too_many)
+
+
+def _create(w, **over):
+    """gen_create with one argument replaced; its validation runs before any device call."""
+    kw = dict(u0=w.u0, y0=w.y0, rates=w.rates, var_params=w.var_params)
+    kw.update(over)
+    return B.GenSim(w.model, kw["u0"], kw["y0"], kw["rates"], kw["var_params"], w.T, seed=w.seed)
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("u0", lambda w: np.where(np.arange(w.u0.size).reshape(w.u0.shape) == 5, -1, w.u0), "u0["),
+    ("u0", lambda w: np.where(np.arange(w.u0.size).reshape(w.u0.shape) == 0, (1 << 30) + 1, w.u0), "2^30"),
+    ("y0", lambda w: np.where(np.arange(w.y0.size).reshape(w.y0.shape) == 3, -0.5, w.y0), "y0["),
+    ("rates", lambda w: w.rates * np.array([1.0, 1.0, -1.0, 1.0, 1.0, 1.0]), "rate["),
+    ("var_params", lambda w: np.concatenate([w.var_params[..., :1], np.full(w.var_params[..., 1:5].shape, 1.5),
+                                             w.var_params[..., 5:]], -1), "beta"),
+    ("var_params", lambda w: np.concatenate([np.full(w.var_params[..., :1].shape, np.nan), w.var_params[..., 1:]], -1),
+     "alpha"),
+])
+def test_create_rejects_bad_arguments(field, value, msg):
+    w = W.seirs_env(N=40, T=5, n_events=0, R=1)
+    with pytest.raises(B.SimError) as e:
+        _create(w, **{field: value(w)})
+    assert e.value.status == B.SIM_E_INVALID_ARG and msg in str(e.value)
