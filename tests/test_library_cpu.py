@@ -133,3 +133,37 @@ def test_integer_pipe_division_matches_ieee_on_host():
     out = np.empty(n); ref = np.empty(n)
     B.debug_div(x.ctypes.data, y.ctypes.data, out.ctypes.data, ref.ctypes.data, n, device=False)
     assert np.array_equal(out.view(np.uint64), (x / y).view(np.uint64))
+
+
+@pytest.mark.parametrize("change,msg", [
+    (lambda w: setattr(w, "u0", np.where(np.arange(w.u0.size).reshape(w.u0.shape) == 7, -2, w.u0)), "u0["),
+    (lambda w: setattr(w, "u0", np.where(np.arange(w.u0.size).reshape(w.u0.shape) == 1, (1 << 30) + 5, w.u0)),
+     "2^30"),
+    (lambda w: setattr(w, "phi0", np.where(np.arange(w.N) == 3, np.inf, w.phi0)), "phi0["),
+    (lambda w: w.params.beta.__setitem__((0, 2), 1.5), "parameters"),
+    (lambda w: w.params.gamma.__setitem__((0, 0), -0.1), "parameters"),
+    (lambda w: setattr(w, "model", 2), "model"),
+])
+def test_create_rejects_bad_arguments(change, msg):
+    # sim_create validates every argument before it touches a device
+    w = W.sise_plain(N=30, T=5, n_events=0)
+    change(w)
+    with pytest.raises(B.SimError) as ei:
+        B.Sim.from_workload(w)
+    assert ei.value.status == B.SIM_E_INVALID_ARG and msg in str(ei.value)
+
+
+def test_create_rejects_unknown_flags_and_reserved():
+    import ctypes
+    L = B.load_library()
+    w = W.sise_plain(N=10, T=5, n_events=0)
+    keep = [np.ascontiguousarray(x, np.float64) for x in (w.params.upsilon, w.params.gamma, w.params.alpha,
+                                                          w.params.beta, w.params.epsilon)]
+    sp = B.SimParams(*[x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for x in keep])
+    u0 = np.ascontiguousarray(w.u0, np.int32); phi0 = np.ascontiguousarray(w.phi0, np.float64)
+    for flags, reserved in ((1 << 7, 0), (0, 3)):
+        cfg = B.SimConfig(W.SISE, w.N, 1, w.T, 0, flags, 1, 0, reserved)
+        h = ctypes.c_void_p()
+        st = L.sim_create(ctypes.byref(cfg), u0.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                          phi0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(sp), ctypes.byref(h))
+        assert st == B.SIM_E_INVALID_ARG and not h.value
