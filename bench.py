@@ -392,8 +392,9 @@ def run_reference(args, dist, rank, ws):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
-            "config": {"workload": "SISe3 national, 37,000 herds, 3M events; each step the first 73 of 1,460 days",
-                       "replicates": 1},
+            "config": {"workload": f"SISe3 national: {w.N} herds x {w.T} days, {len(w.events)} events, "
+                                   "1 replicate per GPU (plain)",
+                       "replicates_per_gpu": 1, "parallelism": f"replicas x{args.gpus}"},
             "cpu_baseline": {"value": value, "unit": "node-days/s", "cores": 1, "kind": "oracle",
                              "sample": "first 73 of 1,460 days of the national SISe3 workload per step"},
             "e2e": {"value": value, "unit": "node-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
