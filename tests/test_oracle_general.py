@@ -266,6 +266,14 @@ MUTATIONS = [
     ("sampling slot off by one",
      "if (slot < have) got = c; else slot -= have;", "if (slot <= have) got = c; else slot -= have;",
      [test_exit_draw_from_noncontiguous_mask_is_hypergeometric]),
+    ("midpoint denominator uses the end-of-day state only",
+     "D = 0.5 * (D0[(int64_t)q * N + v] + D);", "D = D;",
+     [lambda: test_midpoint_hand_example(W.Y_MIDPOINT, 3 / 11)]),
+    ("a0 is the last rate, not the sum",
+     "for (int j = 0; j < nt; ++j) a0 = a0 + a[j];", "for (int j = 0; j < nt; ++j) a0 = a[j];",
+     [lambda: test_sir_ten_animals_matches_generator(True, 1.2)]),
+    ("stopping rule ignores elapsed time",
+     "if (t + tau >= 1.0) break;", "if (tau >= 1.0) break;", [test_sir_pure_recovery_binomial]),
     ("transfer lands in the source node",
      "else if (kind == GO_EXTERNAL) GX(got + off[got], dest) += 1;",
      "else if (kind == GO_EXTERNAL) GX(got + off[got], node) += 1;", [test_event_bookkeeping_by_hand]),
