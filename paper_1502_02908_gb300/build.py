@@ -50,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> pathlib.Path:
                 print(res.stdout + res.stderr)
     if force or jobs or _stale(LIB, objs):
         tmp = BUILD / f"libepisim.{os.getpid()}.so"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", str(tmp)] + [str(o) for o in objs]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", str(tmp)] + [str(o) for o in objs] + ["-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed: " + res.stdout + res.stderr)

@@ -382,19 +382,20 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
   }
   // per day: components of the graph whose edges are the day's transfers
   std::vector<int32_t> parent((size_t)N, -1), comp_ev, comp_off;
-  comp_ev.reserve((size_t)n);
-  comp_off.reserve((size_t)n + 1);
-  std::vector<int32_t> touched, root_comp((size_t)N, -1);
+  comp_ev.reserve((size_t)nk);
+  comp_off.reserve((size_t)nk + 1);
+  std::vector<int32_t> touched, root_comp((size_t)N, -1), roots, comp_of, csize, idx, cpos;
   auto find = [&](int32_t v) {
     while (parent[v] != v) { parent[v] = parent[parent[v]]; v = parent[v]; }
     return v;
   };
   for (int d = 0; d < T; ++d) {
     h->day_comp[d] = (int32_t)comp_off.size();
-    if (first[d + 1] == first[d]) continue;
+    const int64_t s0 = first[d], s1 = first[d + 1];
+    if (s1 == s0) continue;
     touched.clear();
     auto touch = [&](int32_t v) { if (parent[v] < 0) { parent[v] = v; touched.push_back(v); } };
-    for (int64_t s = first[d]; s < first[d + 1]; ++s) {
+    for (int64_t s = s0; s < s1; ++s) {
       touch(rec[s].x);
       if (rec[s].y >= 0) {
         touch(rec[s].y);
@@ -402,21 +403,29 @@ sim_status gen_load_events(gen_handle* h, int64_t n, const int32_t* day, const i
         if (a != b) parent[std::max(a, b)] = std::min(a, b);
       }
     }
-    // components with their events in input order, heaviest first
-    std::vector<int32_t> roots;
-    std::vector<std::vector<int32_t>> lists;
-    for (int64_t s = first[d]; s < first[d + 1]; ++s) {
+    // components numbered by their first event, placed heaviest first (ties in
+    // that numbering), each with its events in input order
+    roots.clear();
+    csize.clear();
+    comp_of.resize((size_t)(s1 - s0));
+    for (int64_t s = s0; s < s1; ++s) {
       const int32_t rt = find(rec[s].x);
-      if (root_comp[rt] < 0) { root_comp[rt] = (int32_t)lists.size(); lists.emplace_back(); roots.push_back(rt); }
-      lists[root_comp[rt]].push_back((int32_t)s);
+      if (root_comp[rt] < 0) { root_comp[rt] = (int32_t)csize.size(); csize.push_back(0); roots.push_back(rt); }
+      comp_of[(size_t)(s - s0)] = root_comp[rt];
+      csize[(size_t)root_comp[rt]]++;
     }
-    std::vector<int32_t> idx(lists.size());
+    const int32_t ncomp = (int32_t)csize.size();
+    idx.resize((size_t)ncomp);
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return lists[a].size() > lists[b].size(); });
-    for (int32_t c : idx) {
-      comp_off.push_back((int32_t)comp_ev.size());
-      comp_ev.insert(comp_ev.end(), lists[c].begin(), lists[c].end());
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return csize[(size_t)a] > csize[(size_t)b]; });
+    cpos.resize((size_t)ncomp);
+    for (int32_t q = 0, at = (int32_t)comp_ev.size(); q < ncomp; ++q) {
+      comp_off.push_back(at);
+      cpos[(size_t)idx[(size_t)q]] = at;
+      at += csize[(size_t)idx[(size_t)q]];
     }
+    comp_ev.resize(comp_ev.size() + (size_t)(s1 - s0));
+    for (int64_t s = s0; s < s1; ++s) comp_ev[(size_t)cpos[(size_t)comp_of[(size_t)(s - s0)]]++] = (int32_t)s;
     for (int32_t v : touched) parent[v] = -1;
     for (int32_t rt : roots) root_comp[rt] = -1;
   }

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace episim;
@@ -389,6 +390,36 @@ struct Schedule {
   std::vector<int32_t> level;
 };
 
+// Scratch of build_owner_form, kept across the days one thread schedules (its
+// vectors are re-filled each day, so the day loop allocates only while they grow).
+struct OwnerScratch {
+  std::vector<int32_t> par, comp_of, comp_ev, id, evcount, blk_of_comp, cs, blk_nt, local, blk_t0, adds, samps,
+      blk_n, comp_depth, comp_nodes, owner, comp_owner;
+  std::vector<int64_t> last_into, last_samp;
+  std::vector<std::pair<int64_t, int>> heapv;
+  std::vector<int4> rec, wt;
+  // per block, in CSR form: its nodes, components and events (ascending)
+  std::vector<int32_t> bn_off, bn, bc_off, bc, be_off, be, fillb;
+  // per block while it is built
+  std::vector<int32_t> units, ord, uowner, slot_of_thr, thr_ids, off, fill;
+  std::vector<int64_t> uev, load;
+  std::vector<std::pair<int64_t, int>> thr_heap;
+  std::vector<char> single;
+};
+
+// CSR of items 0..n-1 grouped by key_of(item) in [0, G), ascending items inside
+// a group (the order push_back in item order gives).
+template <class K>
+void group_csr(int n, int G, K key_of, std::vector<int32_t>& off, std::vector<int32_t>& items,
+               std::vector<int32_t>& fill) {
+  off.assign((size_t)G + 1, 0);
+  for (int i = 0; i < n; ++i) off[(size_t)key_of(i) + 1]++;
+  for (int g = 0; g < G; ++g) off[(size_t)g + 1] += off[(size_t)g];
+  items.resize((size_t)n);
+  fill.assign(off.begin(), off.end() - 1);
+  for (int i = 0; i < n; ++i) items[(size_t)fill[(size_t)key_of(i)]++] = i;
+}
+
 // Owner-computes form of one day (events at day-stable positions [s0, s1)).
 // The day's touched nodes fall into connected components of its transfer graph;
 // events of different components never touch a common node, so the components
@@ -405,13 +436,15 @@ struct Schedule {
 void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
                       const std::vector<int64_t>& by_pos, const int32_t* kind, const int32_t* node,
                       const int32_t* dest, const int32_t* count, const int32_t* cls,
-                      const std::vector<int32_t>& slot_of, const std::vector<int32_t>& lvl_of, int max_blocks) {
+                      const std::vector<int32_t>& slot_of, const std::vector<int32_t>& lvl_of, int max_blocks,
+                      OwnerScratch& W) {
   const int nt = (int)S.touched.size() - touch0;
   const int64_t n = s1 - s0;
   S.day_blk.push_back((int32_t)S.blk_meta.size());
   if (n == 0) return;
   // components (union-find over the day slots)
-  std::vector<int32_t> par((size_t)nt);
+  auto& par = W.par;
+  par.resize((size_t)nt);
   for (int i = 0; i < nt; ++i) par[(size_t)i] = i;
   auto find = [&](int x) {
     while (par[(size_t)x] != x) { par[(size_t)x] = par[(size_t)par[(size_t)x]]; x = par[(size_t)x]; }
@@ -423,16 +456,18 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
     const int a = find(slot_of[node[e]]), b = find(slot_of[dest[e]]);
     if (a != b) par[(size_t)(a < b ? b : a)] = a < b ? a : b;
   }
-  std::vector<int32_t> comp_of((size_t)nt), comp_ev;
-  {
-    std::vector<int32_t> id((size_t)nt, -1);
-    for (int i = 0; i < nt; ++i) {
-      const int r = find(i);
-      if (id[(size_t)r] < 0) { id[(size_t)r] = (int32_t)comp_ev.size(); comp_ev.push_back(0); }
-      comp_of[(size_t)i] = id[(size_t)r];
-    }
+  auto& comp_of = W.comp_of;
+  auto& comp_ev = W.comp_ev;
+  comp_of.resize((size_t)nt);
+  comp_ev.clear();
+  W.id.assign((size_t)nt, -1);
+  for (int i = 0; i < nt; ++i) {
+    const int r = find(i);
+    if (W.id[(size_t)r] < 0) { W.id[(size_t)r] = (int32_t)comp_ev.size(); comp_ev.push_back(0); }
+    comp_of[(size_t)i] = W.id[(size_t)r];
   }
-  std::vector<int32_t> evcount((size_t)nt, 0);
+  auto& evcount = W.evcount;
+  evcount.assign((size_t)nt, 0);
   for (int64_t s = s0; s < s1; ++s) {
     const int a = slot_of[node[by_pos[(size_t)s]]];
     evcount[(size_t)a]++;
@@ -441,12 +476,15 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
   const int ncomp = (int)comp_ev.size();
   const int G = std::max(1, std::min(max_blocks, ncomp));
   // components longest-first onto the least-loaded block
-  std::vector<int32_t> blk_of_comp((size_t)ncomp);
+  auto& blk_of_comp = W.blk_of_comp;
+  blk_of_comp.resize((size_t)ncomp);
   {
-    std::vector<int32_t> cs((size_t)ncomp);
+    auto& cs = W.cs;
+    cs.resize((size_t)ncomp);
     for (int c = 0; c < ncomp; ++c) cs[(size_t)c] = c;
     std::stable_sort(cs.begin(), cs.end(), [&](int a, int b) { return comp_ev[(size_t)a] > comp_ev[(size_t)b]; });
-    std::vector<std::pair<int64_t, int>> heapv;
+    auto& heapv = W.heapv;
+    heapv.clear();
     for (int b = 0; b < G; ++b) heapv.push_back({0, b});
     auto cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
       return a.first > b.first || (a.first == b.first && a.second > b.second);
@@ -460,12 +498,16 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
     }
   }
   // block-local slots, blocks in order, day slot order within a block
-  std::vector<int32_t> blk_nt((size_t)G, 0), local((size_t)nt);
+  auto& blk_nt = W.blk_nt;
+  auto& local = W.local;
+  blk_nt.assign((size_t)G, 0);
+  local.resize((size_t)nt);
   for (int i = 0; i < nt; ++i) {
     const int b = blk_of_comp[(size_t)comp_of[(size_t)i]];
     local[(size_t)i] = blk_nt[(size_t)b]++;
   }
-  std::vector<int32_t> blk_t0((size_t)G + 1, 0);
+  auto& blk_t0 = W.blk_t0;
+  blk_t0.assign((size_t)G + 1, 0);
   for (int b = 0; b < G; ++b) blk_t0[(size_t)b + 1] = blk_t0[(size_t)b] + blk_nt[(size_t)b];
   const size_t tbase = S.touched_df.size();
   S.touched_df.resize(tbase + (size_t)nt);
@@ -476,16 +518,26 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
   // wait counts in input order, and which events must publish: a sampling of v
   // when a transfer into v follows it, a transfer into w when a sampling of w
   // follows it (only those counters are ever waited on)
-  std::vector<int32_t> adds((size_t)nt, 0), samps((size_t)nt, 0);
-  std::vector<int64_t> last_into((size_t)nt, -1), last_samp((size_t)nt, -1);
+  auto& adds = W.adds;
+  auto& samps = W.samps;
+  adds.assign((size_t)nt, 0);
+  samps.assign((size_t)nt, 0);
+  auto& last_into = W.last_into;
+  auto& last_samp = W.last_samp;
+  last_into.assign((size_t)nt, -1);
+  last_samp.assign((size_t)nt, -1);
   for (int64_t s = s0; s < s1; ++s) {
     const int64_t e = by_pos[(size_t)s];
     const int k = kind[e];
     if (k != SIM_ENTER) last_samp[(size_t)slot_of[node[e]]] = s;
     if (k == SIM_EXTERNAL) last_into[(size_t)slot_of[dest[e]]] = s;
   }
-  std::vector<int4> rec((size_t)n), wt((size_t)n);
-  std::vector<int32_t> blk_n((size_t)G, 0);
+  auto& rec = W.rec;
+  auto& wt = W.wt;
+  rec.resize((size_t)n);
+  wt.resize((size_t)n);
+  auto& blk_n = W.blk_n;
+  blk_n.assign((size_t)G, 0);
   for (int64_t s = s0; s < s1; ++s) {
     const int64_t e = by_pos[(size_t)s];
     const int k = kind[e];
@@ -511,43 +563,59 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
   // as register-shaped days mostly give) is owned whole by one thread: its events
   // then need no wait and no publication at all.  A block holding a component
   // with much more parallelism inside gives each of its nodes a thread instead.
-  std::vector<int32_t> comp_depth((size_t)ncomp, 0), comp_nodes((size_t)ncomp, 0);
+  auto& comp_depth = W.comp_depth;
+  auto& comp_nodes = W.comp_nodes;
+  comp_depth.assign((size_t)ncomp, 0);
+  comp_nodes.assign((size_t)ncomp, 0);
   for (int64_t s = s0; s < s1; ++s) {
     const int c = comp_of[(size_t)slot_of[node[by_pos[(size_t)s]]]];
     comp_depth[(size_t)c] = std::max(comp_depth[(size_t)c], lvl_of[(size_t)s]);
   }
   for (int i = 0; i < nt; ++i) comp_nodes[(size_t)comp_of[(size_t)i]]++;
-  std::vector<std::vector<int32_t>> blk_nodes((size_t)G), blk_comps((size_t)G);
-  for (int i = 0; i < nt; ++i) blk_nodes[(size_t)blk_of_comp[(size_t)comp_of[(size_t)i]]].push_back(i);
-  for (int c = 0; c < ncomp; ++c) blk_comps[(size_t)blk_of_comp[(size_t)c]].push_back(c);
-  std::vector<int32_t> owner((size_t)nt, -1), comp_owner((size_t)ncomp, -1);
-  std::vector<std::vector<int32_t>> blk_evs((size_t)G);
-  for (int64_t s = s0; s < s1; ++s) {
-    const int a = slot_of[node[by_pos[(size_t)s]]];
-    blk_evs[(size_t)blk_of_comp[(size_t)comp_of[(size_t)a]]].push_back((int32_t)(s - s0));
-  }
+  group_csr(nt, G, [&](int i) { return blk_of_comp[(size_t)comp_of[(size_t)i]]; }, W.bn_off, W.bn, W.fillb);
+  group_csr(ncomp, G, [&](int c) { return blk_of_comp[(size_t)c]; }, W.bc_off, W.bc, W.fillb);
+  group_csr((int)n, G, [&](int i) { return blk_of_comp[(size_t)comp_of[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]]]; },
+            W.be_off, W.be, W.fillb);
+  auto& owner = W.owner;
+  auto& comp_owner = W.comp_owner;
+  owner.assign((size_t)nt, -1);
+  comp_owner.assign((size_t)ncomp, -1);
   const int warps = kDfThreads / 32;
   for (int b = 0; b < G; ++b) {
+    const int32_t* bnodes = W.bn.data() + W.bn_off[(size_t)b];
+    const int nbn = W.bn_off[(size_t)b + 1] - W.bn_off[(size_t)b];
+    const int32_t* bcomps = W.bc.data() + W.bc_off[(size_t)b];
+    const int nbc = W.bc_off[(size_t)b + 1] - W.bc_off[(size_t)b];
+    const int32_t* bevs = W.be.data() + W.be_off[(size_t)b];
+    const int nbe = W.be_off[(size_t)b + 1] - W.be_off[(size_t)b];
     bool whole = true;
-    for (int c : blk_comps[(size_t)b])
+    for (int q = 0; q < nbc; ++q) {
+      const int c = bcomps[q];
       if (comp_ev[(size_t)c] > 4 * comp_depth[(size_t)c] + 32) whole = false;
+    }
     // owner units: components (whole) or nodes, with their event counts and
     // whether all their events sample one node (register-resident chains)
-    std::vector<int32_t> units;
-    std::vector<int64_t> uev;
-    std::vector<char> single;
+    auto& units = W.units;
+    auto& uev = W.uev;
+    auto& single = W.single;
+    units.clear(); uev.clear(); single.clear();
     if (whole) {
-      for (int c : blk_comps[(size_t)b]) {
+      for (int q = 0; q < nbc; ++q) {
+        const int c = bcomps[q];
         units.push_back(c); uev.push_back(comp_ev[(size_t)c]); single.push_back(comp_nodes[(size_t)c] == 1);
       }
     } else {
-      for (int i : blk_nodes[(size_t)b])
+      for (int q = 0; q < nbn; ++q) {
+        const int i = bnodes[q];
         if (evcount[(size_t)i] > 0) { units.push_back(i); uev.push_back(evcount[(size_t)i]); single.push_back(1); }
+      }
     }
-    std::vector<int32_t> ord(units.size());
+    auto& ord = W.ord;
+    ord.resize(units.size());
     for (size_t k = 0; k < ord.size(); ++k) ord[k] = (int32_t)k;
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return uev[(size_t)x] > uev[(size_t)y]; });
-    std::vector<int32_t> uowner(units.size(), -1);
+    auto& uowner = W.uowner;
+    uowner.assign(units.size(), -1);
     const int64_t nb = blk_n[(size_t)b];
     int heavy = 0;
     const int64_t heavy_min = std::max<int64_t>(32, nb / 64);
@@ -560,46 +628,65 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
     // they last, heaviest first, so that units share no warp: their event kinds
     // would diverge); past 32 per warp, least-loaded threads
     const int wfree = warps - heavy;
-    std::vector<int64_t> load((size_t)kDfThreads, 0);
+    auto& load = W.load;
+    load.assign((size_t)kDfThreads, 0);
     for (int h = 0; h < heavy; ++h) load[(size_t)h * 32] = uev[(size_t)ord[(size_t)h]];
+    // (least loaded: smallest (load, thread), kept in a min-heap once reached)
+    auto& tq = W.thr_heap;
+    auto tq_cmp = [](const std::pair<int64_t, int>& a, const std::pair<int64_t, int>& b) {
+      return a.first > b.first || (a.first == b.first && a.second > b.second);
+    };
     for (size_t k = (size_t)heavy; k < ord.size(); ++k) {
       const int64_t kk = (int64_t)k - heavy;
       int t;
       if (kk < (int64_t)wfree * 32) {
         t = (heavy + (int)(kk % wfree)) * 32 + (int)(kk / wfree);
       } else {
-        t = heavy * 32;
-        for (int q = heavy * 32; q < kDfThreads; ++q) if (load[(size_t)q] < load[(size_t)t]) t = q;
+        if (kk == (int64_t)wfree * 32) {
+          tq.clear();
+          for (int q = heavy * 32; q < kDfThreads; ++q) tq.push_back({load[(size_t)q], q});
+          std::make_heap(tq.begin(), tq.end(), tq_cmp);
+        }
+        std::pop_heap(tq.begin(), tq.end(), tq_cmp);
+        t = tq.back().second;
+        tq.back().first += uev[(size_t)ord[k]];
+        std::push_heap(tq.begin(), tq.end(), tq_cmp);
       }
       uowner[(size_t)ord[k]] = t;
       load[(size_t)t] += uev[(size_t)ord[k]];
     }
     if (whole) {
       for (size_t k = 0; k < units.size(); ++k) comp_owner[(size_t)units[k]] = uowner[k];
-      for (int i : blk_nodes[(size_t)b]) owner[(size_t)i] = comp_owner[(size_t)comp_of[(size_t)i]];
+      for (int q = 0; q < nbn; ++q) owner[(size_t)bnodes[q]] = comp_owner[(size_t)comp_of[(size_t)bnodes[q]]];
     } else {
       for (size_t k = 0; k < units.size(); ++k) owner[(size_t)units[k]] = uowner[k];
     }
     if (whole)                                       // one thread per component: no waits
-      for (int32_t i : blk_evs[(size_t)b]) wt[(size_t)i] = make_int4(0, 0, 0, 0);
+      for (int q = 0; q < nbe; ++q) wt[(size_t)bevs[q]] = make_int4(0, 0, 0, 0);
     // owner threads in use, ascending; events grouped by them, input order within
-    std::vector<int32_t> slot_of_thr((size_t)kDfThreads, -1), thr_ids;
+    auto& slot_of_thr = W.slot_of_thr;
+    auto& thr_ids = W.thr_ids;
+    slot_of_thr.assign((size_t)kDfThreads, -1);
+    thr_ids.clear();
     for (int t = 0; t < kDfThreads; ++t)
       if (load[(size_t)t] > 0) { slot_of_thr[(size_t)t] = (int32_t)thr_ids.size(); thr_ids.push_back(t); }
     const int nslot = (int)thr_ids.size();
-    std::vector<int32_t> off((size_t)nslot + 1, 0);
+    auto& off = W.off;
+    off.assign((size_t)nslot + 1, 0);
     auto slot_of_ev = [&](int32_t i) {
       return slot_of_thr[(size_t)owner[(size_t)slot_of[node[by_pos[(size_t)(s0 + i)]]]]];
     };
-    for (int32_t i : blk_evs[(size_t)b]) off[(size_t)slot_of_ev(i) + 1]++;
+    for (int q = 0; q < nbe; ++q) off[(size_t)slot_of_ev(bevs[q]) + 1]++;
     for (int q = 0; q < nslot; ++q) off[(size_t)q + 1] += off[(size_t)q];
-    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    auto& fill = W.fill;
+    fill.assign(off.begin(), off.end() - 1);
     const size_t base = S.rec_df.size();
     S.blk_meta.push_back(make_int4((int32_t)base, (int32_t)(tbase + (size_t)blk_t0[(size_t)b]),
                                    (int32_t)S.thr_off.size(), heavy | (whole ? (1 << 16) : 0)));
     S.rec_df.resize(base + (size_t)nb);
     S.wait_df.resize(base + (size_t)nb);
-    for (int32_t i : blk_evs[(size_t)b]) {
+    for (int q = 0; q < nbe; ++q) {
+      const int32_t i = bevs[q];
       const int32_t at = fill[(size_t)slot_of_ev(i)]++;
       S.rec_df[base + (size_t)at] = rec[(size_t)i];
       S.wait_df[base + (size_t)at] = wt[(size_t)i];
@@ -607,6 +694,85 @@ void build_owner_form(Schedule& S, int64_t s0, int64_t s1, int32_t touch0,
     S.thr_off.insert(S.thr_off.end(), off.begin(), off.end());
     S.thr_id.insert(S.thr_id.end(), thr_ids.begin(), thr_ids.end());
     S.thr_id.push_back(-1);                          // aligned with thr_off
+  }
+}
+
+// Runs fn(0) .. fn(n - 1), fn(0) on the calling thread and the others on threads of
+// their own; false if a thread could not be started (those started are joined).
+template <class F>
+bool run_parallel(int n, F&& fn) {
+  std::vector<std::thread> pool;
+  bool ok = true;
+  try {
+    for (int p = 1; p < n; ++p) pool.emplace_back(fn, p);
+  } catch (...) { ok = false; }
+  if (ok && n > 0) fn(0);
+  for (auto& t : pool) t.join();
+  return ok;
+}
+
+// Schedules days [d0, d1): the execution-order records (rec, order, level,
+// rec_slot; at their final positions) into S, the rest into the partial schedule P
+// (day_lvl, day_touch and day_blk then hold one entry per day of the range, indices
+// into P's own arrays).
+void schedule_days(int32_t d0, int32_t d1, int N, const std::vector<int64_t>& first,
+                   const std::vector<int64_t>& by_pos, const int32_t* kind, const int32_t* node,
+                   const int32_t* dest, const int32_t* count, const int32_t* cls, int df_blocks,
+                   std::vector<int32_t>& lvl_of, Schedule& P, Schedule& S) {
+  std::vector<int32_t> slot_of(N, -1), slot_day(N, -1), last_s(N, 0), last_a(N, 0), stamp(N, -1);
+  std::vector<int64_t> bucket;
+  OwnerScratch scratch;
+  for (int32_t d = d0; d < d1; ++d) {
+    P.day_lvl.push_back((int32_t)P.lvl_start.size());
+    P.day_touch.push_back((int32_t)P.touched.size());
+    const int32_t touch0 = P.day_touch.back();
+    auto slot = [&](int v) {
+      if (slot_day[v] != d) { slot_day[v] = d; slot_of[v] = (int32_t)P.touched.size() - touch0; P.touched.push_back(v); }
+      return slot_of[v];
+    };
+    const int64_t s0 = first[(size_t)d], s1 = first[(size_t)d + 1];
+    int32_t max_lvl = 0;
+    auto touch = [&](int v) { if (stamp[v] != d) { stamp[v] = d; last_s[v] = 0; last_a[v] = 0; } };
+    for (int64_t s = s0; s < s1; ++s) {
+      const int64_t e = by_pos[(size_t)s];
+      const int k = kind[e], v = node[e];
+      touch(v);
+      int32_t L;
+      if (k == SIM_ENTER) {
+        L = last_s[v] + 1;
+        if (L > last_a[v]) last_a[v] = L;
+      } else {
+        L = (last_s[v] > last_a[v] ? last_s[v] : last_a[v]) + 1;
+        if (k == SIM_EXTERNAL) {
+          const int w = dest[e];
+          touch(w);
+          if (last_s[w] + 1 > L) L = last_s[w] + 1;
+          if (L > last_a[w]) last_a[w] = L;
+        }
+        last_s[v] = L;
+      }
+      lvl_of[(size_t)s] = L;
+      if (L > max_lvl) max_lvl = L;
+    }
+    bucket.assign((size_t)max_lvl + 2, 0);
+    for (int64_t s = s0; s < s1; ++s) bucket[(size_t)lvl_of[(size_t)s] + 1]++;
+    for (int32_t L = 0; L <= max_lvl; ++L) bucket[(size_t)L + 1] += bucket[(size_t)L];
+    for (int32_t L = 1; L <= max_lvl; ++L) P.lvl_start.push_back((int32_t)(s0 + bucket[(size_t)L]));
+    for (int64_t s = s0; s < s1; ++s) {
+      const int64_t e = by_pos[(size_t)s];
+      const size_t slot = (size_t)(s0 + bucket[(size_t)lvl_of[(size_t)s]]++);
+      const uint32_t packed = (uint32_t)kind[e] | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
+      S.rec[slot] = make_int4(node[e], kind[e] == SIM_EXTERNAL ? dest[e] : -1, (int32_t)s, (int32_t)packed);
+      S.order[slot] = s;
+      S.level[slot] = lvl_of[(size_t)s];
+    }
+    for (int64_t k = s0; k < s1; ++k) {          // slots in execution order
+      const int4 rc = S.rec[(size_t)k];
+      const int32_t a = slot(rc.x);
+      const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
+      S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
+    }
+    build_owner_form(P, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of, lvl_of, df_blocks, scratch);
   }
 }
 
@@ -639,12 +805,10 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     if (day[e] + 1 > dmax) dmax = day[e] + 1;
   }
   std::vector<int64_t> first, by_pos;
-  std::vector<int32_t> last_s, last_a, stamp, lvl_of;
-  std::vector<int64_t> bucket;
+  std::vector<int32_t> lvl_of;
   try {
     first.assign((size_t)dmax + 1, 0);
     by_pos.resize((size_t)n);
-    last_s.assign(N, 0); last_a.assign(N, 0); stamp.assign(N, -1);
     S.day_lvl.assign((size_t)T + 1, 0);
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
   for (int64_t e = 0; e < n; ++e) first[(size_t)day[e] + 1]++;
@@ -661,65 +825,77 @@ sim_status build_schedule(sim_handle* h, int N, int na, int32_t T, int64_t n, co
     S.level.resize((size_t)n_run);
     S.rec_slot.resize((size_t)n_run);
     S.day_touch.assign((size_t)T + 1, 0);
-    S.rec_df.reserve((size_t)n_run);
-    S.wait_df.reserve((size_t)n_run);
-    S.thr_off.reserve((size_t)n_run + (size_t)T);
-    S.touched_df.reserve((size_t)n_run);
-    S.day_blk.reserve((size_t)T + 1);
   } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
-  std::vector<int32_t> slot_of(N, -1), slot_day(N, -1);
-  for (int32_t d = 0; d < T; ++d) {
-    S.day_lvl[d] = (int32_t)S.lvl_start.size();
-    S.day_touch[d] = (int32_t)S.touched.size();
-    const int32_t touch0 = S.day_touch[d];
-    auto slot = [&](int v) {
-      if (slot_day[v] != d) { slot_day[v] = d; slot_of[v] = (int32_t)S.touched.size() - touch0; S.touched.push_back(v); }
-      return slot_of[v];
-    };
-    const int64_t s0 = first[(size_t)d], s1 = first[(size_t)d + 1];
-    int32_t max_lvl = 0;
-    auto touch = [&](int v) { if (stamp[v] != d) { stamp[v] = d; last_s[v] = 0; last_a[v] = 0; } };
-    for (int64_t s = s0; s < s1; ++s) {
-      const int64_t e = by_pos[(size_t)s];
-      const int k = kind[e], v = node[e];
-      touch(v);
-      int32_t L;
-      if (k == SIM_ENTER) {
-        L = last_s[v] + 1;
-        if (L > last_a[v]) last_a[v] = L;
-      } else {
-        L = (last_s[v] > last_a[v] ? last_s[v] : last_a[v]) + 1;
-        if (k == SIM_EXTERNAL) {
-          const int w = dest[e];
-          touch(w);
-          if (last_s[w] + 1 > L) L = last_s[w] + 1;
-          if (L > last_a[w]) last_a[w] = L;
-        }
-        last_s[v] = L;
-      }
-      lvl_of[(size_t)s] = L;
-      if (L > max_lvl) max_lvl = L;
-    }
-    bucket.assign((size_t)max_lvl + 2, 0);
-    for (int64_t s = s0; s < s1; ++s) bucket[(size_t)lvl_of[(size_t)s] + 1]++;
-    for (int32_t L = 0; L <= max_lvl; ++L) bucket[(size_t)L + 1] += bucket[(size_t)L];
-    for (int32_t L = 1; L <= max_lvl; ++L) S.lvl_start.push_back((int32_t)(s0 + bucket[(size_t)L]));
-    for (int64_t s = s0; s < s1; ++s) {
-      const int64_t e = by_pos[(size_t)s];
-      const size_t slot = (size_t)(s0 + bucket[(size_t)lvl_of[(size_t)s]]++);
-      const uint32_t packed = (uint32_t)kind[e] | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
-      S.rec[slot] = make_int4(node[e], kind[e] == SIM_EXTERNAL ? dest[e] : -1, (int32_t)s, (int32_t)packed);
-      S.order[slot] = s;
-      S.level[slot] = lvl_of[(size_t)s];
-    }
-    for (int64_t k = s0; k < s1; ++k) {          // slots in execution order
-      const int4 rc = S.rec[(size_t)k];
-      const int32_t a = slot(rc.x);
-      const int32_t b = rc.y >= 0 ? slot(rc.y) : -1;
-      S.rec_slot[(size_t)k] = make_int4(a, b, rc.z, rc.w);
-    }
-    build_owner_form(S, s0, s1, touch0, by_pos, kind, node, dest, count, cls, slot_of, lvl_of, df_blocks);
+  // Days are independent: contiguous ranges of them, balanced by event count, are
+  // scheduled on separate threads into partial schedules, which are then joined in
+  // day order (their indices into the joined arrays shifted).  The records in
+  // execution order go straight to their final positions.
+  const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const int n_part = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)hw, n_run / 65536 + 1, (int64_t)T}));
+  std::vector<int32_t> part_d(n_part + 1, T);
+  part_d[0] = 0;
+  for (int p = 1, d = 0; p < n_part; ++p) {
+    while (d < T && first[(size_t)d] < n_run * p / n_part) ++d;
+    part_d[p] = std::max(d, part_d[p - 1]);
   }
+  std::vector<Schedule> parts(n_part);
+  std::vector<char> part_oom(n_part, 0);
+  const bool threads_ok = run_parallel(n_part, [&](int p) {
+    try {
+      schedule_days(part_d[p], part_d[p + 1], N, first, by_pos, kind, node, dest, count, cls, df_blocks, lvl_of,
+                    parts[p], S);
+    } catch (...) { part_oom[p] = 1; }
+  });
+  if (!threads_ok) return fail(h, SIM_E_OOM, "host threads");
+  for (int p = 0; p < n_part; ++p)
+    if (part_oom[p]) return fail(h, SIM_E_OOM, "host allocation");
+  // the join: each part's arrays at the offsets of the parts before it
+  std::vector<size_t> o_lvl(n_part + 1, 0), o_tch(n_part + 1, 0), o_blk(n_part + 1, 0), o_rec(n_part + 1, 0),
+      o_tdf(n_part + 1, 0), o_thr(n_part + 1, 0);
+  for (int p = 0; p < n_part; ++p) {
+    const Schedule& P = parts[p];
+    o_lvl[p + 1] = o_lvl[p] + P.lvl_start.size();
+    o_tch[p + 1] = o_tch[p] + P.touched.size();
+    o_blk[p + 1] = o_blk[p] + P.blk_meta.size();
+    o_rec[p + 1] = o_rec[p] + P.rec_df.size();
+    o_tdf[p + 1] = o_tdf[p] + P.touched_df.size();
+    o_thr[p + 1] = o_thr[p] + P.thr_off.size();
+  }
+  if (o_tdf[n_part] >= ((size_t)1 << 31) || o_thr[n_part] >= ((size_t)1 << 31))
+    return fail(h, SIM_E_INVALID_ARG, "event schedule exceeds 32-bit indices");
+  try {
+    S.lvl_start.resize(o_lvl[n_part]);
+    S.touched.resize(o_tch[n_part]);
+    S.day_blk.resize((size_t)T);
+    S.blk_meta.resize(o_blk[n_part]);
+    S.rec_df.resize(o_rec[n_part]);
+    S.wait_df.resize(o_rec[n_part]);
+    S.touched_df.resize(o_tdf[n_part]);
+    S.thr_off.resize(o_thr[n_part]);
+    S.thr_id.resize(o_thr[n_part]);
+  } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  const bool join_ok = run_parallel(n_part, [&](int p) {
+    Schedule& P = parts[p];
+    for (int32_t d = part_d[p]; d < part_d[p + 1]; ++d) {
+      const size_t i = (size_t)(d - part_d[p]);
+      S.day_lvl[d] = P.day_lvl[i] + (int32_t)o_lvl[p];
+      S.day_touch[d] = P.day_touch[i] + (int32_t)o_tch[p];
+      S.day_blk[d] = P.day_blk[i] + (int32_t)o_blk[p];
+    }
+    std::copy(P.lvl_start.begin(), P.lvl_start.end(), S.lvl_start.begin() + o_lvl[p]);
+    std::copy(P.touched.begin(), P.touched.end(), S.touched.begin() + o_tch[p]);
+    std::copy(P.rec_df.begin(), P.rec_df.end(), S.rec_df.begin() + o_rec[p]);
+    std::copy(P.wait_df.begin(), P.wait_df.end(), S.wait_df.begin() + o_rec[p]);
+    std::copy(P.touched_df.begin(), P.touched_df.end(), S.touched_df.begin() + o_tdf[p]);
+    std::copy(P.thr_off.begin(), P.thr_off.end(), S.thr_off.begin() + o_thr[p]);
+    std::copy(P.thr_id.begin(), P.thr_id.end(), S.thr_id.begin() + o_thr[p]);
+    for (size_t b = 0; b < P.blk_meta.size(); ++b) {
+      const int4 m = P.blk_meta[b];
+      S.blk_meta[o_blk[p] + b] = make_int4(m.x + (int32_t)o_rec[p], m.y + (int32_t)o_tdf[p], m.z + (int32_t)o_thr[p], m.w);
+    }
+    P = Schedule();
+  });
+  if (!join_ok) return fail(h, SIM_E_OOM, "host threads");
   S.day_lvl[T] = (int32_t)S.lvl_start.size();
   S.day_touch[T] = (int32_t)S.touched.size();
   S.lvl_start.push_back((int32_t)n_run);

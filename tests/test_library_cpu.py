@@ -78,6 +78,25 @@ def test_schedule_levels_reproduce_input_order(model):
     assert np.array_equal(c2, seq.counts[0])
 
 
+def test_schedule_of_a_long_list_equals_its_days_scheduled_alone():
+    # days are scheduled independently (a long list in ranges of days on several
+    # threads, then joined): the whole list's schedule restricted to a day equals
+    # that day's events scheduled on their own, shifted to the day's first position
+    rng = np.random.default_rng(11)
+    N, T, n = 500, 40, 300_000
+    ev = _random_events(rng, N, T, n, W.SISE3)
+    order, level = B.schedule_events(ev, N, W.SISE3, T)
+    stable = np.argsort(ev.day, kind="stable")
+    first = np.searchsorted(ev.day[stable], np.arange(T + 1))
+    assert order.size == n
+    for d in range(T):
+        one = ev.select(stable[first[d]:first[d + 1]])
+        one.day[:] = 0
+        o1, l1 = B.schedule_events(one, N, W.SISE3, 1)
+        assert np.array_equal(order[first[d]:first[d + 1]], o1 + first[d])
+        assert np.array_equal(level[first[d]:first[d + 1]], l1)
+
+
 def test_schedule_level_depth_of_a_hub_chain():
     # five exits on one node in one day form a chain of five levels; enters on
     # another node share one level
