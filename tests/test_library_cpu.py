@@ -78,18 +78,25 @@ def test_schedule_levels_reproduce_input_order(model):
     assert np.array_equal(c2, seq.counts[0])
 
 
-def test_schedule_of_a_long_list_equals_its_days_scheduled_alone():
+# a long list over many days; all of it on the last of three days (empty day
+# ranges); on two days of fifty; all of it on one day
+@pytest.mark.parametrize("T,days", [(40, None), (3, [2]), (50, [7, 31]), (1, [0])])
+def test_schedule_of_a_long_list_equals_its_days_scheduled_alone(T, days):
     # days are scheduled independently (a long list in ranges of days on several
     # threads, then joined): the whole list's schedule restricted to a day equals
     # that day's events scheduled on their own, shifted to the day's first position
     rng = np.random.default_rng(11)
-    N, T, n = 500, 40, 300_000
+    N, n = 500, 300_000
     ev = _random_events(rng, N, T, n, W.SISE3)
+    if days is not None:
+        ev.day[:] = rng.choice(days, size=n)
     order, level = B.schedule_events(ev, N, W.SISE3, T)
     stable = np.argsort(ev.day, kind="stable")
     first = np.searchsorted(ev.day[stable], np.arange(T + 1))
     assert order.size == n
     for d in range(T):
+        if first[d + 1] == first[d]:
+            continue
         one = ev.select(stable[first[d]:first[d + 1]])
         one.day[:] = 0
         o1, l1 = B.schedule_events(one, N, W.SISE3, 1)
