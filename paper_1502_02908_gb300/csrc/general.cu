@@ -12,6 +12,8 @@
 #include "general.h"
 #include "softdiv.cuh"
 
+#include <algorithm>
+
 namespace episim {
 
 namespace {
@@ -222,6 +224,7 @@ __device__ __forceinline__ uint32_t gen_seg_node_day(const GenModelDev& m, const
 
 constexpr int kGenSeg = 8;                          // lanes per node of the group method
 constexpr int kGenWarps = kGenThreads / 32;
+constexpr int kGenEventWarps = 8192;                // event step: a warp per component up to this many
 
 __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   extern __shared__ int4 smem4[];
@@ -339,7 +342,10 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
 }
 
 // One thread per component of the day's transfer graph: its events in input
-// order (no other thread touches its nodes this day).  The counts of the node an
+// order (no other thread touches its nodes this day).  Components (largest first)
+// are dealt lane-major over the grid's warps: component i runs on lane i / W of
+// warp i mod W (W warps in all), so the largest W each have a warp to themselves
+// and no warp serialises several long divergent chains.  The counts of the node an
 // event samples from stay in a shared-memory row across consecutive events at
 // that node; transfers add to the destination in global memory (a destination is
 // never the node in the row, and the row is written back before another node is
@@ -350,7 +356,8 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_events(GenEvArgs a) {
   copy16(&m, a.model, (int)(sizeof(GenModelDev) / 16));
   __syncthreads();
   const int r = blockIdx.y, nc = m.nc, N = a.N;
-  const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = (int)gridDim.x * (int)(blockDim.x >> 5);
+  const int ci = (int)(threadIdx.x & 31) * W + (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
   int32_t* cc = cache + threadIdx.x;
   const int S = kGenThreads;
   uint32_t applied = 0, clamped = 0, skipped = 0;
@@ -485,7 +492,9 @@ cudaError_t launch_gen_ssa(GenSsaArgs a, int nt, int nc, cudaStream_t st) {
 
 cudaError_t launch_gen_events(const GenEvArgs& a, cudaStream_t st) {
   if (a.ncomp <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)((a.ncomp + kGenThreads - 1) / kGenThreads), (unsigned)a.R);
+  // a warp per component up to kGenEventWarps warps, then up to 32 per warp
+  const int warps = std::max((a.ncomp + 31) / 32, std::min(a.ncomp, kGenEventWarps));
+  const dim3 grid((unsigned)((warps + kGenWarps - 1) / kGenWarps), (unsigned)a.R);
   k_gen_events<<<grid, kGenThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
