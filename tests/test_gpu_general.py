@@ -118,6 +118,24 @@ def test_sise_general_matches_the_sise_kernels():
     assert np.array_equal(ctr, g_ctr)
 
 
+def test_many_components_share_warps_bitexact():
+    # about 20,000 components a day: past 8,192 warps the event step puts several
+    # components on the lanes of one warp (each still alone on its nodes)
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    w = W.sir_general(N=40_000, T=4, n_events=160_000, R=1)
+    ev = w.events
+    for d in range(w.T):
+        m = ev.day == d
+        tr = m & (ev.kind == W.EXTERNAL)
+        touched = np.unique(np.concatenate([ev.node[m], ev.dest[tr]]))
+        _, label = connected_components(coo_matrix((np.ones(tr.sum()), (ev.node[tr], ev.dest[tr])), shape=(w.N, w.N)),
+                                        directed=False)
+        assert len(np.unique(label[touched])) > 2 * 8192
+    ref = _same(w, _run(w))
+    assert ref.counters[0, 1] == len(ev)
+
+
 def test_graph_launch_and_split_runs_bitexact():
     w = W.seirs_env(N=1000, T=40, n_events=8000, R=1, y_source=W.Y_MIDPOINT)
     ref = oracle.run_general(w)
