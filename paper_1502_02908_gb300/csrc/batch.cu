@@ -97,7 +97,9 @@ __device__ __forceinline__ void dispatch_events(const BatchInst& I, int r, int d
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchCtl c) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_item;
-  __shared__ int s_go;
+  __shared__ int s_go;   // written by thread 0 only before the loop-top barrier
+  __shared__ int s_ok;   // the item's dependency wait succeeded (its own flag: s_go
+                         // may still be being read when the wait's result lands)
   for (;;) {
     if (threadIdx.x == 0) {
       s_item = (long long)atomicAdd(c.next, 1ull);
@@ -125,15 +127,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchCtl c) {
       }
       const BatchInst& I = c.inst[k];
       const int day = I.day0 + s;
-      if (threadIdx.x == 0) s_go = is_ssa ? wait_at_least(I.ev_done + r, (unsigned)day, c)
+      if (threadIdx.x == 0) s_ok = is_ssa ? wait_at_least(I.ev_done + r, (unsigned)day, c)
                                           : wait_at_least(I.ssa_done + r, (unsigned)((s + 1) * I.bpr), c);
       __syncthreads();
-      if (s_go) {
+      if (s_ok) {
         if (is_ssa) dispatch_chunk(I, r, chunk, day, s > 0, 0);
         else dispatch_events(I, r, day, smem, c.smem_cap);
       }
       __syncthreads();
-      if (threadIdx.x == 0 && s_go) {
+      if (threadIdx.x == 0 && s_ok) {
         __threadfence();
         if (is_ssa) atomicAdd(I.ssa_done + r, 1u);
         else atomicMax(I.ev_done + r, (unsigned)(day + 1));
@@ -145,9 +147,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchCtl c) {
       const long long w = local - c.cumF[k];
       const int r = (int)(w / I.tbpr), chunk = (int)(w - (long long)r * I.tbpr);
       const int last = I.day0 + I.ndays - 1;
-      if (threadIdx.x == 0) s_go = wait_at_least(I.ev_done + r, (unsigned)(last + 1), c);
+      if (threadIdx.x == 0) s_ok = wait_at_least(I.ev_done + r, (unsigned)(last + 1), c);
       __syncthreads();
-      if (s_go) dispatch_chunk(I, r, chunk, last, 1, 1);
+      if (s_ok) dispatch_chunk(I, r, chunk, last, 1, 1);
     }
     __syncthreads();
   }
