@@ -6,12 +6,12 @@
  * One simulated day, for every node (herd) and every replicate, is
  *   1. the stochastic step: Gillespie's direct method per node on [d, d+1)
  *      with the environmental variable phi frozen (Sec. 3.1 Eq. (numstep3);
- *      Sec. 3.3 Eqs. (sampling), (sampling2); Alg. 1 lines 3-10);
+ *      Sec. 3.3 Eqs. (sampling), (sampling2); the per-node loop of Alg. 1);
  *   2. the deterministic step: the day's scheduled events, applied so that the
- *      result equals their input order (Sec. 3.2 Eq. (event); Sec. 3.3; Alg. 1
- *      line 13);
+ *      result equals their input order (Sec. 3.2 Eq. (event); Sec. 3.3; the event
+ *      step of Alg. 1);
  *   3. the continuous-state update phi <- phi (1 - beta) + alpha I / N + epsilon
- *      (Eq. (numstep5) with Eq. (siminfpressure); Alg. 1 line 14).
+ *      (Eq. (numstep5) with Eq. (siminfpressure); the last step of Alg. 1's day).
  * Models: SISe (compartments S, I; S->I at upsilon phi S, I->S at gamma I) and
  * SISe3 (the same per age class; Sec. 4.1 Eqs. (vtectrans)-(recovery_rates)).
  *
@@ -89,10 +89,16 @@ typedef struct sim_params {
 
 typedef struct sim_handle sim_handle;
 
-/* Creates a simulation at day 0.  u0: host int32 [Nc][N] initial counts, the same
- * for every replicate (>= 0); phi0: host double [N]; params: see sim_params.
- * All inputs are copied.  Allocates the device state on the current device.
- * *out is set only on SIM_OK. */
+/* Creates a simulation at day 0: the initial discrete state X (the Nc x N
+ * integer state matrix of Sec. 2.2, Eq. (local)) and the continuous state Y = phi
+ * (one variable per node, Sec. 2.3 Eq. (master_det); Sec. 4.1 Eq.
+ * (siminfpressure)), with the rate constants of Sec. 4.1 Eqs. (vtectrans)-
+ * (recovery_rates) -- the initialisation that precedes Alg. 1's time loop.
+ * u0: host int32 [Nc][N] initial counts, the same for every replicate (>= 0);
+ * phi0: host double [N]; params: see sim_params.  All inputs are copied.
+ * Allocates the device state on the current device.  Errors: SIM_E_INVALID_ARG
+ * (a size, count or constant out of range, named in sim_last_error(NULL)),
+ * SIM_E_OOM, SIM_E_CUDA.  *out is set only on SIM_OK. */
 sim_status sim_create(const sim_config* cfg, const int32_t* u0, const double* phi0,
                       const sim_params* params, sim_handle** out);
 
@@ -122,31 +128,40 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
                            const int32_t* node, const int32_t* dest, const int32_t* count,
                            const int32_t* cls);
 
-/* Advances every replicate by ndays days (ndays >= 0, day + ndays <= max_days),
- * asynchronously on the CUDA stream `stream` (a cudaStream_t; NULL = legacy
- * default stream).  Returns launch errors at once.  Device-side conditions
+/* Advances every replicate by ndays days (ndays >= 0, day + ndays <= max_days):
+ * per day the stochastic step, the day's events and the phi update, i.e. ndays
+ * iterations of Alg. 1's time loop (Sec. 3.1 Eqs. (numstep3)-(numstep5), one
+ * day per step of Eq. (numerical)), asynchronously on the CUDA stream `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Returns launch errors at once.  Device-side conditions
  * (SIM_E_UNDERFLOW under the ERROR policy) are latched and returned by the next
  * synchronising call (sim_state, sim_stats, sim_score, sim_sync). */
 sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream);
 
-/* Waits for the handle's work on `stream` and returns any latched device error. */
+/* Waits for the handle's work on `stream` and returns any latched device error
+ * (the day boundary t_{n+1} of Alg. 1 made observable to the host). */
 sim_status sim_sync(sim_handle* h, void* stream);
 
-/* Copies the state at the start of the current day: counts int32 [R][Nc][N],
- * phi double [R][N] (either may be NULL), and *day.  where = SIM_HOST or
+/* Copies the state at the start of the current day -- X (Sec. 2.2 Eq. (local))
+ * and Y = phi (Sec. 2.3) after the previous day's events and phi update
+ * (Eqs. (numstep4), (numstep5)): counts int32 [R][Nc][N], phi double [R][N]
+ * (either may be NULL), and *day.  where = SIM_HOST or
  * SIM_DEVICE says what the output pointers are.  Synchronises `stream`. */
 sim_status sim_state(sim_handle* h, int32_t* counts, double* phi, int32_t* day, int32_t where,
                      void* stream);
 
-/* Replaces the state (checkpoint restore): counts [R][Nc][N] and phi [R][N] at
- * the start of day `day` (0 <= day <= max_days).  Runs resumed from a state
+/* Replaces the state (checkpoint restore): X and Y = phi (Secs. 2.2, 2.3) at the
+ * start of day `day` (0 <= day <= max_days), the point where Alg. 1's time loop
+ * resumes: counts [R][Nc][N] (>= 0) and phi [R][N].  Errors: SIM_E_INVALID_ARG
+ * (a negative count, a negative or non-finite phi, day out of range), SIM_E_CUDA.  Runs resumed from a state
  * taken by sim_state are bit-identical to uninterrupted runs.  Statistics of
  * days >= day are cleared.  Synchronises `stream`. */
 sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi, int32_t day,
                          int32_t where, void* stream);
 
-/* Daily statistics since day 0: infected[R][max_days] and animals[R][max_days]
- * (after each day's events; int64), counters[R][4] = SSA transitions fired,
+/* Daily statistics since day 0 -- the national totals of I and of all animals
+ * that the goal function of Sec. 4.3 (Eq. (goal)) and the prevalence curves of
+ * Sec. 4.1 aggregate: infected[R][max_days] and animals[R][max_days] (after each
+ * day's events; int64), counters[R][4] = SSA transitions fired,
  * events applied, events clamped, events skipped (ERROR policy).  Any output
  * may be NULL.  Host pointers.  Synchronises `stream`. */
 sim_status sim_stats(sim_handle* h, int64_t* infected, int64_t* animals, int64_t* counters,
@@ -180,6 +195,27 @@ sim_status sim_score_backward(sim_handle* h, void* stream);
 sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_days, double* per_rep,
                                 double* out, void* stream);
 
+/* The score-function estimate from moment sums of sim_gradient_moments: the
+ * likelihood-ratio identity d E[f] / d theta = E[f d log p / d theta] (log p the
+ * path's log-likelihood under the direct method's law, Sec. 3.3 Eqs. (sampling),
+ * (sampling2)), estimated by the sample covariance of f and the score.
+ * moments: host double [n_chunks][n_days][34], each chunk the out array of one
+ * sim_gradient_moments call (chunks of replicates, added in chunk order); R: the
+ * total replicate count (>= 2); jac: host double [8][n_params], d theta_k / d
+ * param_c for the 8 score terms of sim_score (e.g. the age-class ratios when one
+ * parameter scales upsilon of every class).  Writes, host arrays:
+ *   mean_f [n_days]            = sum f / R,
+ *   grad   [n_days][n_params]  = sum_k cov(f, s_k) jac[k][c],
+ *                               cov = (sum f s_k - sum f sum s_k / R) / (R - 1),
+ *   se     [n_days][n_params]  = sqrt(sum_k (Var(f s_k) / R) jac[k][c]^2),
+ *                               Var(f s_k) = max(sum (f s_k)^2 / R - (sum f s_k / R)^2, 0)
+ * (any output may be NULL).  Host arithmetic only; no handle, no device.
+ * Errors: SIM_E_INVALID_ARG (n_chunks < 1, n_days < 0, n_params < 1, R < 2, a
+ * NULL input). */
+sim_status sim_gradient_estimate(const double* moments, int32_t n_chunks, int32_t n_days, int64_t R,
+                                 const double* jac, int32_t n_params, double* mean_f, double* grad,
+                                 double* se);
+
 /* The same result as sim_gradient_moments, from a call that allocates no
  * memory.  The paper has no counterpart: this is for callers that cannot call
  * cudaMalloc -- code whose device memory belongs to another allocator (a
@@ -188,19 +224,26 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
  * cause.  Its scratch is one fixed array in the library's device image (about
  * 650 KiB on every GPU that loads the library, kept until exit), which limits a
  * call to at most 8192 replicates and 512 days; larger requests return
- * SIM_E_INVALID_ARG.  The first call on each device looks the array's device
- * address up once (make it before any stream capture).  Every call shares the
- * array: calls that overlap on the GPU race and must be serialised by the
- * caller.  Nothing needs clearing between calls.  Host outputs; synchronises
- * `stream`. */
+ * SIM_E_INVALID_ARG.  Every call looks the array's address up on the current
+ * device; with lazy module loading (the CUDA default) the first lookup on a
+ * device is when the runtime places the array in device memory, so make the
+ * first call on each device before any stream capture and before measuring free
+ * memory.  Every call shares the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  Nothing needs clearing between calls.
+ * Returns the handle's latched device error as sim_gradient_moments does.  Host
+ * outputs; synchronises `stream`. */
 sim_status sim_gradient_moments_noalloc(sim_handle* h, const int32_t* days, int32_t n_days,
                                         double* per_rep, double* out, void* stream);
 
-/* Back to day 0 with the initial counts and phi; statistics and score cleared.
- * clear_events = 1 also drops the loaded events. */
+/* Back to day 0 with the initial counts and phi of sim_create (the initial
+ * state X_0, Y_0 of Sec. 3.1's time discretisation); statistics and score
+ * cleared.  clear_events = 1 also drops the loaded events (Sec. 3.2's lists
+ * E1, E2).  Synchronises the device.  Errors: SIM_E_CUDA. */
 sim_status sim_reset(sim_handle* h, int32_t clear_events);
 
-/* Frees everything the handle owns.  NULL is accepted. */
+/* Frees everything the handle owns (the device state X, Y and the event
+ * schedule of Secs. 2.2, 2.3 and 3.4); caller-owned buffers of sim_create_on
+ * are left alone.  Synchronises the device.  NULL is accepted. */
 void sim_destroy(sim_handle* h);
 
 /* Text of the last error on this handle ("" if none).  Valid until the next

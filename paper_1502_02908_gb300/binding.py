@@ -104,6 +104,7 @@ def load_library(build_if_missing: bool = True):
             "sim_score_backward": [vp, vp],
             "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
+            "sim_gradient_estimate": [pd, i32, i32, i64, pd, i32, pd, pd, pd],
             "sim_run_batch": [P(vp), i32, pi32, vp],
             "sim_set_option": [vp, i32, i64],
             "sim_set_regions": [vp, pi32, i32],
@@ -164,6 +165,27 @@ def _check(L, h, status):
     if status != SIM_OK:
         msg = L.sim_last_error(h)
         raise SimError(status, msg.decode() if msg else "")
+
+
+def gradient_estimate(chunks, R: int, jac):
+    """The score-function estimate from moment sums (sim_gradient_estimate):
+    chunks [n_chunks, F, 34] (each a sim_gradient_moments result, added in chunk
+    order), R replicates in all, jac [8, P].  Returns mean_f [F], grad [F, P],
+    se [F, P]."""
+    L = load_library()
+    m = np.ascontiguousarray(chunks, np.float64)
+    if m.ndim == 2:
+        m = m[None]
+    J = np.ascontiguousarray(jac, np.float64)
+    F, P = m.shape[1], J.shape[1]
+    mean_f = np.zeros(F)
+    grad = np.zeros((F, P))
+    se = np.zeros((F, P))
+    st = L.sim_gradient_estimate(_p(m, ctypes.c_double), m.shape[0], F, int(R), _p(J, ctypes.c_double), P,
+                                 _p(mean_f, ctypes.c_double), _p(grad, ctypes.c_double), _p(se, ctypes.c_double))
+    if st != SIM_OK:
+        raise SimError(st, "sim_gradient_estimate: invalid arguments")
+    return mean_f, grad, se
 
 
 def current_stream():

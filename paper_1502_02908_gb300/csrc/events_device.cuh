@@ -1,5 +1,5 @@
-// Device code of the deterministic step (Eq. (numstep4); Sec. 3.3; Alg. 1 line
-// 13): the day's scheduled events (Sec. 3.2, Eq. (event)) applied in dependency
+// Device code of the deterministic step (Eq. (numstep4); Sec. 3.3; the event
+// step of Alg. 1): the day's scheduled events (Sec. 3.2, Eq. (event)) applied in dependency
 // levels.  Shared by the per-day kernels (events.cu) and the persistent batch
 // kernel (batch.cu).  The host assigns levels so that, within a level, no two
 // events sample the same node and no node is both sampled and added to; adds

@@ -942,6 +942,7 @@ sim_status handle_score_view(sim_handle* h, HandleScoreView* out) {
 }
 sim_status handle_fail(sim_handle* h, sim_status s, const char* msg) { return fail(h, s, "%s", msg); }
 sim_status handle_cuda_fail(sim_handle* h, cudaError_t e, const char* what) { return cuda_fail(h, e, what); }
+sim_status handle_check_latched(sim_handle* h) { return check_latched(h); }
 }  // namespace episim
 
 extern "C" {
@@ -1451,6 +1452,40 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
   if (n_days > 0) CK(h, cudaMemcpyAsync(out, h->d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st), "copy moments");
   CK(h, cudaStreamSynchronize(st), "stream synchronize");
   return check_latched(h);
+}
+
+sim_status sim_gradient_estimate(const double* moments, int32_t n_chunks, int32_t n_days, int64_t R,
+                                 const double* jac, int32_t n_params, double* mean_f, double* grad,
+                                 double* se) {
+  if (!moments || !jac || n_chunks < 1 || n_days < 0 || n_params < 1 || R < 2) return SIM_E_INVALID_ARG;
+  constexpr int kM = 34;
+  const double dR = (double)R;
+  for (int i = 0; i < n_days; ++i) {
+    double m[kM] = {0};
+    for (int c = 0; c < n_chunks; ++c)
+      for (int q = 0; q < kM; ++q) m[q] += moments[((size_t)c * n_days + i) * kM + q];
+    const double sf = m[0];
+    if (mean_f) mean_f[i] = sf / dR;
+    double cov[kScoreTerms], var8[kScoreTerms];
+    for (int k = 0; k < kScoreTerms; ++k) {
+      const double s_k = m[2 + 4 * k], fs_k = m[4 + 4 * k], fs2_k = m[5 + 4 * k];
+      cov[k] = (fs_k - sf * s_k / dR) / (dR - 1.0);
+      const double mean_fs = fs_k / dR;
+      const double v = fs2_k / dR - mean_fs * mean_fs;
+      var8[k] = (v > 0.0 ? v : 0.0) / dR;
+    }
+    for (int c = 0; c < n_params; ++c) {
+      double g = 0.0, v = 0.0;
+      for (int k = 0; k < kScoreTerms; ++k) {
+        const double j = jac[(size_t)k * n_params + c];
+        g += cov[k] * j;
+        v += var8[k] * j * j;
+      }
+      if (grad) grad[(size_t)i * n_params + c] = g;
+      if (se) se[(size_t)i * n_params + c] = std::sqrt(v);
+    }
+  }
+  return SIM_OK;
 }
 
 sim_status sim_set_params(sim_handle* h, const sim_params* p) {

@@ -197,4 +197,7 @@ struct HandleScoreView {
 sim_status handle_score_view(sim_handle* h, HandleScoreView* out);
 sim_status handle_fail(sim_handle* h, sim_status s, const char* msg);
 sim_status handle_cuda_fail(sim_handle* h, cudaError_t e, const char* what);
+// The handle's latched device error (underflow under the ERROR policy, an event
+// wait that ran out), read and cleared as every synchronising entry point does.
+sim_status handle_check_latched(sim_handle* h);
 }  // namespace episim

@@ -11,9 +11,14 @@
 // list of days) lives in one file-scope __device__ array of fixed size, present
 // on every GPU that loads the library until the process exits.  Host code cannot
 // use the array's name as a device address (on the host it names a stand-in), so
-// the first call on each device, with that device current, looks the address up
-// once with cudaGetSymbolAddress and keeps it; make that first call before any
-// stream capture.  Limits: at most kMaxReplicates replicates and kMaxDays days per
+// every call asks the runtime for the array's address on the current device (the
+// handle's device, as for every call on a handle) with cudaGetSymbolAddress.  Nothing is cached: a cached
+// pointer would go stale if the device's context were torn down and rebuilt
+// (cudaDeviceReset), which reloads the library's device image elsewhere.  With
+// lazy module loading (the CUDA default) the runtime places the array in device
+// memory on the first lookup on a device, so the first call on each device may
+// load it; make that first call before any stream capture and before measuring
+// free memory.  Limits: at most kMaxReplicates replicates and kMaxDays days per
 // call; larger requests are refused with SIM_E_INVALID_ARG.  All calls share the
 // one array: calls that overlap on the GPU (for example on two streams) race and
 // must be serialised by the caller.  Every word the kernels read from the array
@@ -22,7 +27,6 @@
 #include "internal.h"
 
 #include <cstdio>
-#include <mutex>
 
 namespace episim {
 
@@ -37,24 +41,12 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_lock;
-unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_lock);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -93,5 +85,5 @@ extern "C" sim_status sim_gradient_moments_noalloc(sim_handle* h, const int32_t*
     e = cudaMemcpyAsync(out, d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return handle_cuda_fail(h, e, "gradient moments (no-alloc)");
-  return SIM_OK;
+  return handle_check_latched(h);
 }

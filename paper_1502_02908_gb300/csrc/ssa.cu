@@ -1,9 +1,10 @@
 // Stochastic step (Eq. (numstep3)): Gillespie's direct method per node on
-// [d, d+1) with phi frozen (Sec. 3.3, Eqs. (sampling) and (sampling2); Alg. 1
-// lines 3-10), one thread per (replicate, node).  The continuous-state update of
-// the previous day (Eq. (numstep5) with Eq. (siminfpressure); Alg. 1 line 14)
-// is fused into the prologue, as Alg. 2 line 5 places it at the start of the
-// next stochastic task; the day's infected/total statistics are reduced there too.
+// [d, d+1) with phi frozen (Sec. 3.3, Eqs. (sampling) and (sampling2); the
+// per-node loop of Alg. 1), one thread per (replicate, node).  The
+// continuous-state update of the previous day (Eq. (numstep5) with Eq.
+// (siminfpressure); the last step of Alg. 1's day) is fused into the prologue,
+// as Alg. 2 places it at the start of the next stochastic task; the day's
+// infected/total statistics are reduced there too.
 //
 // Arithmetic (identical, by specification, to the CPU oracle): per class j,
 //   a_inf = (upsilon_j * phi) * S_j, a_rec = gamma_j * I_j, A_j = a_inf + a_rec,

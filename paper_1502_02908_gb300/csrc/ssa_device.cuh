@@ -1,5 +1,5 @@
 // Device code of the stochastic step (Eq. (numstep3); Sec. 3.3 Eqs. (sampling),
-// (sampling2); Alg. 1 lines 3-10) with the fused phi update (Eq. (numstep5)):
+// (sampling2); the per-node loop of Alg. 1) with the fused phi update (Eq. (numstep5)):
 // shared by the per-day kernels (ssa.cu) and the persistent batch kernel
 // (batch.cu).  State other blocks may have written in the same launch is read
 // with L2-coherent loads.

@@ -181,8 +181,9 @@ def prevalence_curve(w: W.Workload, days, x=(0.0, 0.0), seed_offset=0):
     """E[f_d] over w.R replicates at log scales x (replicate streams of seed w.seed + seed_offset)."""
     from . import gradient as GR
     wx = dataclasses.replace(w, params=scaled_params(w.params, x), seed=w.seed + seed_offset)
-    m, R, _ = GR.run_moments(GR.GradientSpec(wx, np.asarray(days, np.int32)))
-    return m[:, 0] / R
+    spec = GR.GradientSpec(wx, np.asarray(days, np.int32))
+    m, R, _ = GR.run_moments(spec)
+    return GR.estimate(m, R, spec.class_ratios())[0]
 
 
 class PrevalenceGoal:

@@ -5,9 +5,10 @@ minus the integral of the total rate a0 (the direct method's sampling law), with
 phi's dependence on (beta, alpha) carried through the daily recursion.  Then
 d E[f] / d theta = E[f * d log p / d theta], estimated by the covariance of f and
 the score over replicates.  The simulation, the per-node score terms, the reverse
-sweep of the phi recursion and the moment sums all run in libepisim's kernels;
-this module chooses replicate chunks, combines their moment sums and exposes the
-estimate as a ``torch.autograd.Function``.
+sweep of the phi recursion and the moment sums all run in libepisim's kernels,
+and the covariance estimate and its standard error in the library's
+sim_gradient_estimate; this module chooses replicate chunks, passes their moment
+sums on and exposes the estimate as a ``torch.autograd.Function``.
 
 theta = (upsilon, gamma, beta, alpha).  upsilon and gamma scale every age class
 (SISe3: the class ratios of the workload are kept), beta is one value for the
@@ -62,14 +63,15 @@ def _slice_params(p: W.Params, r0, r1):
 
 
 def run_moments(spec: GradientSpec, per_replicate=False, rank=0, world=1):
-    """Runs every replicate (in chunks), returns (moments [F, 34] summed over all
-    replicates, R, optional per-replicate (f [R, F], score [R, 8])).  With
-    world > 1 (torch.distributed initialised, one GPU per rank) each rank runs
-    its contiguous replicate range and the moment sums are combined in rank order."""
+    """Runs every replicate (in chunks), returns (moment sums [n_chunks, F, 34], one
+    row per chunk in replicate order, R, optional per-replicate (f [R, F], score
+    [R, 8])).  With world > 1 (torch.distributed initialised, one GPU per rank)
+    each rank runs its contiguous replicate range and the ranks' chunk rows are
+    gathered in rank order, so every rank holds the single-process rows."""
     from . import replicas
     w = spec.w
     days = np.ascontiguousarray(spec.days, np.int32)
-    total = np.zeros((days.size, N_MOMENTS))
+    rows = []
     fs, ss = [], []
     lo, hi = replicas.shard(w.R, world, rank)
     for r0 in range(lo, hi, spec.chunk):
@@ -82,35 +84,23 @@ def run_moments(spec: GradientSpec, per_replicate=False, rank=0, world=1):
             s.run(w.T)
             s.score_backward()
             m, per = s.gradient_moments(days)
-            total += m
+            rows.append(m)
             if per_replicate:
                 pi, pn, _ = s.stats()
                 fs.append(pi[:, days] / np.maximum(pn[:, days], 1))
                 ss.append(per)
         finally:
             s.close()
+    chunks = np.stack(rows) if rows else np.zeros((0, days.size, N_MOMENTS))
     if world > 1:
-        total = replicas.allreduce_moments(total)
+        chunks = replicas.allgather_rows(chunks)
     extra = (np.concatenate(fs), np.concatenate(ss)) if per_replicate and fs else None
-    return total, w.R, extra
+    return chunks, w.R, extra
 
 
-def estimate(moments, R, ratios):
-    """E[f], the gradient with respect to theta and its standard error.
-
-    moments [F, 34] (see run_moments); ratios = (upsilon class ratios, gamma class
-    ratios).  Returns mean_f [F], grad [F, 4], se [F, 4]."""
-    F = moments.shape[0]
-    sf, sf2 = moments[:, 0], moments[:, 1]
-    mean_f = sf / R
-    k = np.arange(8)
-    s_k = moments[:, 2 + 4 * k]
-    fs_k = moments[:, 4 + 4 * k]
-    fs2_k = moments[:, 5 + 4 * k]
-    cov = (fs_k - sf[:, None] * s_k / R) / (R - 1)            # [F, 8]
-    # SE of the mean of f*s (E[s] = 0): sqrt(Var(f s) / R)
-    var_fs = np.maximum(fs2_k / R - (fs_k / R) ** 2, 0.0)
-    se8 = np.sqrt(var_fs / R)
+def jacobian(ratios):
+    """d theta_k / d (upsilon, gamma, beta, alpha) for the 8 score terms: upsilon
+    and gamma scale every age class with the given class ratios."""
     ru, rg = ratios
     na = ru.size
     J = np.zeros((8, 4))
@@ -118,9 +108,14 @@ def estimate(moments, R, ratios):
     J[3:3 + na, 1] = rg
     J[6, 2] = 1.0
     J[7, 3] = 1.0
-    grad = cov @ J
-    se = np.sqrt((se8 ** 2) @ (J ** 2))
-    return mean_f, grad, se
+    return J
+
+
+def estimate(moments, R, ratios):
+    """E[f], the gradient with respect to theta and its standard error, computed by
+    the library (sim_gradient_estimate) from the moment sums of run_moments
+    ([n_chunks, F, 34] or [F, 34]).  Returns mean_f [F], grad [F, 4], se [F, 4]."""
+    return B.gradient_estimate(moments, R, jacobian(ratios))
 
 
 def score_gradient(spec: GradientSpec):

@@ -4,9 +4,9 @@ Replicates (and batch instances) are independent and share only the read-only
 event schedule, so several GPUs run disjoint replicate ranges with no exchange on
 the data path; each GPU draws its replicates' own Philox streams
 (``replicate_base``), so the union of the ranges is identical to one GPU running
-all of them.  The one collective is the final reduction of the gradient-moment
-sums, gathered to every rank and added in rank order (deterministic, identical to
-the single-GPU sum over chunks in the same order).
+all of them.  The one collective is the final gather of the gradient-moment
+sums to every rank in rank order (deterministic: the library then adds them in
+that order, as it adds one GPU's replicate chunks).
 """
 from __future__ import annotations
 
@@ -40,3 +40,17 @@ def allreduce_moments(moments: np.ndarray, group=None):
     parts = [torch.empty_like(t) for _ in range(world)]
     dist.all_gather(parts, t, group=group)
     return combine([p.cpu().numpy() for p in parts])
+
+
+def allgather_rows(rows: np.ndarray, group=None):
+    """Gathers every rank's moment rows [n_rows, F, 34] (the same shape on every
+    rank) and concatenates them in rank order (torch.distributed; gloo or nccl)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    t = torch.as_tensor(np.ascontiguousarray(rows, np.float64))
+    if dist.get_backend(group) == "nccl":
+        t = t.cuda()
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t, group=group)
+    return np.concatenate([p.cpu().numpy() for p in parts])

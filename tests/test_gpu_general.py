@@ -247,3 +247,38 @@ def test_largest_model_bitexact(warp, group):
     w = W.GeneralWorkload("ring16", m, N, T, R, u0, y0, rates, vp, ev, 21)
     ref = _same(w, _run(w, warp=warp, group=group))
     assert ref.counters[:, 0].min() > 10_000
+
+
+def _exact_component_days(counts, N, R, seed=5):
+    """A SIR workload whose day d holds exactly counts[d] transfer-graph components:
+    each component is one event on a node of its own (exit of any animal, entry of
+    susceptibles or vaccination), or a transfer a -> b followed by an exit at b."""
+    w = W.sir_general(N=N, T=len(counts), n_events=0, R=R)
+    rng = np.random.default_rng(seed)
+    cols = [[] for _ in range(7)]
+    for d, c in enumerate(counts):
+        nodes = rng.permutation(N)[:2 * c]
+        for i in range(c):
+            a, b = int(nodes[2 * i]), int(nodes[2 * i + 1])
+            n = int(rng.integers(1, 6))
+            kind = int(rng.integers(0, 4))
+            if kind == 3:
+                rows = [(W.EXTERNAL, a, b, n, 0, -1), (W.EXIT, b, -1, n, 0, -1)]
+            else:
+                rows = [((W.EXIT, W.ENTER, W.INTERNAL)[kind], a, -1, n, (0, 1, 1)[kind], (-1, -1, 0)[kind])]
+            for kd, nd, ds, ct, sel, sh in rows:
+                for col, v in zip(cols, (d, kd, nd, ds, ct, sel, sh)):
+                    col.append(v)
+    w.events = W.GeneralEvents(*(np.asarray(c, np.int32) for c in cols))
+    return w
+
+
+@pytest.mark.parametrize("counts", [(8193, 8250, 8300, 8192, 8191), (1, 17, 31, 32, 33, 95)])
+def test_component_counts_at_the_warp_deal_edges_bitexact(counts):
+    # just above 8,192 components (the lane-major deal puts a second component on a
+    # warp's lanes), counts that are not multiples of 32, and fewer than one warp's
+    # worth; two replicates, so the event grid's second dimension varies
+    w = _exact_component_days(counts, N=20_000, R=2)
+    ref = _same(w, _run(w))
+    assert ref.counters[:, 1].sum() == 2 * len(w.events)
+    _same(w, _run(w, launch="graph"), ref)

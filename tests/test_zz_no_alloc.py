@@ -47,11 +47,17 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
     s.score_backward()
     days = np.array([9, 19, 39])
     ref_out, ref_per = s.gradient_moments(days)
+    import torch
+    free = []
     for _ in range(2):
         st, out, per = _noalloc(s, days)
+        free.append(torch.cuda.mem_get_info()[0])
         assert st == B.SIM_OK, s.L.sim_last_error(s.h)
         np.testing.assert_allclose(out, ref_out, rtol=RTOL, atol=0)
         np.testing.assert_allclose(per, ref_per, rtol=RTOL, atol=0)
+    # the first call on a device may place the library's array in device memory
+    # (lazy module loading); a later call takes no device memory at all
+    assert free[1] == free[0]
     # a different request reuses the same scratch
     st, out, _ = _noalloc(s, days[:1])
     assert st == B.SIM_OK
@@ -74,3 +80,26 @@ def test_noalloc_refuses_requests_beyond_its_scratch():
     assert st == B.SIM_E_INVALID_ARG
     assert b"512" in s.L.sim_last_error(s.h)
     s.close()
+
+
+def test_noalloc_returns_a_latched_device_error_as_the_regular_entry_point():
+    # under the ERROR policy a run whose events ask for absent animals latches
+    # SIM_E_UNDERFLOW; both entry points report it (and clear it) the same way
+    w = W.sise3_national(N=3000, T=12, n_events=20_000, e1_source="powerlaw")
+    days = np.array([5, 11])
+    status = []
+    for regular in (True, False):
+        s = B.Sim.from_workload(w, underflow_error=True, score=True)
+        s.run(w.T)
+        if regular:
+            with pytest.raises(B.SimError) as ei:
+                s.gradient_moments(days)
+            status.append(ei.value.status)
+            ref_out, _ = s.gradient_moments(days)         # the error was cleared
+        else:
+            status.append(_noalloc(s, days)[0])
+            st, out, _ = _noalloc(s, days)
+            assert st == B.SIM_OK
+            np.testing.assert_allclose(out, ref_out, rtol=RTOL, atol=0)
+        s.close()
+    assert status == [B.SIM_E_UNDERFLOW, B.SIM_E_UNDERFLOW]
