@@ -1,12 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the event-based SISe3 simulation on one GB300 (or N, as replicas).
 
-Workload (one "step"): the national-scale SISe3 instance, 37,000 herds x 1,460 days,
-3,000,000 scheduled events (exit / enter / aging / external transfer), one replicate
-per GPU; the whole horizon is the step (stochastic step, events and phi update of
-every day).  Inputs are resident in HBM when the timed region starts; the L2 cache
-(129 MB; the state and event schedule fit in it) is flushed between timed steps by
-writing a 512 MB buffer.
+Main line (one "step"): the national-scale SISe3 instance, 37,000 herds x 1,460
+days, 3,000,000 scheduled events (exit / enter / aging / external transfer), one
+replicate per GPU; the whole horizon is the step (stochastic step, events and phi
+update of every day).  Inputs are resident in HBM when the timed region starts; the
+L2 cache (129 MB; the state and event schedule fit in it) is flushed between timed
+steps by writing a 512 MB buffer.
+
+Legs, each with its correctness check: the plain SISe instance (1,000 nodes x 365
+days; bit-exact against the oracle over the whole horizon), the batched national
+network (256 replicates x 365 days; a seeded subset of replicates bit-exact against
+the oracle), the score-function gradient (10,000 nodes x 4,096 replicates x 365
+days; central differences under common random numbers on 1,024 replicates), the
+uneven batch (512 instances in one persistent launch against running them one after
+another; a seeded subset bit-exact against the oracle), the synthetic benchmark of
+Sec. 4.2, the parameter fit of Sec. 4.3 and the general model.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
 specification the CUDA path matches bit for bit) on a bounded sample instead.
@@ -16,7 +25,9 @@ stream), no collective on the data path; value = all ranks' node-days / max time
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -30,28 +41,33 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "node-days/sec and SSA events/sec (batched vs plain, bit-exact to oracle)"
-# FP64 pipe peak for the roofline, from unit counts and the clock: each SM sub-partition
-# (4 per SM) retires one 32-lane FP64 instruction per 64 cycles, so the GPU retires
-# SMs x 4 x 32 / 64 lanes per cycle (152 SMs at 2.07 GHz: 6.29e11 lane-ops/s, the
-# nominal 1.25 TFLOP/s FP64 with an FMA counted as two flops).
-FP64_LANES_PER_SM_CYCLE = 4 * 32 / 64
-# algorithmic HBM bytes of the stochastic step per node-day (SISe3: counts read and
-# written 24 + 24 B, phi read and written 8 + 8 B)
+# algorithmic HBM bytes of the stochastic step per node-day (counts read and written,
+# SISe3 24 + 24 B, SISe 8 + 8 B; phi read and written 8 + 8 B)
 SSA_BYTES_PER_NODE_DAY = {3: 64, 1: 32}
-# FP64 instruction-lanes the specification costs on the FP64 pipe (IEEE add / mul = 1,
-# IEEE divide = 7: its measured throughput is 1/7 of DFMA's on GB300), SISe3:
-#   per fired transition: 2 (P sums) + 7 (tau) + 1 (t + tau) + 1 (r) + 1 (threshold)
-#                         + 2 (two rates) + 1 (A_j) = 15
-#   per node-day: closing draw 2 + 7 + 1 = 10; rates 3 x 4 = 12; phi update 12  = 34
+# Algorithmic binary64 work of the direct method, counted two ways (FP64 lane-ops):
+#  - per draw (Gillespie step, including the one draw per node-day that ends the
+#    day): about 40 -- -log(u) 20-25, one IEEE divide 8-10, rates, sums and compares
+#    about 6 -- the figure the kernel's roofline uses;
+#  - the specification's own operations (R4-R6, R8 of the design record), add/mul = 1
+#    and divide = 7 (its measured throughput is 1/7 of DFMA's), the -log counted as 0
+#    because the specification computes it in integer fixed point.  SISe3:
+#      per fired transition: 2 (P sums) + 7 (tau) + 1 (t + tau) + 1 (r) + 1 (threshold)
+#                            + 2 (two rates) + 1 (A_j) = 15
+#      per node-day: closing draw 2 + 7 + 1 = 10; rates 3 x 4 = 12; phi update 12 = 34
+FP64_PER_DRAW = 40
 FP64_PER_TRANSITION = {3: 15, 1: 12}
 FP64_PER_NODE_DAY = {3: 34, 1: 24}
+# event step: a 16-B record per event, and read + write of the Nc int32 counts of
+# each herd it touches (two for a transfer)
+EVENT_RECORD_BYTES = 16
 # ncu summary of the stochastic-step kernel: its DRAM bytes per launch count as the
 # roofline's traffic only while the kernel sources still hash to the captured ones
 SSA_PROFILE = os.path.join(ROOT, "profiles", "k_node_day_dealt_national_day300.md")
-
-
 # the device sources the stochastic-step kernel is compiled from
 SSA_SOURCES = ("ssa.cu", "ssa_device.cuh", "devmath.cuh", "softdiv.cuh", "neglog_table.h", "internal.h")
+# days whose prevalence the gradient leg differentiates: the last day and the 52
+# week ends (days 7, 14, ..., 364 of the year, as indices 6, 13, ..., 363)
+GRADIENT_DAYS = np.array([364] + [7 * k - 1 for k in range(1, 53)], np.int32)
 
 
 def measured_peaks():
@@ -95,7 +111,11 @@ def parse():
     ap.add_argument("--days", type=int, default=1460)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--uneven-instances", type=int, default=512)
     ap.add_argument("--no-synthetic", action="store_true")
     ap.add_argument("--no-fitting", action="store_true")
     ap.add_argument("--no-general", action="store_true")
@@ -164,9 +184,148 @@ def oracle_baseline(w, days, note):
             "seconds": dt, "events_per_s": ev / dt}, r
 
 
-def batched_leg(args, B, W, torch, plain_value):
-    """The same national network batched: 256 replicates x 365 days, each with its
-    own (upsilon, gamma), in one handle; launch mode chosen by a short autotune."""
+def oracle_many(jobs, threads=None):
+    """Runs the CPU oracle on every (workload, replicate, days) of `jobs`, one job per
+    host thread on all cores (each oracle call is single-threaded C that releases
+    the interpreter lock).  Returns (results, wall seconds, threads used)."""
+    import oracle
+    oracle.build()
+    L = oracle.lib()
+    n = max(1, min(threads or os.cpu_count() or 1, len(jobs)))
+    # largest jobs first, so that the pool's tail is short
+    by_size = sorted(range(len(jobs)), key=lambda i: -jobs[i][0].N * jobs[i][2])
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=n) as ex:
+        futs = {i: ex.submit(oracle.run, jobs[i][0], ndays=jobs[i][2], replicates=[jobs[i][1]], lib_handle=L)
+                for i in by_size}
+        res = [futs[i].result() for i in range(len(jobs))]
+    return res, time.perf_counter() - t0, n
+
+
+def traced_kernels(sim, reset, run):
+    """Per-kernel device time over one untimed run: the day loop captured as a CUDA
+    graph with a pair of CUDA events around every kernel (no host launch gaps in
+    the spans) and without programmatic dependent launch, so that each span holds
+    that kernel's own execution only (under programmatic dependent launch a kernel
+    starts early and its span includes waiting for the previous one).  Returns
+    {"ssa" | "events" | "finalize": (ms, launches)}."""
+    sim.set_launch("graph")
+    sim.set_overlap(False)
+    reset()
+    sim.profile(True)
+    run()
+    prof = sim.profile_read()
+    sim.profile(False)
+    sim.set_overlap(True)
+    return prof
+
+
+def event_bytes(w, days):
+    """Algorithmic bytes of the event step over days [0, days): each event's 16-B
+    record plus a read and a write of the Nc counts of every herd it touches."""
+    from paper_1502_02908_gb300 import workloads as W
+    m = w.events.day < days
+    n = int(m.sum())
+    n_transfer = int((w.events.kind[m] == W.EXTERNAL).sum())
+    return n * EVENT_RECORD_BYTES + (n + n_transfer) * w.nc * 4 * 2
+
+
+def fp64_peak(B):
+    """Measured FP64 instruction-lane throughput (sim_fp64_peak): FMA and add."""
+    fma, fma_ms = B.fp64_peak(0, 1 << 14)
+    add, _ = B.fp64_peak(1, 1 << 14)
+    return {"fma_lane_ops_per_s": fma, "add_lane_ops_per_s": add, "fma_launch_ms": fma_ms,
+            "how": "sim_fp64_peak: 8 independent chains per thread, whole waves, best of 3 launches"}
+
+
+def ssa_roofline(w, R, T, transitions, prof, peak, ms_per_step, hbm_peak):
+    """Roofline of the stochastic-step kernel from the traced per-launch time."""
+    ssa_ms, ssa_n = prof["ssa"]
+    avg_s = ssa_ms / 1000 / max(ssa_n, 1)
+    node_days = w.N * R * T
+    # draws: every fired transition plus the one draw per node-day that ends the day
+    # (an upper bound: a node-day with no positive rate draws nothing)
+    draws = transitions + node_days
+    per_launch = FP64_PER_DRAW * draws / max(ssa_n, 1)
+    spec_per_launch = (FP64_PER_TRANSITION[w.model] * transitions + FP64_PER_NODE_DAY[w.model] * node_days) / max(ssa_n, 1)
+    achieved = per_launch / avg_s
+    bytes_per_launch = SSA_BYTES_PER_NODE_DAY[w.model] * w.N * R
+    hbm = bytes_per_launch / avg_s / 1e9
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G FP64 lane-ops/s",
+            "frac": achieved / peak,
+            "ops_per_launch": per_launch, "ops_count": f"{FP64_PER_DRAW} per draw (draws = transitions + node-days)",
+            "frac_spec_count": spec_per_launch / avg_s / peak,
+            "avg_launch_us": 1e6 * avg_s, "launches": ssa_n,
+            "avg_launch_x_launches_ms": 1e3 * avg_s * ssa_n, "fits_in_ms_per_step": 1e3 * avg_s * ssa_n <= ms_per_step,
+            "peak_source": "measured: sim_fp64_peak (FP64 FMA lane-ops/s on this GPU)",
+            "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm / hbm_peak if hbm_peak else None, "bytes_per_launch": bytes_per_launch}}
+
+
+def events_roofline(w, T, prof, hbm_peak):
+    ev_ms, ev_n = prof["events"]
+    if not ev_n:
+        return None
+    avg_s = ev_ms / 1000 / ev_n
+    b = event_bytes(w, T) / ev_n
+    return {"kernel": "k_events_day_df (event step)", "bound": "latency", "achieved": b / avg_s / 1e9,
+            "peak": hbm_peak, "unit": "GB/s", "frac": (b / avg_s / 1e9) / hbm_peak if hbm_peak else None,
+            "bytes_per_launch": b, "avg_launch_us": 1e6 * avg_s, "launches": ev_n,
+            "note": "HBM view of algorithmic bytes; the launch is bound by the day's longest "
+                    "transfer-graph component, applied serially by one thread"}
+
+
+def plain_sise_leg(args, B, W, torch, oracle_check):
+    """The plain SISe instance: 1,000 nodes x 365 days, 20,000 events; bit-exact
+    against the oracle over the whole horizon."""
+    from paper_1502_02908_gb300 import autotune
+    w = W.sise_plain()
+    best, _ = autotune.autotune(w, days=73, thresholds=(1 << 30, 200), modes=("stream", "graph"), repeats=1,
+                                groups=(1 << 30, 100))
+    sim = B.Sim.from_workload(w)
+    sim.set_group_threshold(best["group_threshold"]); sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
+    u0 = w.u0[None]; phi0 = w.phi0[None]
+    steps, warm = 10, 3
+    times = []
+    _, _, c0 = sim.stats()
+    for i in range(warm + steps):
+        sim.set_state(u0, phi0, 0)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(); sim.run(w.T); e1.record()
+        torch.cuda.synchronize()
+        if i >= warm:
+            times.append(e0.elapsed_time(e1))
+    c, p, _ = sim.state()
+    pi, pn, c1 = sim.stats()
+    sim.close()
+    ms = statistics.median(times)
+    per = (c1[0] - c0[0]) // (warm + steps)
+    line = {"workload": f"SISe plain: {w.N} nodes x {w.T} days, {len(w.events)} events, 1 replicate",
+            "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warm, "transitions_per_step": int(per[0]), "events_per_step": int(per[1]),
+            "events_per_s": int(per[0] + per[1]) / (ms / 1000), "launch": best}
+    if oracle_check:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        ref = oracle.run(w)
+        dt = time.perf_counter() - t0
+        line["bitexact_vs_oracle"] = {
+            "days": w.T, "counts_equal": bool(np.array_equal(c, ref.counts)),
+            "phi_equal": bool(np.array_equal(p, ref.phi)),
+            "daily_stats_equal": bool(np.array_equal(pi[:, :w.T], ref.prev_i) and np.array_equal(pn[:, :w.T], ref.prev_n)),
+            "counters_equal": bool(np.array_equal(c1[0] - c0[0], ref.counters[0] * (warm + steps)))}
+        line["cpu_baseline"] = {"value": w.N * w.T / dt, "unit": "node-days/s", "cores": 1, "kind": "oracle",
+                                "sample": "the whole instance, 1 replicate, single thread"}
+    return line
+
+
+def batched_leg(args, B, W, torch, plain_value, hbm_peak, fp64, oracle_check):
+    """The national network batched: 256 replicates x 365 days, each with its own
+    (upsilon, gamma), in one handle; launch mode chosen by a short autotune.  A
+    seeded subset of replicates is checked bit for bit against the oracle, which
+    also gives the all-core CPU baseline."""
     from paper_1502_02908_gb300 import autotune
     w = W.sise3_batched(R=256, T=365)
     # the persistent kernel is for uneven batches; on one handle its per-replicate
@@ -176,8 +335,9 @@ def batched_leg(args, B, W, torch, plain_value):
     sim = B.Sim.from_workload(w)
     sim.set_group_threshold(best["group_threshold"]); sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
     u0 = np.repeat(w.u0[None], w.R, 0); phi0 = np.repeat(w.phi0[None], w.R, 0)
-    steps, warm = 2, 1
+    steps, warm = 3, 1
     times = []
+    _, _, c0 = sim.stats()
     for i in range(warm + steps):
         sim.set_state(u0, phi0, 0)
         torch.cuda.synchronize()
@@ -186,15 +346,138 @@ def batched_leg(args, B, W, torch, plain_value):
         torch.cuda.synchronize()
         if i >= warm:
             times.append(e0.elapsed_time(e1))
-    _, _, ctr = sim.stats()
-    sim.close()
-    ms = sum(times) / len(times)
+    counts, phi, _ = sim.state()
+    _, _, c1 = sim.stats()
+    ms = statistics.median(times)
     value = w.N * w.R * w.T / (ms / 1000)
-    trans = int(ctr[:, 0].sum()) // (warm + steps)
-    evs = int(ctr[:, 1].sum()) // (warm + steps)
-    return {"workload": f"SISe3 national network, {w.R} replicates x {w.T} days, own (upsilon, gamma) each",
+    trans = int((c1[:, 0] - c0[:, 0]).sum()) // (warm + steps)
+    evs = int((c1[:, 1] - c0[:, 1]).sum()) // (warm + steps)
+    prof = traced_kernels(sim, lambda: sim.set_state(u0, phi0, 0), lambda: sim.run(w.T))
+    sim.close()
+    line = {"workload": f"SISe3 national network, {w.R} replicates x {w.T} days, own (upsilon, gamma) each",
             "value": value, "unit": "node-days/s", "steps": steps, "warmup": warm, "ms_per_step": ms,
-            "events_per_s": (trans + evs) / (ms / 1000), "launch": best, "vs_plain": value / plain_value}
+            "events_per_s": (trans + evs) / (ms / 1000), "transitions_per_step": trans, "events_per_step": evs,
+            "launch": best, "vs_plain": value / plain_value,
+            "roofline": dict(kernel="k_node_day_dealt (stochastic step, 256 replicates)",
+                             **ssa_roofline(w, w.R, w.T, trans, prof, fp64, ms, hbm_peak))}
+    line["roofline"]["hbm"]["note"] = "the state (counts and phi of 256 replicates, 0.3 GB) exceeds L2"
+    if oracle_check:
+        rng = np.random.default_rng(3)
+        reps = sorted(int(r) for r in rng.choice(w.R, size=16, replace=False))
+        res, dt, n = oracle_many([(w, r, w.T) for r in reps])
+        ok_c = all(np.array_equal(counts[r], x.counts[0]) for r, x in zip(reps, res))
+        ok_p = all(np.array_equal(phi[r], x.phi[0]) for r, x in zip(reps, res))
+        line["bitexact_vs_oracle"] = {"replicates": reps, "days": w.T, "counts_equal": bool(ok_c),
+                                      "phi_equal": bool(ok_p)}
+        line["cpu_baseline"] = {"value": len(reps) * w.N * w.T / dt, "unit": "node-days/s", "cores": n,
+                                "kind": "oracle",
+                                "sample": f"{len(reps)} seeded replicates of the {w.R}, whole horizon, "
+                                          "one replicate per host thread"}
+    return line
+
+
+def gradient_leg(args, B, W, G, torch):
+    """The score-function gradient on SISe, 10,000 nodes x 4,096 replicates x 365
+    days, of the final prevalence and the 52 week-end prevalences with respect to
+    (upsilon, gamma, beta, alpha): simulation with score terms, the reverse sweep of
+    the phi recursion and the moment sums, in chunks of 1,024 replicates.  Checked
+    against central finite differences (h = 1e-3 relative, common random numbers)
+    on the first 1,024 replicates at the final day and the week-26 day."""
+    w = W.sise_gradient()
+    spec = G.GradientSpec(w, GRADIENT_DAYS, chunk=1024)
+    G.score_gradient(G.GradientSpec(W.sise_gradient(R=64, T=30), np.array([29], np.int32), chunk=64))  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chunks, R, _ = G.run_moments(spec)
+    dt = time.perf_counter() - t0
+    ratios = spec.class_ratios()
+    mean_f, grad, se = G.estimate(chunks, R, ratios)
+    line = {"workload": f"score-function gradient, SISe {w.N} nodes x {w.R} replicates x {w.T} days, "
+                        f"{len(w.events)} events; f = final and 52 week-end prevalences; theta = "
+                        "(upsilon, gamma, beta, alpha)",
+            "seconds": dt, "value": w.N * w.R * w.T / dt, "unit": "node-days/s (with score terms)",
+            "chunks": int(chunks.shape[0]), "chunk_replicates": spec.chunk,
+            "final_prevalence": float(mean_f[0]), "gradient_final": grad[0].tolist(), "se_final": se[0].tolist()}
+    # central differences with common random numbers on the first chunk's replicates
+    w1 = W.sise_gradient(R=spec.chunk)
+    pick = np.array([0, 26])                       # final day (364) and week 26 (day index 181)
+    s1 = G.GradientSpec(w1, GRADIENT_DAYS[pick], chunk=spec.chunk)
+    _, g1, se1 = G.estimate(chunks[:1, pick], spec.chunk, ratios)
+    t0 = time.perf_counter()
+    fd, fd_se = G.fd_gradient(s1, rel_h=1e-3)
+    z = np.abs(g1 - fd) / np.sqrt(se1 ** 2 + fd_se ** 2)
+    line["fd_check"] = {"replicates": spec.chunk, "days": GRADIENT_DAYS[pick].tolist(), "rel_h": 1e-3,
+                        "score": g1.tolist(), "score_se": se1.tolist(), "fd": fd.tolist(), "fd_se": fd_se.tolist(),
+                        "z": z.tolist(), "max_z": float(z.max()), "within_3_se": bool(np.all(z < 3.0)),
+                        "seconds": time.perf_counter() - t0}
+    return line
+
+
+def uneven_leg(args, B, W, torch, oracle_check):
+    """The uneven batch: 512 instances mixing SISe and SISe3 (node counts log-uniform
+    in [100, 50,000], horizons 90-1,460 days, 80 events per node-year) advanced in
+    one persistent work-stealing launch, against running the instances one after
+    another (CUDA-graph day loops); every instance's final counts equal across the
+    two, and a seeded subset of instances bit-exact against the oracle."""
+    t0 = time.perf_counter()
+    ws = W.uneven_batch(n_inst=args.uneven_instances)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sims = [B.Sim.from_workload(w) for w in ws]
+    load_s = time.perf_counter() - t0
+    node_days = sum(w.N * w.T for w in ws)
+    n_events = sum(len(w.events) for w in ws)
+    steps, warm = 2, 1
+    times = []
+    for i in range(warm + steps):
+        for s in sims:
+            s.reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); B.run_batch(sims); e1.record()
+        torch.cuda.synchronize()
+        if i >= warm:
+            times.append(e0.elapsed_time(e1))
+    finals = [s.state()[:2] for s in sims]
+    batch_states = [f[0] for f in finals]
+    batch_phi = [f[1] for f in finals]
+    ctr = np.stack([s.stats()[2][0] for s in sims])
+    ms = statistics.median(times)
+    # one after another: each instance's own CUDA-graph day loop
+    for s in sims:
+        s.reset()
+        s.set_launch("graph")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for w, s in zip(ws, sims):
+        s.run(w.T)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    same = all(np.array_equal(s.state()[0], c) for s, c in zip(sims, batch_states))
+    for s in sims:
+        s.close()
+    per_run = ctr // (warm + steps)
+    line = {"workload": f"uneven batch: {len(ws)} instances (SISe / SISe3, N log-uniform 100-50,000, "
+                        "T 90-1,460 days, 80 events per node-year), one persistent launch",
+            "value": node_days / (ms / 1000), "unit": "node-days/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warm, "node_days_per_step": node_days, "events": n_events,
+            "events_per_s": float(per_run[:, 0].sum() + per_run[:, 1].sum()) / (ms / 1000),
+            "one_after_another_ms": seq_ms, "speedup_vs_one_after_another": seq_ms / ms,
+            "batch_equals_one_after_another": bool(same), "generate_s": gen_s, "load_events_s": load_s}
+    if oracle_check:
+        rng = np.random.default_rng(5)
+        pick = sorted(int(i) for i in rng.choice(len(ws), size=min(16, len(ws)), replace=False))
+        res, dt, n = oracle_many([(ws[i], 0, ws[i].T) for i in pick])
+        ok_c = all(np.array_equal(batch_states[i][0], r.counts[0]) for i, r in zip(pick, res))
+        ok_p = all(np.array_equal(batch_phi[i][0], r.phi[0]) for i, r in zip(pick, res))
+        line["bitexact_vs_oracle"] = {"instances": pick, "counts_equal": bool(ok_c), "phi_equal": bool(ok_p)}
+        nd = sum(ws[i].N * ws[i].T for i in pick)
+        line["cpu_baseline"] = {"value": nd / dt, "unit": "node-days/s", "cores": n, "kind": "oracle",
+                                "sample": f"{len(pick)} seeded instances of the {len(ws)}, whole horizons "
+                                          f"({nd} node-days), one instance per host thread"}
+    return line
 
 
 def synthetic_leg(args, B, W, torch, oracle_check):
@@ -375,12 +658,17 @@ def dist_setup():
     return None, 0, 1
 
 
+# days of the national horizon that one CPU step covers: the same sample for the
+# reference arm's steps and for the main line's cpu_baseline
+CPU_SAMPLE_DAYS = 365
+
+
 def run_reference(args, dist, rank, ws):
     from paper_1502_02908_gb300 import workloads as W
     if rank != 0:
         return
     w = W.sise3_national()
-    days = 73                                   # bounded sample per step
+    days = CPU_SAMPLE_DAYS                      # bounded sample per step
     times = []
     for i in range(args.warmup + args.steps):
         base, _ = oracle_baseline(w, days, "national SISe3")
@@ -388,6 +676,7 @@ def run_reference(args, dist, rank, ws):
             times.append(base["seconds"])
     total = sum(times)
     value = w.N * days * args.steps / total
+    sample = f"national SISe3: first {days} of {w.T} days, 1 replicate, single thread, per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-days/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -395,8 +684,7 @@ def run_reference(args, dist, rank, ws):
             "config": {"workload": f"SISe3 national: {w.N} herds x {w.T} days, {len(w.events)} events, "
                                    "1 replicate per GPU (plain)",
                        "replicates_per_gpu": 1, "parallelism": f"replicas x{args.gpus}"},
-            "cpu_baseline": {"value": value, "unit": "node-days/s", "cores": 1, "kind": "oracle",
-                             "sample": "first 73 of 1,460 days of the national SISe3 workload per step"},
+            "cpu_baseline": {"value": value, "unit": "node-days/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "node-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -416,6 +704,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     build()
+    leg_s = {}
+    t_leg = time.perf_counter()
     w = W.sise3_national()
     w.T = min(args.days, w.T)        # a shorter horizon of the same instance
     tuned = {"warp_threshold": -1, "group_threshold": -1, "launch": "graph"}
@@ -427,9 +717,13 @@ def main():
     t0 = time.perf_counter()
     sim.load_events(w.events)
     preprocess_s = time.perf_counter() - t0
-    sim.set_group_threshold(tuned["group_threshold"])
-    sim.tune(tuned["warp_threshold"])
-    sim.set_launch(tuned["launch"])
+
+    def configure():
+        sim.set_group_threshold(tuned["group_threshold"])
+        sim.tune(tuned["warp_threshold"])
+        sim.set_launch(tuned["launch"])
+
+    configure()
     stream = torch.cuda.current_stream()
     R, N, T = 1, w.N, w.T
     u0_all = np.repeat(w.u0[None], R, 0)
@@ -472,6 +766,7 @@ def main():
     node_days = N * T * R * ws
     value = node_days * args.steps / (total_ms / 1000)
     ev_rate = (transitions + events) * ws * args.steps / (total_ms / 1000)
+    ms_per_step = total_ms / args.steps
 
     # end to end through the C ABI with host buffers: set state from host, run, read
     # the final state and the daily statistics back to host
@@ -489,38 +784,25 @@ def main():
     e2e = {"value": node_days / statistics.median(e2e_times), "unit": "node-days/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # per-kernel device time over one traced (untimed) step
-    reset()
-    sim.profile(True)
-    step()
-    prof = sim.profile_read()
-    sim.profile(False)
+    # per-kernel device time over one traced (untimed) step without overlap
+    prof = traced_kernels(sim, reset, step)
+    configure()
     ssa_ms, ssa_n = prof["ssa"]
     ev_ms, ev_n = prof["events"]
     fin_ms, fin_n = prof["finalize"]
     tot_k = ssa_ms + ev_ms + fin_ms
-    fp64_ops = FP64_PER_TRANSITION[w.model] * transitions + FP64_PER_NODE_DAY[w.model] * N * T
-    ssa_avg_s = ssa_ms / 1000 / max(ssa_n, 1)
-    achieved = fp64_ops / ssa_n / ssa_avg_s if ssa_n else 0.0
     peaks = measured_peaks()
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    fp64_peak = sms * FP64_LANES_PER_SM_CYCLE * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    hbm_achieved = SSA_BYTES_PER_NODE_DAY[w.model] * N / ssa_avg_s / 1e9 if ssa_n else 0.0
-    roofline = {"kernel": "k_node_day_dealt (stochastic step)", "bound": "alu", "achieved": achieved / 1e9,
-                "peak": fp64_peak / 1e9, "unit": "G FP64 lane-ops/s",
-                "frac": achieved / fp64_peak, "traffic": profiled_traffic(SSA_PROFILE),
-                "peak_source": f"unit counts: {sms} SMs x 4 sub-partitions x one 32-lane FP64 instruction per 64 "
-                               f"cycles x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz (MEASURED_PEAKS sm_max_mhz); "
-                               "the nominal 1.25 TFLOP/s FP64 / 2",
-                "hbm": {"achieved": hbm_achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                        "frac": hbm_achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                        "bytes_per_launch": SSA_BYTES_PER_NODE_DAY[w.model] * N,
-                        "note": "algorithmic bytes; the state stays in L2 within a step"},
-                "kernel_share": {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k},
-                "avg_launch_us": {"ssa": 1000 * ssa_ms / max(ssa_n, 1), "events": 1000 * ev_ms / max(ev_n, 1)}}
+    fp64 = fp64_peak(B)
+    roofline = dict(kernel="k_node_day_dealt (stochastic step)",
+                    **ssa_roofline(w, R, T, transitions, prof, fp64["fma_lane_ops_per_s"], ms_per_step,
+                                   peaks.get("hbm_gbs")))
+    roofline["traffic"] = profiled_traffic(SSA_PROFILE)
+    roofline["hbm"]["note"] = "algorithmic bytes; the state stays in L2 within a step"
+    roofline["kernel_share_traced"] = {"ssa": ssa_ms / tot_k, "events": ev_ms / tot_k, "finalize": fin_ms / tot_k}
+    roofline["traced_step_ms"] = tot_k
 
     line = {"metric": METRIC, "value": value, "unit": "node-days/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
             "config": {"workload": f"SISe3 national: {N} herds x {T} days, {len(w.events)} events, "
                                    "1 replicate per GPU (plain)",
@@ -528,21 +810,17 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "events_per_s": ev_rate, "ssa_transitions_per_step": transitions, "events_per_step": events,
             "preprocess_s": preprocess_s, "e2e": e2e, "roofline": roofline,
+            "roofline_events": events_roofline(w, T, prof, peaks.get("hbm_gbs")),
+            "fp64_peak_measured": fp64,
             "gpu_launches": (ssa_n + ev_n + fin_n) * args.steps, "clocks": clk.summary()}
-
     line["config"]["launch"] = tuned
-    if not args.no_batched:
-        line["batched"] = batched_leg(args, B, W, torch, value)
-    if not args.no_synthetic and rank == 0:
-        line["synthetic"] = synthetic_leg(args, B, W, torch, not args.no_cpu_baseline)
-    if not args.no_fitting and rank == 0:
-        line["fitting"] = fitting_leg(args, B, W, torch)
-    if not args.no_general and rank == 0:
-        line["general"] = general_leg(args, B, W, torch, not args.no_cpu_baseline)
-    if rank == 0 and not args.no_cpu_baseline:
-        days = min(365, T)
+    oracle_check = not args.no_cpu_baseline
+    if rank == 0 and oracle_check:
+        days = min(CPU_SAMPLE_DAYS, T)
         base, ref = oracle_baseline(w, days, "national SISe3")
-        line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: base[k] for k in ("value", "unit", "cores", "kind")}
+        line["cpu_baseline"]["sample"] = (f"national SISe3: first {days} of {w.T} days, 1 replicate, single "
+                                          "thread (the reference arm times the same sample per step)")
         # bit-exactness of this configuration at the sampled horizon
         chk = B.Sim(w.model, w.u0, w.phi0, w.params, w.T, seed=w.seed)
         chk.load_events(w.events)
@@ -553,7 +831,33 @@ def main():
                                       "phi_max_rel": float(np.max(np.abs(p[0] - ref.phi[0]) /
                                                                   np.maximum(np.abs(ref.phi[0]), 1e-300)))}
     sim.close()
+    del flush
+    leg_s["main"] = time.perf_counter() - t_leg
+
+    def leg(name, fn):
+        t = time.perf_counter()
+        line[name] = fn()
+        torch.cuda.empty_cache()
+        leg_s[name] = time.perf_counter() - t
+
     if rank == 0:
+        if not args.no_plain:
+            leg("sise_plain", lambda: plain_sise_leg(args, B, W, torch, oracle_check))
+        if not args.no_batched:
+            leg("batched", lambda: batched_leg(args, B, W, torch, value / ws, peaks.get("hbm_gbs"),
+                                               fp64["fma_lane_ops_per_s"], oracle_check))
+        if not args.no_gradient:
+            from paper_1502_02908_gb300 import gradient as G
+            leg("gradient", lambda: gradient_leg(args, B, W, G, torch))
+        if not args.no_uneven:
+            leg("uneven", lambda: uneven_leg(args, B, W, torch, oracle_check))
+        if not args.no_synthetic:
+            leg("synthetic", lambda: synthetic_leg(args, B, W, torch, oracle_check))
+        if not args.no_fitting:
+            leg("fitting", lambda: fitting_leg(args, B, W, torch))
+        if not args.no_general:
+            leg("general", lambda: general_leg(args, B, W, torch, oracle_check))
+        line["leg_seconds"] = leg_s
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

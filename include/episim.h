@@ -188,9 +188,11 @@ sim_status sim_score_backward(sim_handle* h, void* stream);
 /* Moments for the score-function gradient estimate, on the device: for each
  * replicate, f = infected / animals after day days[i] (i < n_days) and s = its
  * score summed over nodes; writes per_rep [R][8] (may be NULL) and out
- * [n_days][34] = sum f, sum f^2, then for each of the 8 score terms k:
- * sum s_k, sum s_k^2, sum f s_k, sum (f s_k)^2 (replicates added in index
- * order).  d E[f] / d theta_k is estimated by the covariance of f and s_k.
+ * [n_days][42] = sum f, sum f^2, then for each of the 8 score terms k:
+ * sum s_k, sum s_k^2, sum f s_k, sum (f s_k)^2, then for each k: sum f s_k^2
+ * (replicates added in index order).  d E[f] / d theta_k is estimated by the
+ * covariance of f and s_k (the likelihood-ratio identity; Sec. 3.3 Eqs.
+ * (sampling), (sampling2) give the path's law).
  * Host outputs; synchronises `stream`. */
 sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_days, double* per_rep,
                                 double* out, void* stream);
@@ -199,7 +201,7 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
  * likelihood-ratio identity d E[f] / d theta = E[f d log p / d theta] (log p the
  * path's log-likelihood under the direct method's law, Sec. 3.3 Eqs. (sampling),
  * (sampling2)), estimated by the sample covariance of f and the score.
- * moments: host double [n_chunks][n_days][34], each chunk the out array of one
+ * moments: host double [n_chunks][n_days][42], each chunk the out array of one
  * sim_gradient_moments call (chunks of replicates, added in chunk order); R: the
  * total replicate count (>= 2); jac: host double [8][n_params], d theta_k / d
  * param_c for the 8 score terms of sim_score (e.g. the age-class ratios when one
@@ -207,8 +209,10 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
  *   mean_f [n_days]            = sum f / R,
  *   grad   [n_days][n_params]  = sum_k cov(f, s_k) jac[k][c],
  *                               cov = (sum f s_k - sum f sum s_k / R) / (R - 1),
- *   se     [n_days][n_params]  = sqrt(sum_k (Var(f s_k) / R) jac[k][c]^2),
- *                               Var(f s_k) = max(sum (f s_k)^2 / R - (sum f s_k / R)^2, 0)
+ *   se     [n_days][n_params]  = sqrt(sum_k (V_k / R) jac[k][c]^2), V_k the variance of the
+ *                               centred product (f - mean f) s_k from the moment sums,
+ *                               max(E[(f - mu)^2 s_k^2] - E[(f - mu) s_k]^2, 0) (the score's
+ *                               mean is zero; covariances between terms are left out)
  * (any output may be NULL).  Host arithmetic only; no handle, no device.
  * Errors: SIM_E_INVALID_ARG (n_chunks < 1, n_days < 0, n_params < 1, R < 2, a
  * NULL input). */
@@ -222,7 +226,7 @@ sim_status sim_gradient_estimate(const double* moments, int32_t n_chunks, int32_
  * framework's caching pool, an application with a fixed memory budget) or that
  * must avoid the device synchronisation and fragmentation an allocation can
  * cause.  Its scratch is one fixed array in the library's device image (about
- * 650 KiB on every GPU that loads the library, kept until exit), which limits a
+ * 690 KiB on every GPU that loads the library, kept until exit), which limits a
  * call to at most 8192 replicates and 512 days; larger requests return
  * SIM_E_INVALID_ARG.  Every call looks the array's address up on the current
  * device; with lazy module loading (the CUDA default) the first lookup on a
@@ -363,6 +367,20 @@ sim_status sim_debug_batch_stall(sim_handle* h, int32_t until, int64_t spin_limi
  * the last enable; host arrays of 3 entries. */
 sim_status sim_profile(sim_handle* h, int32_t enable);
 sim_status sim_profile_read(sim_handle* h, double* ms, int64_t* launches);
+
+/* FP64 pipe throughput of the current device, measured: a kernel whose threads
+ * each run 8 independent chains of one binary64 instruction kind (kind 0: fused
+ * multiply-add, kind 1: add) for `iters` iterations, over a whole number of waves
+ * (blocks per SM from the occupancy API x SMs); best of three timed launches
+ * after one warm-up, CUDA events on the legacy default stream.  Writes the
+ * instruction-lanes retired per second (*lane_ops_per_s; one FMA counts as one)
+ * and the best launch's time (*ms, may be NULL).  The paper has no counterpart:
+ * this is the denominator of the stochastic step's arithmetic roofline, since the
+ * simulation's specification is binary64 arithmetic (Sec. 3.3 Eqs. (sampling),
+ * (sampling2)).  Allocates and frees a few KB of device memory; synchronous.
+ * Errors: SIM_E_INVALID_ARG (kind not 0 or 1, iters < 1, NULL output),
+ * SIM_E_CUDA. */
+sim_status sim_fp64_peak(int32_t kind, int64_t iters, double* lane_ops_per_s, double* ms);
 
 /* Test hook (not part of the simulation path): evaluates the library's
  * -log(u) for u = (2 j + 1) 2^-53 on the GPU, for n device inputs j (uint64)

@@ -19,6 +19,8 @@ _LOCK = threading.Lock()
 HEADER = pathlib.Path(__file__).resolve().parent.parent / "include" / "episim.h"
 
 SIM_OK, SIM_E_INVALID_ARG, SIM_E_OOM, SIM_E_CUDA, SIM_E_UNDERFLOW, SIM_E_TIMEOUT, SIM_E_STATE = range(7)
+# moment sums per day written by sim_gradient_moments (see include/episim.h)
+N_MOMENTS = 42
 SIM_HOST, SIM_DEVICE = 0, 1
 FLAG_PHI_PRE_EVENT, FLAG_SCORE, FLAG_SCORE_REVERSE = 1, 2, 4
 STATUS_NAMES = {0: "SIM_OK", 1: "SIM_E_INVALID_ARG", 2: "SIM_E_OOM", 3: "SIM_E_CUDA",
@@ -105,6 +107,7 @@ def load_library(build_if_missing: bool = True):
             "sim_gradient_moments": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_estimate": [pd, i32, i32, i64, pd, i32, pd, pd, pd],
+            "sim_fp64_peak": [i32, i64, pd, pd],
             "sim_run_batch": [P(vp), i32, pi32, vp],
             "sim_set_option": [vp, i32, i64],
             "sim_set_regions": [vp, pi32, i32],
@@ -169,7 +172,7 @@ def _check(L, h, status):
 
 def gradient_estimate(chunks, R: int, jac):
     """The score-function estimate from moment sums (sim_gradient_estimate):
-    chunks [n_chunks, F, 34] (each a sim_gradient_moments result, added in chunk
+    chunks [n_chunks, F, 42] (each a sim_gradient_moments result, added in chunk
     order), R replicates in all, jac [8, P].  Returns mean_f [F], grad [F, P],
     se [F, P]."""
     L = load_library()
@@ -186,6 +189,18 @@ def gradient_estimate(chunks, R: int, jac):
     if st != SIM_OK:
         raise SimError(st, "sim_gradient_estimate: invalid arguments")
     return mean_f, grad, se
+
+
+def fp64_peak(kind: int = 0, iters: int = 1 << 16):
+    """Measured FP64 instruction-lane throughput of the current device (lane-ops/s)
+    and the best launch's time in ms (sim_fp64_peak; kind 0 = FMA, 1 = add)."""
+    L = load_library()
+    v = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    st = L.sim_fp64_peak(int(kind), int(iters), ctypes.byref(v), ctypes.byref(ms))
+    if st != SIM_OK:
+        raise SimError(st, "sim_fp64_peak failed")
+    return v.value, ms.value
 
 
 def current_stream():
@@ -316,9 +331,9 @@ class Sim:
         _check(self.L, self.h, self.L.sim_score_backward(self.h, self._stream(stream)))
 
     def gradient_moments(self, days, stream=None):
-        """Returns (moments [n_days, 34], per-replicate scores [R, 8])."""
+        """Returns (moments [n_days, 42], per-replicate scores [R, 8])."""
         d = np.ascontiguousarray(days, np.int32)
-        out = np.zeros((d.size, 34), np.float64)
+        out = np.zeros((d.size, N_MOMENTS), np.float64)
         per = np.zeros((self.R, 8), np.float64)
         _check(self.L, self.h, self.L.sim_gradient_moments(self.h, _p(d, ctypes.c_int32), d.size,
                                                            _p(per, ctypes.c_double), _p(out, ctypes.c_double),

@@ -1440,7 +1440,7 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
   if (n_days > h->moments_cap) {
     cudaFree(h->d_moments); cudaFree(h->d_days);
     h->d_moments = nullptr; h->d_days = nullptr; h->moments_cap = 0;
-    CK(h, dalloc(&h->d_moments, (size_t)n_days * 34), "moments allocation");
+    CK(h, dalloc(&h->d_moments, (size_t)n_days * kMoments), "moments allocation");
     CK(h, dalloc(&h->d_days, (size_t)n_days), "moments allocation");
     h->moments_cap = n_days;
   }
@@ -1449,7 +1449,7 @@ sim_status sim_gradient_moments(sim_handle* h, const int32_t* days, int32_t n_da
                                 h->cfg.n_replicates, h->cfg.max_days, h->d_per_rep, h->d_moments, st),
      "gradient moments launch");
   if (per_rep) CK(h, cudaMemcpyAsync(per_rep, h->d_per_rep, (size_t)h->cfg.n_replicates * kScoreTerms * 8, cudaMemcpyDeviceToHost, st), "copy scores");
-  if (n_days > 0) CK(h, cudaMemcpyAsync(out, h->d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st), "copy moments");
+  if (n_days > 0) CK(h, cudaMemcpyAsync(out, h->d_moments, (size_t)n_days * kMoments * 8, cudaMemcpyDeviceToHost, st), "copy moments");
   CK(h, cudaStreamSynchronize(st), "stream synchronize");
   return check_latched(h);
 }
@@ -1458,20 +1458,25 @@ sim_status sim_gradient_estimate(const double* moments, int32_t n_chunks, int32_
                                  const double* jac, int32_t n_params, double* mean_f, double* grad,
                                  double* se) {
   if (!moments || !jac || n_chunks < 1 || n_days < 0 || n_params < 1 || R < 2) return SIM_E_INVALID_ARG;
-  constexpr int kM = 34;
+  constexpr int kM = kMoments;
   const double dR = (double)R;
   for (int i = 0; i < n_days; ++i) {
     double m[kM] = {0};
     for (int c = 0; c < n_chunks; ++c)
       for (int q = 0; q < kM; ++q) m[q] += moments[((size_t)c * n_days + i) * kM + q];
     const double sf = m[0];
-    if (mean_f) mean_f[i] = sf / dR;
+    const double mu = sf / dR;
+    if (mean_f) mean_f[i] = mu;
     double cov[kScoreTerms], var8[kScoreTerms];
     for (int k = 0; k < kScoreTerms; ++k) {
-      const double s_k = m[2 + 4 * k], fs_k = m[4 + 4 * k], fs2_k = m[5 + 4 * k];
+      const double s_k = m[2 + 4 * k], s2_k = m[3 + 4 * k], fs_k = m[4 + 4 * k], fs2_k = m[5 + 4 * k];
+      const double fss_k = m[2 + 4 * kScoreTerms + k];
       cov[k] = (fs_k - sf * s_k / dR) / (dR - 1.0);
-      const double mean_fs = fs_k / dR;
-      const double v = fs2_k / dR - mean_fs * mean_fs;
+      // variance of the centred product (f - mu) s_k, whose mean the covariance
+      // estimates (the score has mean zero): E[(f - mu)^2 s^2] - (E[(f - mu) s])^2
+      const double e2 = (fs2_k - 2.0 * mu * fss_k + mu * mu * s2_k) / dR;
+      const double e1 = (fs_k - mu * s_k) / dR;
+      const double v = e2 - e1 * e1;
       var8[k] = (v > 0.0 ? v : 0.0) / dR;
     }
     for (int c = 0; c < n_params; ++c) {

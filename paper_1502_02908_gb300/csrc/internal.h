@@ -23,6 +23,10 @@ static_assert(sizeof(DevParams) == 128, "DevParams layout");
 
 // Score-function accumulators per node: [upsilon_1..3, gamma_1..3, beta, alpha].
 constexpr int kScoreTerms = 8;
+// Moment sums per listed day of the score-function gradient (sim_gradient_moments):
+// sum f, sum f^2; per score term k: sum s_k, sum s_k^2, sum f s_k, sum (f s_k)^2;
+// then per k: sum f s_k^2.
+constexpr int kMoments = 2 + 5 * kScoreTerms;
 
 struct SsaArgs {
   int32_t* counts;            // [R][Nc][N]

@@ -33,7 +33,7 @@ namespace episim {
 constexpr int kMaxReplicates = 8192;
 constexpr int kMaxDays = 512;
 constexpr size_t kPerRepBytes = (size_t)kMaxReplicates * kScoreTerms * sizeof(double);  // 512 KiB
-constexpr size_t kMomentBytes = (size_t)kMaxDays * 34 * sizeof(double);                 // 136 KiB
+constexpr size_t kMomentBytes = (size_t)kMaxDays * kMoments * sizeof(double);           // 168 KiB
 constexpr size_t kDayBytes = (size_t)kMaxDays * sizeof(int32_t);                        // 2 KiB
 constexpr size_t kScratchBytes = kPerRepBytes + kMomentBytes + kDayBytes;
 
@@ -82,7 +82,7 @@ extern "C" sim_status sim_gradient_moments_noalloc(sim_handle* h, const int32_t*
   if (e == cudaSuccess && per_rep)
     e = cudaMemcpyAsync(per_rep, d_per_rep, (size_t)hv.R * kScoreTerms * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && n_days > 0)
-    e = cudaMemcpyAsync(out, d_moments, (size_t)n_days * 34 * 8, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(out, d_moments, (size_t)n_days * kMoments * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return handle_cuda_fail(h, e, "gradient moments (no-alloc)");
   return handle_check_latched(h);

@@ -193,8 +193,8 @@ __global__ void k_gradient_moments(const double* per_rep, const unsigned long lo
   const int di = blockIdx.x;
   if (di >= n_days || threadIdx.x != 0) return;
   const int d = days[di];
-  double m[34];
-  for (int i = 0; i < 34; ++i) m[i] = 0.0;
+  double m[kMoments];
+  for (int i = 0; i < kMoments; ++i) m[i] = 0.0;
   for (int r = 0; r < R; ++r) {
     const unsigned long long I = prev_i[(size_t)r * max_days + d], T = prev_n[(size_t)r * max_days + d];
     const double f = T ? __ddiv_rn((double)I, (double)T) : 0.0;
@@ -206,9 +206,10 @@ __global__ void k_gradient_moments(const double* per_rep, const unsigned long lo
       m[3 + 4 * k] = __dadd_rn(m[3 + 4 * k], __dmul_rn(sk, sk));
       m[4 + 4 * k] = __dadd_rn(m[4 + 4 * k], fs);
       m[5 + 4 * k] = __dadd_rn(m[5 + 4 * k], __dmul_rn(fs, fs));
+      m[2 + 4 * kScoreTerms + k] = __dadd_rn(m[2 + 4 * kScoreTerms + k], __dmul_rn(fs, sk));
     }
   }
-  for (int i = 0; i < 34; ++i) out[(size_t)di * 34 + i] = m[i];
+  for (int i = 0; i < kMoments; ++i) out[(size_t)di * kMoments + i] = m[i];
 }
 
 cudaError_t launch_gradient_moments(const double* score, const unsigned long long* prev_i,

@@ -24,7 +24,7 @@ import numpy as np
 from . import binding as B
 from . import workloads as W
 
-N_MOMENTS = 34
+N_MOMENTS = B.N_MOMENTS
 
 
 @dataclasses.dataclass
@@ -63,7 +63,7 @@ def _slice_params(p: W.Params, r0, r1):
 
 
 def run_moments(spec: GradientSpec, per_replicate=False, rank=0, world=1):
-    """Runs every replicate (in chunks), returns (moment sums [n_chunks, F, 34], one
+    """Runs every replicate (in chunks), returns (moment sums [n_chunks, F, 42], one
     row per chunk in replicate order, R, optional per-replicate (f [R, F], score
     [R, 8])).  With world > 1 (torch.distributed initialised, one GPU per rank)
     each rank runs its contiguous replicate range and the ranks' chunk rows are
@@ -114,7 +114,7 @@ def jacobian(ratios):
 def estimate(moments, R, ratios):
     """E[f], the gradient with respect to theta and its standard error, computed by
     the library (sim_gradient_estimate) from the moment sums of run_moments
-    ([n_chunks, F, 34] or [F, 34]).  Returns mean_f [F], grad [F, 4], se [F, 4]."""
+    ([n_chunks, F, 42] or [F, 42]).  Returns mean_f [F], grad [F, 4], se [F, 4]."""
     return B.gradient_estimate(moments, R, jacobian(ratios))
 
 

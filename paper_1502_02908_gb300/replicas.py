@@ -43,7 +43,7 @@ def allreduce_moments(moments: np.ndarray, group=None):
 
 
 def allgather_rows(rows: np.ndarray, group=None):
-    """Gathers every rank's moment rows [n_rows, F, 34] (the same shape on every
+    """Gathers every rank's moment rows [n_rows, F, 42] (the same shape on every
     rank) and concatenates them in rank order (torch.distributed; gloo or nccl)."""
     import torch
     import torch.distributed as dist

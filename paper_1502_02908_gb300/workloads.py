@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -321,32 +322,60 @@ def latin_hypercube(rng, n, lo, hi):
     return lo + u * (hi - lo)
 
 
+def _uniform_events_by_day(rng, N, T, n_events, mix, max_count=5):
+    """The law of _uniform_events without its sort: i.i.d. events with uniform day
+    and node (destination uniform != node) listed stably by day.  Sorting i.i.d.
+    records by day leaves the other fields i.i.d. and independent of the days, and
+    the number of events on each day multinomial, so the days are drawn as
+    multinomial counts and every other field in list order."""
+    per_day = rng.multinomial(n_events, np.full(T, 1.0 / T))
+    day = np.repeat(np.arange(T, dtype=np.int32), per_day)
+    kinds = np.searchsorted(np.cumsum(mix)[:-1], rng.random(n_events), side="right")
+    node = rng.integers(0, N, size=n_events, dtype=np.int32)
+    dest = rng.integers(0, N - 1, size=n_events, dtype=np.int32)
+    dest += (dest >= node)
+    count = rng.integers(1, max_count + 1, size=n_events, dtype=np.int32)
+    kind = np.array([EXIT, ENTER, EXTERNAL], np.int32)[kinds]
+    cls = np.where(kind == ENTER, 0, -1).astype(np.int32)
+    dest = np.where(kind == EXTERNAL, dest, -1).astype(np.int32)
+    return Events(day, kind, node, dest, count, cls)
+
+
 def uneven_batch(n_inst=512, N_lo=100, N_hi=50_000, T_lo=90, T_hi=1460, events_per_node_year=80,
-                 seed=5, R=1):
+                 seed=5, R=1, threads=None):
     """Instances mixing SISe and SISe3 (probability 1/2 each), node counts
     log-uniform in [N_lo, N_hi], horizons uniform in [T_lo, T_hi], events at
     `events_per_node_year` with the plain SISe type mix (exit/enter/external
     50/30/20 %, no aging), and parameters from an n_inst-point Latin hypercube over
     log(upsilon, gamma, beta, alpha) in [0.5, 1.5] x (0.0357, 0.1, 0.005, 1.0).
     SISe3 instances use one (upsilon, gamma) for the three age classes.  Herds are
-    U{20..200}, 5% infected (SISe3: split 20/20/60 by age)."""
+    U{20..200}, 5% infected (SISe3: split 20/20/60 by age).  The instance
+    scalars come from one stream; each instance's arrays from a child stream of
+    its own (numpy SeedSequence.spawn), so instances are generated in parallel
+    (`threads`, default all cores) with the same result."""
+    import concurrent.futures as cf
     rng = np.random.Generator(np.random.PCG64(seed))
     base = np.log([0.0357, 0.1, 0.005, 1.0])
     lhs = np.exp(latin_hypercube(rng, n_inst, base + np.log(0.5), base + np.log(1.5)))
-    out = []
-    for i in range(n_inst):
-        model = SISE if rng.random() < 0.5 else SISE3
-        N = int(round(math.exp(rng.uniform(math.log(N_lo), math.log(N_hi)))))
-        T = int(rng.integers(T_lo, T_hi + 1))
-        herd = rng.integers(20, 201, size=N)
-        u0 = _initial_counts(model, herd)
+    model = np.where(rng.random(n_inst) < 0.5, SISE, SISE3)
+    Ns = np.rint(np.exp(rng.uniform(math.log(N_lo), math.log(N_hi), size=n_inst))).astype(np.int64)
+    Ts = rng.integers(T_lo, T_hi + 1, size=n_inst)
+    children = np.random.SeedSequence(seed).spawn(n_inst)
+
+    def make(i):
+        crng = np.random.Generator(np.random.PCG64(children[i]))
+        m, N, T = int(model[i]), int(Ns[i]), int(Ts[i])
+        herd = crng.integers(20, 201, size=N)
+        u0 = _initial_counts(m, herd)
         n_ev = int(round(events_per_node_year * N * T / 365))
-        ev = _uniform_events(rng, N, T, n_ev, (0.5, 0.3, 0.2)) if n_ev else Events.empty()
+        ev = _uniform_events_by_day(crng, N, T, n_ev, (0.5, 0.3, 0.2)) if n_ev else Events.empty()
         ups, gam, bet, alp = lhs[i]
-        params = Params.broadcast(R, [ups] * (3 if model == SISE3 else 1), [gam] * (3 if model == SISE3 else 1),
-                                  alp, bet, 1e-6)
-        out.append(Workload(f"uneven_{i}", model, N, T, R, u0, np.zeros(N), params, ev, seed=1000 + i))
-    return out
+        na = 3 if m == SISE3 else 1
+        params = Params.broadcast(R, [ups] * na, [gam] * na, alp, bet, 1e-6)
+        return Workload(f"uneven_{i}", m, N, T, R, u0, np.zeros(N), params, ev, seed=1000 + i)
+
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        return list(ex.map(make, range(n_inst)))
 
 
 # ------------------------------------------------------------------ general model

@@ -32,6 +32,17 @@ def test_score_gradient_agrees_with_central_differences():
     assert np.all(z < 3.0), (g, fd, se, fd_se)
 
 
+def test_score_gradient_agrees_with_central_differences_at_gradient_workload_size():
+    # the 10,000-node, 365-day gradient workload on 1,024 replicates: final
+    # prevalence and the week-26 prevalence, all four parameters
+    w = W.sise_gradient(R=1024)
+    spec = G.GradientSpec(w, np.array([364, 181]), chunk=1024)
+    _, g, se = G.score_gradient(spec)
+    fd, fd_se = G.fd_gradient(spec, rel_h=1e-3)
+    z = np.abs(g - fd) / np.sqrt(se ** 2 + fd_se ** 2)
+    assert np.all(z < 3.0), (g, fd, se, fd_se)
+
+
 def _sis_law(N, I0, ups, gam, alpha, beta, eps, phi0, T):
     def P(phi):
         Q = np.zeros((N + 1, N + 1))

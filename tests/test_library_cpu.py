@@ -198,27 +198,29 @@ def test_create_rejects_unknown_flags_and_reserved():
 def test_gradient_estimate_is_the_sample_covariance_of_f_and_the_score():
     """sim_gradient_estimate, from chunked moment sums, against numpy's sample
     covariance of the raw per-replicate values and the standard error of the mean
-    of f * s."""
+    of the centred product (f - mean f) * s."""
     rng = np.random.default_rng(11)
     R, F = 300, 3
     f = rng.random((R, F))
     s = rng.normal(size=(R, 8)) + 0.3 * f[:, :1]
     chunks = []
     for r0, r1 in ((0, 100), (100, 250), (250, 300)):
-        m = np.zeros((F, 34))
+        m = np.zeros((F, B.N_MOMENTS))
         fc, sc = f[r0:r1], s[r0:r1]
         m[:, 0] = fc.sum(0); m[:, 1] = (fc ** 2).sum(0)
         for k in range(8):
             m[:, 2 + 4 * k] = sc[:, k].sum(); m[:, 3 + 4 * k] = (sc[:, k] ** 2).sum()
             m[:, 4 + 4 * k] = (fc * sc[:, k:k + 1]).sum(0)
             m[:, 5 + 4 * k] = ((fc * sc[:, k:k + 1]) ** 2).sum(0)
+            m[:, 34 + k] = (fc * sc[:, k:k + 1] ** 2).sum(0)
         chunks.append(m)
     J = rng.random((8, 4))
     mean_f, grad, se = B.gradient_estimate(np.stack(chunks), R, J)
     np.testing.assert_allclose(mean_f, f.mean(0), rtol=1e-13)
     cov = np.array([[np.cov(f[:, i], s[:, k])[0, 1] for k in range(8)] for i in range(F)])
     np.testing.assert_allclose(grad, cov @ J, rtol=1e-10)
-    fs = f[:, :, None] * s[:, None, :]                            # [R, F, 8]
+    # the standard error of the mean of the centred product (f - mean f) s
+    fs = (f - f.mean(0))[:, :, None] * s[:, None, :]              # [R, F, 8]
     se8 = fs.std(0) / np.sqrt(R)
     np.testing.assert_allclose(se, np.sqrt((se8 ** 2) @ (J ** 2)), rtol=1e-10)
     with pytest.raises(B.SimError):

@@ -13,11 +13,11 @@ from paper_1502_02908_gb300 import workloads as W
 
 
 def _moments(w, r0, r1):
-    """Per-replicate final prevalence and score sums -> the 34 moment sums, in
+    """Per-replicate final prevalence and score sums -> the 42 moment sums, in
     replicate order (same definition as the library's moment kernel)."""
     import oracle
     res = oracle.run(w, replicates=range(r0, r1), score=True)
-    m = np.zeros(34)
+    m = np.zeros(42)
     for i in range(r1 - r0):
         f = res.prev_i[i, -1] / res.prev_n[i, -1]
         s = res.score[i].sum(axis=1)
@@ -25,6 +25,7 @@ def _moments(w, r0, r1):
         for k in range(8):
             m[2 + 4 * k] += s[k]; m[3 + 4 * k] += s[k] ** 2
             m[4 + 4 * k] += f * s[k]; m[5 + 4 * k] += (f * s[k]) ** 2
+            m[34 + k] += f * s[k] ** 2
     return m
 
 

@@ -32,7 +32,7 @@ def _cuda():
 
 def _noalloc(s, days):
     d = np.ascontiguousarray(days, np.int32)
-    out = np.zeros((d.size, 34), np.float64)
+    out = np.zeros((d.size, B.N_MOMENTS), np.float64)
     per = np.zeros((s.R, 8), np.float64)
     st = s.L.sim_gradient_moments_noalloc(s.h, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), d.size,
                                           per.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
