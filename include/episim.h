@@ -239,6 +239,43 @@ sim_status sim_gradient_estimate(const double* moments, int32_t n_chunks, int32_
 sim_status sim_gradient_moments_noalloc(sim_handle* h, const int32_t* days, int32_t n_days,
                                         double* per_rep, double* out, void* stream);
 
+/* Node-sharded single replicate (Sec. 3.4's split of the nodes over workers with
+ * a daily exchange for the crossing events, and Sec. 5's multi-node outlook),
+ * one handle per rank, each holding the whole state:
+ *   sim_shard restricts the handle's stochastic step, phi update and statistics
+ *   (Eqs. (numstep3), (numstep5)) to nodes [node_lo, node_hi); the daily
+ *   statistics and the transition counter then sum those nodes only, while every
+ *   rank applies the whole event list (Eq. (numstep4)) and counts every event.
+ *   Call at day 0, after sim_load_events or before; not with SIM_FLAG_SCORE or
+ *   region statistics (SIM_E_STATE), not in sim_run_batch.  Synchronises the device.
+ *   A day then runs in two halves: sim_run_day_stochastic (the stochastic step of
+ *   the current day, own nodes) and sim_run_day_events (the day's events on every
+ *   node, then the phi update and statistics of the own nodes; the day advances).
+ *   Between them the ranks exchange the post-stochastic-step counts of the herds
+ *   the day's events touch: sim_touched_count(h, day) herds (host; -1 for a bad
+ *   day), listed by sim_touched_nodes (host int32 [n]); sim_pack_touched writes
+ *   their counts as device int32 [R][Nc][n] into the caller's buffer; the caller
+ *   gathers the world ranks' packs back to back in rank order (e.g. an all-gather
+ *   over NCCL) and sim_unpack_touched takes, for every touched herd, the counts
+ *   from the pack of the rank that owns it -- bounds: host int32 [world + 1],
+ *   rank k owns [bounds[k], bounds[k+1]), bounds[0] = 0, bounds[world] = N,
+ *   non-decreasing.  With every rank doing this the counts of each rank's own
+ *   nodes equal a single handle's sim_run_days bit for bit (the random numbers
+ *   are keyed by node, day and event position, not by rank).  The two halves and
+ *   the pack and unpack are asynchronous on `stream`; sim_unpack_touched
+ *   synchronises it before reading `bounds`.  While a day is between its halves,
+ *   sim_run_days, sim_state and sim_set_state return SIM_E_STATE.  Any handle
+ *   (sharded or not) may run its days in halves; with no exchange an unsharded
+ *   handle's halves equal sim_run_days. */
+sim_status sim_shard(sim_handle* h, int32_t node_lo, int32_t node_hi);
+sim_status sim_run_day_stochastic(sim_handle* h, void* stream);
+sim_status sim_run_day_events(sim_handle* h, void* stream);
+int32_t sim_touched_count(const sim_handle* h, int32_t day);
+sim_status sim_touched_nodes(const sim_handle* h, int32_t day, int32_t* nodes);
+sim_status sim_pack_touched(sim_handle* h, int32_t* dev_out, void* stream);
+sim_status sim_unpack_touched(sim_handle* h, const int32_t* dev_in, int32_t world, const int32_t* bounds,
+                              void* stream);
+
 /* Back to day 0 with the initial counts and phi of sim_create (the initial
  * state X_0, Y_0 of Sec. 3.1's time discretisation); statistics and score
  * cleared.  clear_events = 1 also drops the loaded events (Sec. 3.2's lists

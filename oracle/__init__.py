@@ -90,6 +90,12 @@ def load(path):
     L.orc_apply_events.restype = ctypes.c_int
     L.orc_apply_events.argtypes = [P(OrcCfg), P(ctypes.c_int32), ctypes.c_int64, P(ctypes.c_int64)] + \
                                   [P(ctypes.c_int32)] * 6 + [P(OrcCounters)]
+    L.orc_ssa_nodes.restype = ctypes.c_int
+    L.orc_ssa_nodes.argtypes = [P(OrcCfg), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_int32, P(OrcCounters)]
+    L.orc_phi_nodes.restype = ctypes.c_int
+    L.orc_phi_nodes.argtypes = [P(OrcCfg), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_int32]
     L.go_run.restype = ctypes.c_int
     L.go_run.argtypes = [P(GoModel), P(GoCfg), P(ctypes.c_int32), P(ctypes.c_double), ctypes.c_int32,
                          ctypes.c_int32, ctypes.c_int64] + [P(ctypes.c_int32)] * 7 + [P(OrcCounters)]
@@ -223,6 +229,28 @@ def apply_events(w, counts, pos, events, replicate=0, underflow_error=False):
     L.orc_apply_events(ctypes.byref(cfg), _ptr(counts, ctypes.c_int32), len(pos), _ptr(pos, ctypes.c_int64),
                        *[_ptr(a, ctypes.c_int32) for a in arr], ctypes.byref(ctr))
     return (ctr.transitions, ctr.events_applied, ctr.events_clamped, ctr.events_skipped)
+
+
+def ssa_nodes(w, counts, phi, day, v0, v1, replicate=0):
+    """The stochastic step of day ``day`` for nodes [v0, v1) of ``counts`` [Nc, N]
+    (in place) with phi [N] frozen; returns the transitions fired."""
+    L = lib()
+    cfg = make_cfg(w.model, w.N, w.params, replicate, w.seed)
+    ctr = OrcCounters()
+    if L.orc_ssa_nodes(ctypes.byref(cfg), _ptr(counts, ctypes.c_int32), _ptr(phi, ctypes.c_double), int(day),
+                       int(v0), int(v1), ctypes.byref(ctr)) != 0:
+        raise ValueError("oracle rejected its arguments")
+    return ctr.transitions
+
+
+def phi_nodes(w, counts, phi, day, v0, v1, replicate=0):
+    """The continuous-state update after day ``day`` for nodes [v0, v1) of phi [N]
+    (in place) from ``counts`` [Nc, N]."""
+    L = lib()
+    cfg = make_cfg(w.model, w.N, w.params, replicate, w.seed)
+    if L.orc_phi_nodes(ctypes.byref(cfg), _ptr(counts, ctypes.c_int32), _ptr(phi, ctypes.c_double), int(day),
+                       int(v0), int(v1)) != 0:
+        raise ValueError("oracle rejected its arguments")
 
 
 def _go_model(m):

@@ -523,3 +523,28 @@ int orc_apply_events(const orc_cfg* c, int32_t* counts, int64_t n, const int64_t
         apply_event(c, counts, N, pos[k], day[k], kind[k], node[k], dest[k], count[k], cls[k], ctr);
     return 0;
 }
+
+/* The steps of one day of orc_run, separately and over a node range: the
+ * stochastic step (Eq. numstep3) of nodes [v0, v1) on day `day` with their
+ * frozen phi, and the continuous-state update (Eq. numstep5) of nodes [v0, v1)
+ * from the current counts.  orc_run is these two around the day's events
+ * (orc_apply_events) for every node; the split is used to check a trajectory whose
+ * nodes are divided among several workers.  No score terms. */
+int orc_ssa_nodes(const orc_cfg* c, int32_t* counts, const double* phi, int32_t day, int32_t v0,
+                  int32_t v1, orc_counters* ctr)
+{
+    const int32_t N = c->n_nodes;
+    if (v0 < 0 || v1 < v0 || v1 > N || day < 0 || c->score) return -1;
+    orc_counters local = {0, 0, 0, 0};
+    if (!ctr) ctr = &local;
+    for (int32_t v = v0; v < v1; ++v) ctr->transitions += ssa_node_day(c, counts, N, v, day, phi[v], NULL);
+    return 0;
+}
+
+int orc_phi_nodes(const orc_cfg* c, const int32_t* counts, double* phi, int32_t day, int32_t v0, int32_t v1)
+{
+    const int32_t N = c->n_nodes;
+    if (v0 < 0 || v1 < v0 || v1 > N || day < 0) return -1;
+    for (int32_t v = v0; v < v1; ++v) phi[v] = phi_next(c, counts, N, v, day, phi[v], NULL);
+    return 0;
+}

@@ -108,6 +108,12 @@ def load_library(build_if_missing: bool = True):
             "sim_gradient_moments_noalloc": [vp, pi32, i32, pd, pd, vp],
             "sim_gradient_estimate": [pd, i32, i32, i64, pd, i32, pd, pd, pd],
             "sim_fp64_peak": [i32, i64, pd, pd],
+            "sim_shard": [vp, i32, i32],
+            "sim_run_day_stochastic": [vp, vp],
+            "sim_run_day_events": [vp, vp],
+            "sim_touched_nodes": [vp, i32, pi32],
+            "sim_pack_touched": [vp, vp, vp],
+            "sim_unpack_touched": [vp, vp, i32, pi32, vp],
             "sim_run_batch": [P(vp), i32, pi32, vp],
             "sim_set_option": [vp, i32, i64],
             "sim_set_regions": [vp, pi32, i32],
@@ -144,6 +150,8 @@ def load_library(build_if_missing: bool = True):
         L.gen_group_nodes.restype = ctypes.c_int32
         L.sim_warp_nodes.argtypes = [vp]
         L.sim_warp_nodes.restype = ctypes.c_int32
+        L.sim_touched_count.argtypes = [vp, i32]
+        L.sim_touched_count.restype = ctypes.c_int32
         L.sim_debug_schedule_size.argtypes = [vp]
         L.sim_debug_schedule_size.restype = ctypes.c_int64
         _LIB = L
@@ -409,6 +417,37 @@ class Sim:
     def set_clock_margin(self, k):
         """Speculative clock margin 2^-k, k in [0, 17] (0: exact clock only)."""
         _check(self.L, self.h, self.L.sim_set_option(self.h, 3, int(k)))
+
+    def shard(self, node_lo, node_hi):
+        """Restricts the stochastic step, phi update and statistics to nodes
+        [node_lo, node_hi) (sim_shard); events still apply to every node."""
+        _check(self.L, self.h, self.L.sim_shard(self.h, int(node_lo), int(node_hi)))
+
+    def run_day_stochastic(self, stream=None):
+        _check(self.L, self.h, self.L.sim_run_day_stochastic(self.h, self._stream(stream)))
+
+    def run_day_events(self, stream=None):
+        _check(self.L, self.h, self.L.sim_run_day_events(self.h, self._stream(stream)))
+
+    def touched_count(self, day):
+        return int(self.L.sim_touched_count(self.h, int(day)))
+
+    def touched_nodes(self, day):
+        out = np.zeros(max(self.touched_count(day), 0), np.int32)
+        _check(self.L, self.h, self.L.sim_touched_nodes(self.h, int(day), _p(out, ctypes.c_int32)))
+        return out
+
+    def pack_touched(self, dev_out, stream=None):
+        """Counts of the current day's touched herds, int32 [R][Nc][n], into the
+        device buffer at address dev_out."""
+        _check(self.L, self.h, self.L.sim_pack_touched(self.h, ctypes.c_void_p(dev_out), self._stream(stream)))
+
+    def unpack_touched(self, dev_in, bounds, stream=None):
+        """Every touched herd's counts from its owner's pack: dev_in = the ranks'
+        packs back to back in rank order; bounds [world + 1] the ranks' node ranges."""
+        b = np.ascontiguousarray(bounds, np.int32)
+        _check(self.L, self.h, self.L.sim_unpack_touched(self.h, ctypes.c_void_p(dev_in), b.size - 1,
+                                                         _p(b, ctypes.c_int32), self._stream(stream)))
 
     def profile(self, enable=True):
         _check(self.L, self.h, self.L.sim_profile(self.h, 1 if enable else 0))

@@ -44,6 +44,13 @@ struct sim_handle {
   int32_t moments_cap = 0;
   int32_t* d_u0 = nullptr;          // [Nc][N] master copy for resets
   int32_t* d_order = nullptr;       // node order of the stochastic step
+  int32_t n_order = 0;              // nodes in it: the handle's node range
+  int32_t node_lo = 0, node_hi = 0; // nodes whose stochastic step and phi update this handle runs
+                                    // (sim_shard; default every node); events apply to all nodes
+  int32_t phase = 0;                // 1: the current day's stochastic step ran alone
+                                    // (sim_run_day_stochastic), its event step is due
+  int32_t* d_pack_touched = nullptr;// scratch of sim_unpack_touched: rank bounds
+  int32_t pack_bounds_cap = 0;
   int32_t n_big = 0;                // leading nodes of the order simulated one per warp
   int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
   int32_t group_threshold = -1;     // herd size from which a node gets an 8-lane group (-1: automatic)
@@ -199,6 +206,9 @@ void free_all(sim_handle* h) {
   cudaFree(h->d_prev_n); cudaFree(h->d_ctr); cudaFree(h->d_err); cudaFree(h->d_score);
   cudaFree(h->d_tang); cudaFree(h->d_u0); cudaFree(h->d_phi0); cudaFree(h->d_order);
   cudaFree(h->d_traj); cudaFree(h->d_per_rep); cudaFree(h->d_moments); cudaFree(h->d_days);
+  cudaFree(h->d_pack_touched);
+  h->d_pack_touched = nullptr;
+  h->pack_bounds_cap = 0;
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -283,7 +293,9 @@ SsaArgs ssa_args(sim_handle* h) {
   a.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
   a.sm_count = h->sm_count;
   a.overlap = h->overlap;
-  a.n_list = h->cfg.n_nodes;
+  a.n_list = h->n_order;
+  a.node_lo = h->node_lo;
+  a.node_hi = h->node_hi;
   a.skip = nullptr;
   return a;
 }
@@ -339,8 +351,9 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   std::vector<int64_t> herd(N, 0);
   for (int c = 0; c < h->nc; ++c)
     for (int v = 0; v < N; ++v) herd[v] += h->u0[(size_t)c * N + v];
-  std::vector<int32_t> order(N);
-  for (int v = 0; v < N; ++v) order[v] = v;
+  const int n_own = h->node_hi - h->node_lo;
+  std::vector<int32_t> order(n_own);
+  for (int i = 0; i < n_own; ++i) order[i] = h->node_lo + i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return herd[a] > herd[b]; });
   int32_t thr = threshold;
   if (thr < 0) {
@@ -354,11 +367,13 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   }
   int32_t nb = 0, nm = 0;
   if (!(h->cfg.flags & SIM_FLAG_SCORE)) {
-    while (nb < N && herd[order[nb]] >= thr) ++nb;
-    while (nb + nm < N && herd[order[nb + nm]] >= gthr) ++nm;
+    while (nb < n_own && herd[order[nb]] >= thr) ++nb;
+    while (nb + nm < n_own && herd[order[nb + nm]] >= gthr) ++nm;
   }
   if (!h->d_order) CK(h, dalloc(&h->d_order, (size_t)N), "node order allocation");
-  CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "node order upload");
+  if (n_own > 0)
+    CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)n_own * 4, cudaMemcpyHostToDevice), "node order upload");
+  h->n_order = n_own;
   h->n_big = nb;
   h->n_mid = nm;
   h->eff_group_threshold = (h->cfg.flags & SIM_FLAG_SCORE) ? (1 << 30) : gthr;
@@ -1064,6 +1079,8 @@ sim_status create_impl(const sim_config* cfg, const int32_t* u0, const double* p
     delete h;
     return s;
   }
+  h->node_lo = 0;
+  h->node_hi = N;
   sim_status s = reset_state(h);
   if (s == SIM_OK) s = set_order(h, -1);
   if (s != SIM_OK) {
@@ -1184,32 +1201,68 @@ sim_status sim_schedule_events(int32_t n_nodes, int32_t model, int32_t max_days,
 extern "C" {
 
 // Enqueues the launches of days [d0, d0 + ndays) on st (no state change).
-static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStream_t st) {
-  const bool score = (h->cfg.flags & SIM_FLAG_SCORE) != 0;
-  SsaArgs a = ssa_args(h);
-  EvArgs ev{};
+// Arguments of the three event-step kernels of a handle.
+struct DayEventArgs {
+  EvArgs ev;
+  EvSmemArgs es;
+  EvDfArgs df;
+};
+
+static DayEventArgs day_event_args(sim_handle* h) {
+  DayEventArgs E{};
+  EvArgs& ev = E.ev;
+  EvSmemArgs& es = E.es;
+  EvDfArgs& df = E.df;
   ev.counts = h->d_counts; ev.rec = h->d_rec; ev.lvl_start = h->d_lvl_start; ev.day_lvl = h->d_day_lvl;
   ev.ctr = h->d_ctr; ev.err = h->d_err; ev.seed = h->cfg.seed; ev.rep_base = h->cfg.replicate_base;
   ev.N = h->cfg.n_nodes; ev.R = h->cfg.n_replicates; ev.Nc = h->nc;
   ev.underflow_error = h->cfg.underflow_policy == SIM_UNDERFLOW_ERROR;
-  EvSmemArgs es{};
   es.counts = h->d_counts; es.rec = h->d_rec_slot; es.lvl_start = h->d_lvl_start; es.day_lvl = h->d_day_lvl;
   es.touched = h->d_touched; es.day_touch = h->d_day_touch; es.ctr = h->d_ctr; es.err = h->d_err;
   es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
   es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
-  EvDfArgs df{};
   df.counts = h->d_counts; df.rec = h->d_rec_df; df.wait = h->d_wait_df; df.thr_off = h->d_thr_off;
   df.touched = h->d_touched_df; df.blk_meta = h->d_blk_meta; df.thr_id = h->d_thr_id; df.ctr = h->d_ctr;
   df.err = h->d_err; df.seed = h->cfg.seed; df.rep_base = h->cfg.replicate_base;
   df.N = h->cfg.n_nodes; df.R = h->cfg.n_replicates; df.Nc = h->nc; df.underflow_error = ev.underflow_error;
   df.spin_limit = 1 << 24;
   df.overlap = h->overlap;
+  return E;
+}
+
+// The event step of day d (nothing when the day has no events): the
+// owner-computes kernel where the day's largest block fits in shared memory,
+// else the level-staged kernel, else the global-memory one.
+static sim_status launch_day_events(sim_handle* h, DayEventArgs& E, int32_t d, cudaStream_t st) {
+  if (!(h->events_loaded && h->day_lvl[(size_t)d + 1] > h->day_lvl[(size_t)d])) return SIM_OK;
+  if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
+    E.df.day = d;
+    E.df.nblk = h->day_nblk[(size_t)d];
+    E.df.blk0 = h->day_blk0[(size_t)d];
+    E.df.smem_bytes = h->day_df[(size_t)d];
+    CK(h, traced(h, 1, st, [&] { return launch_events_day_df(E.df, h->n_age, st); }), "event step launch");
+  } else if (h->event_variant != 1 && h->day_smem[(size_t)d] > 0) {
+    E.es.day = d;
+    E.es.smem_bytes = h->day_smem[(size_t)d];
+    CK(h, traced(h, 1, st, [&] { return launch_events_day_smem(E.es, h->n_age, st); }), "event step launch");
+  } else {
+    E.ev.day = d;
+    CK(h, traced(h, 1, st, [&] { return launch_events_day(E.ev, h->n_age, st); }), "event step launch");
+  }
+  return SIM_OK;
+}
+
+static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStream_t st) {
+  const bool score = (h->cfg.flags & SIM_FLAG_SCORE) != 0;
+  SsaArgs a = ssa_args(h);
+  DayEventArgs E = day_event_args(h);
   // Split day step: after a day d with events, the stochastic step of day d + 1
   // runs as two launches -- the herds d's events leave untouched, on the side
   // stream as soon as day d's stochastic step is complete (alongside d's event
   // step), and the touched herds after the event step; the side launch is joined
   // before the event step of day d + 1.  Without events the day is one launch.
-  const bool split = h->split && !score && h->events_loaded && h->d_skip && h->d_tlist && h->n_regions == 0;
+  const bool split = h->split && !score && h->events_loaded && h->d_skip && h->d_tlist && h->n_regions == 0 &&
+                     h->node_lo == 0 && h->node_hi == h->cfg.n_nodes;
   const size_t words = ((size_t)h->cfg.n_nodes + 31) / 32;
   if (split && !h->side) {
     CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "side stream");
@@ -1248,21 +1301,9 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
          "stochastic step launch");
       CK(h, cudaEventRecord(h->ev_join, h->side), "join");
     }
-    if (has_events(d)) {
-      if (h->event_variant == 0 && h->day_df[(size_t)d] > 0) {
-        df.day = d;
-        df.nblk = h->day_nblk[(size_t)d];
-        df.blk0 = h->day_blk0[(size_t)d];
-        df.smem_bytes = h->day_df[(size_t)d];
-        CK(h, traced(h, 1, st, [&] { return launch_events_day_df(df, h->n_age, st); }), "event step launch");
-      } else if (h->event_variant != 1 && h->day_smem[(size_t)d] > 0) {
-        es.day = d;
-        es.smem_bytes = h->day_smem[(size_t)d];
-        CK(h, traced(h, 1, st, [&] { return launch_events_day_smem(es, h->n_age, st); }), "event step launch");
-      } else {
-        ev.day = d;
-        CK(h, traced(h, 1, st, [&] { return launch_events_day(ev, h->n_age, st); }), "event step launch");
-      }
+    {
+      const sim_status es = launch_day_events(h, E, d, st);
+      if (es != SIM_OK) return es;
     }
     if (h->n_regions > 0)                            // region totals of the state after day d
       CK(h, launch_region_day(h->d_counts, h->d_reg_nodes, h->d_reg_off, h->cfg.n_nodes, h->cfg.n_replicates,
@@ -1275,6 +1316,7 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
 
 sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   if (!h) return SIM_E_INVALID_ARG;
+  if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
   if (ndays < 0 || (int64_t)h->day + ndays > h->cfg.max_days)
     return fail(h, SIM_E_INVALID_ARG, "ndays %d from day %d passes max_days %d", ndays, h->day, h->cfg.max_days);
   if (ndays == 0) return SIM_OK;
@@ -1349,9 +1391,110 @@ sim_status sim_sync(sim_handle* h, void* stream) {
   return check_latched(h);
 }
 
+sim_status sim_shard(sim_handle* h, int32_t node_lo, int32_t node_hi) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (node_lo < 0 || node_hi < node_lo || node_hi > h->cfg.n_nodes)
+    return fail(h, SIM_E_INVALID_ARG, "node range [%d, %d) outside [0, %d]", node_lo, node_hi, h->cfg.n_nodes);
+  if (h->day != 0 || h->phase) return fail(h, SIM_E_STATE, "a node range is set at day 0");
+  if (h->cfg.flags & SIM_FLAG_SCORE) return fail(h, SIM_E_STATE, "score mode runs every node");
+  if (h->n_regions > 0) return fail(h, SIM_E_STATE, "region statistics need every node");
+  CK(h, cudaDeviceSynchronize(), "synchronize");
+  h->node_lo = node_lo;
+  h->node_hi = node_hi;
+  return set_order(h, h->warp_threshold);
+}
+
+sim_status sim_run_day_stochastic(sim_handle* h, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
+  if (h->day >= h->cfg.max_days) return fail(h, SIM_E_INVALID_ARG, "day %d is max_days", h->day);
+  if (h->cfg.flags & SIM_FLAG_SCORE) return fail(h, SIM_E_STATE, "score mode runs whole days (sim_run_days)");
+  if (h->n_regions > 0) return fail(h, SIM_E_STATE, "region statistics run whole days (sim_run_days)");
+  cudaStream_t st = (cudaStream_t)stream;
+  SsaArgs a = ssa_args(h);
+  a.day = h->day;
+  a.prologue = 0;
+  CK(h, traced(h, 0, st, [&] { return launch_ssa_day(a, h->n_age, false, st); }), "stochastic step launch");
+  h->phase = 1;
+  return SIM_OK;
+}
+
+sim_status sim_run_day_events(sim_handle* h, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (!h->phase) return fail(h, SIM_E_STATE, "no stochastic step of day %d ran (sim_run_day_stochastic)", h->day);
+  cudaStream_t st = (cudaStream_t)stream;
+  DayEventArgs E = day_event_args(h);
+  const sim_status s = launch_day_events(h, E, h->day, st);
+  if (s != SIM_OK) return s;
+  SsaArgs a = ssa_args(h);
+  a.day = h->day;
+  CK(h, traced(h, 2, st, [&] { return launch_finalize(a, h->n_age, false, st); }), "phi update launch");
+  h->phase = 0;
+  h->day += 1;
+  return SIM_OK;
+}
+
+int32_t sim_touched_count(const sim_handle* h, int32_t day) {
+  if (!h || day < 0 || day >= h->cfg.max_days) return -1;
+  if (!h->events_loaded) return 0;
+  return h->day_touch_host[(size_t)day + 1] - h->day_touch_host[(size_t)day];
+}
+
+sim_status sim_touched_nodes(const sim_handle* h, int32_t day, int32_t* nodes) {
+  if (!h || !nodes || day < 0 || day >= h->cfg.max_days) return SIM_E_INVALID_ARG;
+  if (!h->events_loaded) return SIM_OK;
+  const int32_t b = h->day_touch_host[(size_t)day], e = h->day_touch_host[(size_t)day + 1];
+  for (int32_t i = b; i < e; ++i) nodes[i - b] = h->touched_host[(size_t)i];
+  return SIM_OK;
+}
+
+sim_status sim_pack_touched(sim_handle* h, int32_t* dev_out, void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (!h->phase) return fail(h, SIM_E_STATE, "pack after the day's stochastic step (sim_run_day_stochastic)");
+  const int32_t n_t = sim_touched_count(h, h->day);
+  if (n_t <= 0) return SIM_OK;
+  if (!dev_out) return fail(h, SIM_E_INVALID_ARG, "null output buffer");
+  const int32_t b = h->day_touch_host[(size_t)h->day];
+  CK(h, launch_pack_touched(h->d_counts, h->d_touched + b, n_t, h->cfg.n_nodes,
+                            (int64_t)h->cfg.n_replicates * h->nc, dev_out, (cudaStream_t)stream), "pack launch");
+  return SIM_OK;
+}
+
+sim_status sim_unpack_touched(sim_handle* h, const int32_t* dev_in, int32_t world, const int32_t* bounds,
+                              void* stream) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (!h->phase) return fail(h, SIM_E_STATE, "unpack after the day's stochastic step (sim_run_day_stochastic)");
+  if (world < 1 || world > (1 << 16) || !bounds) return fail(h, SIM_E_INVALID_ARG, "world must be in [1, 65536]");
+  if (bounds[0] != 0 || bounds[world] != h->cfg.n_nodes)
+    return fail(h, SIM_E_INVALID_ARG, "bounds must run from 0 to n_nodes");
+  for (int k = 0; k < world; ++k)
+    if (bounds[k + 1] < bounds[k]) return fail(h, SIM_E_INVALID_ARG, "bounds must not decrease");
+  const int32_t n_t = sim_touched_count(h, h->day);
+  if (n_t <= 0) return SIM_OK;
+  if (!dev_in) return fail(h, SIM_E_INVALID_ARG, "null input buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (world + 1 > h->pack_bounds_cap) {
+    CK(h, cudaStreamSynchronize(st), "stream synchronize");
+    cudaFree(h->d_pack_touched);
+    h->d_pack_touched = nullptr;
+    h->pack_bounds_cap = 0;
+    CK(h, dalloc(&h->d_pack_touched, (size_t)world + 1), "bounds allocation");
+    h->pack_bounds_cap = world + 1;
+  }
+  // a synchronous copy: the caller's host array may go away when this call returns
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  CK(h, cudaMemcpy(h->d_pack_touched, bounds, ((size_t)world + 1) * 4, cudaMemcpyHostToDevice), "bounds upload");
+  const int32_t b = h->day_touch_host[(size_t)h->day];
+  CK(h, launch_unpack_touched(h->d_counts, h->d_touched + b, n_t, h->cfg.n_nodes,
+                              (int64_t)h->cfg.n_replicates * h->nc, dev_in, h->d_pack_touched, world, st),
+     "unpack launch");
+  return SIM_OK;
+}
+
 sim_status sim_state(sim_handle* h, int32_t* counts, double* phi, int32_t* day, int32_t where,
                      void* stream) {
   if (!h) return SIM_E_INVALID_ARG;
+  if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
   if (where != SIM_HOST && where != SIM_DEVICE) return fail(h, SIM_E_INVALID_ARG, "where must be SIM_HOST or SIM_DEVICE");
   cudaStream_t st = (cudaStream_t)stream;
   const cudaMemcpyKind k = where == SIM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -1365,6 +1508,7 @@ sim_status sim_state(sim_handle* h, int32_t* counts, double* phi, int32_t* day, 
 sim_status sim_set_state(sim_handle* h, const int32_t* counts, const double* phi, int32_t day,
                          int32_t where, void* stream) {
   if (!h || !counts || !phi) return SIM_E_INVALID_ARG;
+  if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
   if (where != SIM_HOST && where != SIM_DEVICE) return fail(h, SIM_E_INVALID_ARG, "where must be SIM_HOST or SIM_DEVICE");
   if (day < 0 || day > h->cfg.max_days) return fail(h, SIM_E_INVALID_ARG, "day %d out of range", day);
   if (where == SIM_HOST) {
@@ -1507,6 +1651,8 @@ sim_status sim_set_params(sim_handle* h, const sim_params* p) {
 
 sim_status sim_set_regions(sim_handle* h, const int32_t* region_of_node, int32_t n_regions) {
   if (!h) return SIM_E_INVALID_ARG;
+  if (n_regions > 0 && (h->node_lo != 0 || h->node_hi != h->cfg.n_nodes))
+    return fail(h, SIM_E_STATE, "region statistics need every node (the handle is sharded)");
   CK(h, cudaDeviceSynchronize(), "synchronize");
   free_regions(h);
   free_graph(h);
@@ -1576,6 +1722,7 @@ sim_status sim_goal(sim_handle* h, const int64_t* ref, int32_t day0, int32_t nda
 sim_status sim_reset(sim_handle* h, int32_t clear_events) {
   if (!h) return SIM_E_INVALID_ARG;
   CK(h, cudaDeviceSynchronize(), "synchronize");
+  h->phase = 0;
   if (clear_events) { free_events(h); free_graph(h); }
   return reset_state(h);
 }
@@ -1610,6 +1757,8 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
   if (n == 0) return SIM_OK;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return fail(nullptr, SIM_E_INVALID_ARG, "handle %d is NULL", i);
+    if (hs[i]->phase || hs[i]->node_lo != 0 || hs[i]->node_hi != hs[i]->cfg.n_nodes)
+      return fail(hs[i], SIM_E_STATE, "handle %d is sharded or between the halves of a day", i);
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(nullptr, SIM_E_INVALID_ARG, "handle %d listed twice", i);
     const int32_t u = until ? until[i] : hs[i]->cfg.max_days;

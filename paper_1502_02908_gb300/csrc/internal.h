@@ -55,6 +55,7 @@ struct SsaArgs {
   int32_t overlap;            // launch with programmatic stream serialization
   int32_t max_per_sm;         // dealt grid: at most this many blocks per SM (0: as many as fit)
   int32_t max_warps;          // dealt grid: warps per block (0: 8)
+  int32_t node_lo, node_hi;   // nodes this handle simulates without an order list: [node_lo, node_hi)
 };
 
 // One scheduled event, 16 bytes: node, dest, position in the day-stable order,
@@ -166,6 +167,11 @@ cudaError_t launch_goal(const unsigned long long* s1, const unsigned long long* 
 cudaError_t launch_events_day(const EvArgs& a, int n_age, cudaStream_t st);
 // After the last day of a call: phi update (post-event mode) and statistics of day a.day.
 cudaError_t launch_finalize(const SsaArgs& a, int n_age, bool score, cudaStream_t st);
+// node-sharded exchange (shard.cu): counts of the day's touched herds, [R][Nc][n_t]
+cudaError_t launch_pack_touched(const int32_t* counts, const int32_t* touched, int n_t, int N, int64_t planes,
+                                int32_t* out, cudaStream_t st);
+cudaError_t launch_unpack_touched(int32_t* counts, const int32_t* touched, int n_t, int N, int64_t planes,
+                                  const int32_t* in, const int32_t* bounds, int world, cudaStream_t st);
 cudaError_t launch_debug_neglog(const uint64_t* j, double* out, int64_t n, cudaStream_t st);
 cudaError_t launch_debug_neglog_f32(const uint64_t* j, float* out, int64_t n, cudaStream_t st);
 

@@ -61,8 +61,9 @@ static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStre
         : launch_maybe_pdl(k_node_day_dealt<3>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a);
   }
   const int warp_blocks = (MODE == 0 && !score) ? a.warp_blocks : 0;
-  const int n_thread = a.N - ((MODE == 0 && !score && a.order) ? a.n_big : 0);
+  const int n_thread = (MODE == 0 && !score && a.order) ? a.n_list - a.n_big : a.node_hi - a.node_lo;
   const int bpr = warp_blocks + (n_thread + 255) / 256;
+  if (bpr <= 0) return cudaSuccess;                // an empty node range: nothing to run
   dim3 block(256), grid((unsigned)((int64_t)bpr * a.R));
   if (n_age == 1) {
     if (score) k_node_day<1, true, MODE><<<grid, block, 0, st>>>(a, bpr);

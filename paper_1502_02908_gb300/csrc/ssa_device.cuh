@@ -939,9 +939,14 @@ __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) 
     v = active ? a.order[wi] : 0;
   } else {
     const int i = (bx - ((MODE == 0 && !SCORE) ? a.warp_blocks : 0)) * blockDim.x + threadIdx.x;
-    const int base = (MODE == 0 && !SCORE && a.order) ? a.n_big : 0;
-    active = i + base < a.N;
-    v = active ? (a.order && MODE == 0 && !SCORE ? a.order[base + i] : i + base) : 0;
+    if (MODE == 0 && !SCORE && a.order) {
+      active = a.n_big + i < a.n_list;
+      v = active ? a.order[a.n_big + i] : 0;
+    } else {                                       // the handle's node range, in id order
+      v = a.node_lo + i;
+      active = v < a.node_hi;
+      if (!active) v = 0;
+    }
   }
   node_day_work<NA, SCORE, MODE>(a, r, v, active, warp_role ? kRoleWarp : kRoleThread);
 }

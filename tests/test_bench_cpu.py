@@ -30,22 +30,22 @@ def test_measured_peaks_is_a_mapping():
 
 
 class _W:
-    model, N, nc = 3, 37_000, 6
+    model, N, nc, T = 3, 37_000, 6, 1460
 
 
 def test_roofline_fraction_follows_from_its_inputs():
     # frac = (40 FP64 lane-ops per draw x (transitions + node-days) / launches)
-    #        / average traced launch time / measured peak
-    transitions, T, launches, ssa_ms, peak = 109_901_254, 1460, 1460, 14.6, 5.0e11
-    prof = {"ssa": (ssa_ms, launches), "events": (8.0, 1460), "finalize": (0.01, 1)}
-    r = bench.ssa_roofline(_W, 1, T, transitions, prof, peak, ms_per_step=28.9, hbm_peak=6762.6)
-    avg_s = ssa_ms / 1000 / launches
-    ops = 40 * (transitions + _W.N * T) / launches
+    #        / average launch time of the stochastic step timed alone / measured peak
+    transitions, T, peak = 109_901_254, 1460, 5.0e11
+    alone = {"ms_per_launch": 0.0146, "launches": T, "transitions": transitions, "node_days": _W.N * T}
+    r = bench.ssa_roofline(_W, 1, alone, peak, ms_per_step=28.9, hbm_peak=6762.6)
+    avg_s = 0.0146 / 1000
+    ops = 40 * (transitions + _W.N * T) / T
     assert abs(r["frac"] - ops / avg_s / peak) < 1e-12
     assert abs(r["achieved"] * 1e9 - ops / avg_s) < 1e-3
-    assert r["fits_in_ms_per_step"] and abs(r["avg_launch_x_launches_ms"] - ssa_ms) < 1e-9
+    assert r["fits_in_ms_per_step"]
     assert abs(r["hbm"]["achieved"] - 64 * _W.N / avg_s / 1e9) < 1e-9
-    spec = (15 * transitions + 34 * _W.N * T) / launches / avg_s / peak
+    spec = (15 * transitions + 34 * _W.N * T) / T / avg_s / peak
     assert abs(r["frac_spec_count"] - spec) < 1e-12
-    r2 = bench.ssa_roofline(_W, 1, T, transitions, prof, peak, ms_per_step=10.0, hbm_peak=6762.6)
+    r2 = bench.ssa_roofline(_W, 1, alone, peak, ms_per_step=10.0, hbm_peak=6762.6)
     assert not r2["fits_in_ms_per_step"]
