@@ -342,12 +342,21 @@ int32_t sim_warp_nodes(const sim_handle* h);
  *     (two launches per day on the stream), SIM_LAUNCH_GRAPH (the call's launch
  *     sequence captured once as a CUDA graph, keyed by start day and day count,
  *     and replayed), SIM_LAUNCH_PERSISTENT (one persistent batch-kernel launch,
- *     synchronous).  Under tracing (sim_profile), SIM_LAUNCH_GRAPH runs a
+ *     synchronous), SIM_LAUNCH_FLOW (the call's days as one dataflow launch with
+ *     no per-day barrier: warps take the stochastic step of groups of herds and
+ *     the events of groups of transfer-graph components from one counter in day
+ *     order, each waiting only for its own herds' previous half-day -- a herd
+ *     the day's events leave untouched starts its next day as soon as its own
+ *     day is done, as the paper's tasks do (Sec. 3.4, Alg. 2); the day's
+ *     components are built on the host at the first such call; bounded waits
+ *     return SIM_E_TIMEOUT from the next synchronising call; asynchronous; falls
+ *     back to stream launches in score mode, with region statistics or on a
+ *     node range).  Under tracing (sim_profile), SIM_LAUNCH_GRAPH runs a
  *     one-shot graph with the event records inside, the other modes stream
  *     launches. */
 enum { SIM_OPT_WARP_THRESHOLD = 1, SIM_OPT_LAUNCH = 2, SIM_OPT_CLOCK_MARGIN = 3, SIM_OPT_OVERLAP = 4,
        SIM_OPT_SPLIT = 5, SIM_OPT_GROUP_THRESHOLD = 6 };
-enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2 };
+enum { SIM_LAUNCH_STREAM = 0, SIM_LAUNCH_GRAPH = 1, SIM_LAUNCH_PERSISTENT = 2, SIM_LAUNCH_FLOW = 3 };
 sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value);
 
 /* Replaces every replicate's parameters (same layout and checks as sim_create;
@@ -388,6 +397,14 @@ sim_status sim_goal(sim_handle* h, const int64_t* ref, int32_t day0, int32_t nda
  * SIM_E_TIMEOUT (the batch's state is then undefined); device errors of a
  * handle are latched in it as for sim_run_days. */
 sim_status sim_run_batch(sim_handle** handles, int32_t n, const int32_t* until, void* stream);
+
+/* Test hook for the dataflow loop's failure path: runs ndays days from the
+ * current day (>= 1) with SIM_LAUNCH_FLOW, but with the first stochastic-step
+ * unit's herd (replicate 0) held at readiness 0, so that its wait makes
+ * spin_limit polls, gives up and the launch returns; the call synchronises and
+ * returns SIM_E_TIMEOUT with the device usable.  The handle's state is undefined
+ * afterwards (sim_reset or sim_set_state it). */
+sim_status sim_debug_flow_stall(sim_handle* h, int32_t ndays, int64_t spin_limit);
 
 /* Test hooks for the batch kernel's failure path: sets the number of polls a
  * dependency wait makes before giving up (default ~2 s worth); runs h (whose

@@ -122,6 +122,7 @@ def load_library(build_if_missing: bool = True):
             "sim_goal": [vp, pi64, i32, i32, pd, pd],
             "sim_debug_batch_spin_limit": [i64],
             "sim_debug_batch_stall": [vp, i32, i64],
+            "sim_debug_flow_stall": [vp, i32, i64],
             "sim_profile_read": [vp, pd, pi64],
             "gen_model_check": [P(GenModel), P(ctypes.c_uint32)],
             "gen_create": [P(GenModel), P(GenConfig), pi32, pd, pd, pd, P(vp)],
@@ -362,7 +363,7 @@ class Sim:
         _check(self.L, self.h, self.L.sim_tune(self.h, int(warp_herd_threshold)))
         return self.L.sim_warp_nodes(self.h)
 
-    LAUNCH = {"stream": 0, "graph": 1, "persistent": 2}
+    LAUNCH = {"stream": 0, "graph": 1, "persistent": 2, "flow": 3}
 
     def set_launch(self, mode):
         _check(self.L, self.h, self.L.sim_set_option(self.h, 2, self.LAUNCH[mode]))

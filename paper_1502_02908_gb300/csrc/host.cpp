@@ -51,6 +51,30 @@ struct sim_handle {
                                     // (sim_run_day_stochastic), its event step is due
   int32_t* d_pack_touched = nullptr;// scratch of sim_unpack_touched: rank bounds
   int32_t pack_bounds_cap = 0;
+  // dataflow day loop (SIM_LAUNCH_FLOW)
+  std::vector<int4> ev_host;          // events of days < max_days in day-stable order:
+                                      // {node, dest (-1 unless a transfer), position, packed}
+  std::vector<int64_t> ev_first;      // [max_days + 1]
+  bool flow_built = false;
+  std::vector<int32_t> flow_day_comp; // [max_days + 1] first component of each day
+  int4* d_fl_rec = nullptr;
+  int32_t* d_fl_cev = nullptr;
+  int32_t* d_fl_cnode = nullptr;
+  int32_t* d_fl_cnoff = nullptr;
+  int32_t* d_fl_day_comp = nullptr;
+  int32_t* d_fl_day_long = nullptr;
+  std::vector<int32_t> flow_day_long; // [max_days] components of >= kFlowLong events
+  int32_t* d_fl_cunit = nullptr;      // per component: its herds' distinct units
+  int32_t* d_fl_cuoff = nullptr;
+  int32_t* d_fl_K = nullptr;          // [max_days + 1][U1] cumulative components per unit
+  int32_t flow_U1 = 0;
+  std::vector<int32_t> order_host;    // the node order of the stochastic step (host copy)
+  unsigned* d_rdy = nullptr;          // [R][U1] unit completion counters
+  unsigned long long* d_flow_next = nullptr;
+  int32_t* d_flow_abort = nullptr;
+  long long* d_item_off = nullptr;
+  int32_t item_cap = 0;
+  long long flow_spin_limit = 1ll << 22;  // ~2 s of polling per wait
   int32_t n_big = 0;                // leading nodes of the order simulated one per warp
   int32_t warp_threshold = -1;      // herd size from which a node gets a warp (-1: automatic)
   int32_t group_threshold = -1;     // herd size from which a node gets an 8-lane group (-1: automatic)
@@ -154,7 +178,27 @@ void free_split(sim_handle* h) {
   h->tlist_nbig.clear();
 }
 
+void free_flow(sim_handle* h) {
+  cudaFree(h->d_fl_rec); cudaFree(h->d_fl_cev); cudaFree(h->d_fl_cnode); cudaFree(h->d_fl_cnoff);
+  cudaFree(h->d_fl_day_comp); cudaFree(h->d_fl_day_long);
+  cudaFree(h->d_fl_cunit); cudaFree(h->d_fl_cuoff); cudaFree(h->d_fl_K);
+  cudaFree(h->d_rdy);
+  h->d_rdy = nullptr;
+  h->d_fl_cunit = nullptr; h->d_fl_cuoff = nullptr; h->d_fl_K = nullptr;
+  h->flow_U1 = 0;
+  h->d_fl_day_long = nullptr;
+  h->flow_day_long.clear();
+  h->d_fl_rec = nullptr; h->d_fl_cev = nullptr; h->d_fl_cnode = nullptr; h->d_fl_cnoff = nullptr;
+  h->d_fl_day_comp = nullptr;
+  h->flow_day_comp.clear();
+  h->flow_built = false;
+}
+
 void free_events(sim_handle* h) {
+  free_flow(h);
+  h->ev_host.clear();
+  h->ev_host.shrink_to_fit();
+  h->ev_first.clear();
   cudaFree(h->d_rec); cudaFree(h->d_lvl_start); cudaFree(h->d_day_lvl);
   cudaFree(h->d_rec_slot); cudaFree(h->d_touched); cudaFree(h->d_day_touch); cudaFree(h->d_day_smem);
   cudaFree(h->d_rec_df); cudaFree(h->d_wait_df); cudaFree(h->d_thr_off); cudaFree(h->d_touched_df);
@@ -209,6 +253,10 @@ void free_all(sim_handle* h) {
   cudaFree(h->d_pack_touched);
   h->d_pack_touched = nullptr;
   h->pack_bounds_cap = 0;
+  free_flow(h);
+  cudaFree(h->d_flow_next); cudaFree(h->d_flow_abort); cudaFree(h->d_item_off);
+  h->d_flow_next = nullptr; h->d_flow_abort = nullptr; h->d_item_off = nullptr;
+  h->item_cap = 0;
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
@@ -374,6 +422,8 @@ sim_status set_order(sim_handle* h, int32_t threshold) {
   if (n_own > 0)
     CK(h, cudaMemcpy(h->d_order, order.data(), (size_t)n_own * 4, cudaMemcpyHostToDevice), "node order upload");
   h->n_order = n_own;
+  h->order_host.swap(order);
+  free_flow(h);
   h->n_big = nb;
   h->n_mid = nm;
   h->eff_group_threshold = (h->cfg.flags & SIM_FLAG_SCORE) ? (1 << 30) : gthr;
@@ -1170,6 +1220,21 @@ sim_status sim_load_events(sim_handle* h, int64_t n, const int32_t* day, const i
     if (e2 == cudaSuccess && T > 0) e2 = cudaMemcpy(h->d_day_smem, h->day_smem.data(), (size_t)T * 4, cudaMemcpyHostToDevice);
     if (e2 != cudaSuccess) { free_events(h); return cuda_fail(h, e2, "event upload"); }
   }
+  // the events of the run's days in day-stable order, for the dataflow schedule
+  try {
+    h->ev_first.assign((size_t)T + 1, 0);
+    for (int64_t e = 0; e < n; ++e)
+      if (day[e] < T) h->ev_first[(size_t)day[e] + 1]++;
+    for (int32_t d = 0; d < T; ++d) h->ev_first[(size_t)d + 1] += h->ev_first[(size_t)d];
+    h->ev_host.resize((size_t)h->ev_first[(size_t)T]);
+    std::vector<int64_t> fill(h->ev_first.begin(), h->ev_first.end() - 1);
+    for (int64_t e = 0; e < n; ++e) {
+      if (day[e] >= T) continue;
+      const int64_t s = fill[(size_t)day[e]]++;
+      const uint32_t packed = (uint32_t)kind[e] | ((uint32_t)(cls[e] + 1) << 2) | ((uint32_t)count[e] << 4);
+      h->ev_host[(size_t)s] = make_int4(node[e], kind[e] == SIM_EXTERNAL ? dest[e] : -1, (int32_t)s, (int32_t)packed);
+    }
+  } catch (...) { free_events(h); return fail(h, SIM_E_OOM, "host allocation"); }
   h->sched_order.swap(S.order);
   h->sched_level.swap(S.level);
   h->day_lvl.swap(S.day_lvl);
@@ -1314,6 +1379,208 @@ static sim_status enqueue_days(sim_handle* h, int32_t d0, int32_t ndays, cudaStr
   return SIM_OK;
 }
 
+// Dataflow schedule: per day, the connected components of the day's transfer
+// graph (union-find over the herds the events name), longest first (ties by first
+// event); per component its herds in order of first appearance (their slots) and
+// its events in day-stable order as {src slot, dst slot, position, packed}.
+static sim_status build_flow(sim_handle* h) {
+  free_flow(h);
+  const int N = h->cfg.n_nodes;
+  const int32_t T = h->cfg.max_days;
+  std::vector<int4> rec;
+  std::vector<int32_t> cev(1, 0), cnode, cnoff(1, 0), cunit, cuoff(1, 0);
+  std::vector<int32_t> day_comp((size_t)T + 1, 0), day_long((size_t)std::max<int32_t>(T, 1), 0);
+  // the stochastic-step unit of every herd of the node order (warp herds one each,
+  // group herds four to a unit, thread herds 32 to a unit)
+  const int nb = h->n_big, nm = h->n_mid, no = h->n_order;
+  const int U1 = nb + (nm + 3) / 4 + (no - nb - nm + 31) / 32;
+  std::vector<int32_t> K;
+  try {
+    std::vector<int32_t> unit_of(N, -1), ustamp((size_t)std::max(U1, 1), -1), kday((size_t)std::max(U1, 1), 0);
+    for (int i = 0; i < no; ++i) {
+      const int v = h->order_host[(size_t)i];
+      unit_of[v] = i < nb ? i : (i < nb + nm ? nb + (i - nb) / 4 : nb + (nm + 3) / 4 + (i - nb - nm) / 32);
+    }
+    K.assign(((size_t)T + 1) * (size_t)U1, 0);
+    rec.reserve(h->ev_host.size());
+    std::vector<int32_t> stamp(N, -1), local(N, 0), slot_of(N, -1);
+    std::vector<int32_t> par, first_ev, comp_of_root, ev_comp, order, count, fill, nodes_of;
+    std::vector<int32_t> lnode;                    // local index -> herd
+    for (int32_t d = 0; d < T; ++d) {
+      day_comp[(size_t)d] = (int32_t)(cev.size() - 1);
+      if (d > 0)
+        for (int u = 0; u < U1; ++u) {
+          K[(size_t)d * U1 + u] = K[(size_t)(d - 1) * U1 + u] + kday[(size_t)u];
+          kday[(size_t)u] = 0;
+        }
+      if (h->ev_first.empty()) continue;
+      const int64_t s0 = h->ev_first[(size_t)d], s1 = h->ev_first[(size_t)d + 1];
+      const int n = (int)(s1 - s0);
+      if (n == 0) continue;
+      lnode.clear();
+      par.clear();
+      auto loc = [&](int v) {
+        if (stamp[v] != d) { stamp[v] = d; local[v] = (int32_t)lnode.size(); lnode.push_back(v); par.push_back(local[v]); }
+        return local[v];
+      };
+      auto find = [&](int x) {
+        while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+        return x;
+      };
+      for (int64_t s = s0; s < s1; ++s) {
+        const int4 e = h->ev_host[(size_t)s];
+        const int a = loc(e.x);
+        if (e.y >= 0) {
+          const int b = loc(e.y);
+          const int ra = find(a), rb = find(b);
+          if (ra != rb) par[std::max(ra, rb)] = std::min(ra, rb);
+        }
+      }
+      // components in order of first event; event counts
+      comp_of_root.assign(lnode.size(), -1);
+      ev_comp.resize((size_t)n);
+      count.clear();
+      first_ev.clear();
+      for (int i = 0; i < n; ++i) {
+        const int rt = find(local[h->ev_host[(size_t)(s0 + i)].x]);
+        if (comp_of_root[rt] < 0) { comp_of_root[rt] = (int32_t)count.size(); count.push_back(0); first_ev.push_back(i); }
+        ev_comp[(size_t)i] = comp_of_root[rt];
+        count[(size_t)comp_of_root[rt]]++;
+      }
+      const int nc = (int)count.size();
+      order.resize((size_t)nc);
+      for (int c = 0; c < nc; ++c) order[(size_t)c] = c;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return count[a] > count[b]; });
+      // rank of each component in the sorted order, then the events bucketed by rank
+      std::vector<int32_t> rank((size_t)nc);
+      for (int c = 0; c < nc; ++c) rank[(size_t)order[(size_t)c]] = c;
+      fill.assign((size_t)nc + 1, 0);
+      for (int c = 0; c < nc; ++c) fill[(size_t)rank[(size_t)c] + 1] = count[(size_t)c];
+      for (int c = 0; c < nc; ++c) fill[(size_t)c + 1] += fill[(size_t)c];
+      std::vector<int32_t> evs((size_t)n);
+      {
+        std::vector<int32_t> f2(fill.begin(), fill.end() - 1);
+        for (int i = 0; i < n; ++i) evs[(size_t)f2[(size_t)rank[(size_t)ev_comp[(size_t)i]]]++] = i;
+      }
+      for (int c = 0; c < nc; ++c) day_long[(size_t)d] += count[(size_t)order[(size_t)c]] >= kFlowLong ? 1 : 0;
+      for (int c = 0; c < nc; ++c) {
+        const int32_t nbase = (int32_t)cnode.size();
+        int32_t k = 0;
+        for (int32_t j = fill[(size_t)c]; j < fill[(size_t)c + 1]; ++j) {
+          const int4 e = h->ev_host[(size_t)(s0 + evs[(size_t)j])];
+          auto slot = [&](int v) {
+            if (slot_of[v] < 0 || slot_of[v] >= k || cnode[(size_t)(nbase + slot_of[v])] != v) {
+              slot_of[v] = k++;
+              cnode.push_back(v);
+            }
+            return slot_of[v];
+          };
+          const int sx = slot(e.x);
+          const int sy = e.y >= 0 ? slot(e.y) : -1;
+          rec.push_back(make_int4(sx, sy, e.z, e.w));
+        }
+        cev.push_back((int32_t)rec.size());
+        cnoff.push_back((int32_t)cnode.size());
+        // the component's distinct units; each counts once towards the next day
+        const int32_t cid = (int32_t)cev.size() - 2;
+        for (int32_t j = nbase; j < (int32_t)cnode.size(); ++j) {
+          const int u = unit_of[cnode[(size_t)j]];
+          if (ustamp[(size_t)u] != cid) { ustamp[(size_t)u] = cid; cunit.push_back(u); kday[(size_t)u]++; }
+        }
+        cuoff.push_back((int32_t)cunit.size());
+      }
+    }
+    day_comp[(size_t)T] = (int32_t)(cev.size() - 1);
+    if (T > 0)
+      for (int u = 0; u < U1; ++u) K[(size_t)T * U1 + u] = K[(size_t)(T - 1) * U1 + u] + kday[(size_t)u];
+  } catch (...) { return fail(h, SIM_E_OOM, "host allocation"); }
+  if (rec.size() >= ((size_t)1 << 31) || cnode.size() >= ((size_t)1 << 31))
+    return fail(h, SIM_E_INVALID_ARG, "dataflow schedule exceeds 32-bit indices");
+  cudaError_t err = cudaSuccess;
+  auto up = [&](auto** dst, const auto& v, size_t elem) {
+    if (err == cudaSuccess) err = dalloc(dst, std::max<size_t>(v.size(), 1));
+    if (err == cudaSuccess && !v.empty()) err = cudaMemcpy(*dst, v.data(), v.size() * elem, cudaMemcpyHostToDevice);
+  };
+  up(&h->d_fl_rec, rec, sizeof(int4));
+  up(&h->d_fl_cev, cev, 4);
+  up(&h->d_fl_cnode, cnode, 4);
+  up(&h->d_fl_cnoff, cnoff, 4);
+  up(&h->d_fl_day_comp, day_comp, 4);
+  up(&h->d_fl_day_long, day_long, 4);
+  up(&h->d_fl_cunit, cunit, 4);
+  up(&h->d_fl_cuoff, cuoff, 4);
+  up(&h->d_fl_K, K, 4);
+  if (err == cudaSuccess) err = dalloc(&h->d_rdy, (size_t)h->cfg.n_replicates * std::max(U1, 1));
+  if (err == cudaSuccess && !h->d_flow_next) err = dalloc(&h->d_flow_next, 1);
+  if (err == cudaSuccess && !h->d_flow_abort) err = dalloc(&h->d_flow_abort, 1);
+  if (err != cudaSuccess) { free_flow(h); return cuda_fail(h, err, "dataflow schedule upload"); }
+  h->flow_day_comp.swap(day_comp);
+  h->flow_day_long.swap(day_long);
+  h->flow_U1 = U1;
+  h->flow_built = true;
+  return SIM_OK;
+}
+
+// Whether sim_run_days can take the dataflow loop (else it falls back to stream
+// launches): not in score mode, with region statistics, or on a node range.
+static bool flow_usable(const sim_handle* h) {
+  return !(h->cfg.flags & SIM_FLAG_SCORE) && h->n_regions == 0 && h->node_lo == 0 &&
+         h->node_hi == h->cfg.n_nodes;
+}
+
+// Days [d0, d0 + ndays) as one dataflow launch, then the phi update and statistics
+// of the last day.  stall (test hook): the first unit's first wait (replicate 0)
+// asks for a count that is never reached, so that it runs out.
+static sim_status enqueue_flow(sim_handle* h, int32_t d0, int32_t ndays, cudaStream_t st, long long spin_limit,
+                               bool stall = false) {
+  if (!h->flow_built) {
+    const sim_status s = build_flow(h);
+    if (s != SIM_OK) return s;
+  }
+  const int R = h->cfg.n_replicates;
+  const long long units = (long long)R * (h->n_big + (h->n_mid + 3) / 4 + (h->n_order - h->n_big - h->n_mid + 31) / 32);
+  std::vector<long long> item_off((size_t)ndays + 1, 0);
+  for (int32_t k = 0; k < ndays; ++k) {
+    const int32_t d = d0 + k;
+    const long long nc = h->flow_day_comp[(size_t)d + 1] - h->flow_day_comp[(size_t)d];
+    const long long nl = h->flow_day_long[(size_t)d];
+    item_off[(size_t)k + 1] = item_off[(size_t)k] + units + (long long)R * (nl + (nc - nl + 31) / 32);
+  }
+  if (ndays + 1 > h->item_cap) {
+    CK(h, cudaStreamSynchronize(st), "stream synchronize");
+    cudaFree(h->d_item_off);
+    h->d_item_off = nullptr;
+    h->item_cap = 0;
+    CK(h, dalloc(&h->d_item_off, (size_t)ndays + 1), "item table allocation");
+    h->item_cap = ndays + 1;
+  }
+  // a synchronous copy: the host table goes away when this call returns, and an
+  // earlier launch may still read the device table
+  CK(h, cudaStreamSynchronize(st), "stream synchronize");
+  CK(h, cudaMemcpy(h->d_item_off, item_off.data(), item_off.size() * sizeof(long long), cudaMemcpyHostToDevice),
+     "item table upload");
+  FlowArgs f{};
+  f.a.ssa = ssa_args(h);
+  f.a.ev = day_event_args(h).ev;
+  f.a.err_word = h->d_err;
+  f.rec = h->d_fl_rec; f.cev = h->d_fl_cev; f.cnode = h->d_fl_cnode; f.cnoff = h->d_fl_cnoff;
+  f.day_comp = h->d_fl_day_comp;
+  f.day_long = h->d_fl_day_long;
+  f.cunit = h->d_fl_cunit; f.cuoff = h->d_fl_cuoff; f.K = h->d_fl_K; f.U1 = h->flow_U1;
+  f.unit_cnt = h->d_rdy; f.next = h->d_flow_next; f.abort = h->d_flow_abort;
+  f.spin_limit = spin_limit;
+  f.stall_extra = stall ? (1u << 30) : 0u;
+  f.d0 = d0; f.ndays = ndays;
+  f.units = units;
+  f.item_off = h->d_item_off;
+  CK(h, traced(h, 0, st, [&] { return launch_flow(f, h->n_age, h->sm_count, st); }), "dataflow launch");
+  if (stall) return SIM_OK;
+  SsaArgs a = ssa_args(h);
+  a.day = d0 + ndays - 1;
+  CK(h, traced(h, 2, st, [&] { return launch_finalize(a, h->n_age, false, st); }), "phi update launch");
+  return SIM_OK;
+}
+
 sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   if (!h) return SIM_E_INVALID_ARG;
   if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
@@ -1324,6 +1591,12 @@ sim_status sim_run_days(sim_handle* h, int32_t ndays, void* stream) {
   const int32_t d0 = h->day;
   if (h->launch_mode == 2 && !h->profiling && h->n_regions > 0)
     return fail(h, SIM_E_STATE, "region statistics need the stream or graph launch mode");
+  if (h->launch_mode == SIM_LAUNCH_FLOW && flow_usable(h)) {
+    const sim_status s = enqueue_flow(h, d0, ndays, st, h->flow_spin_limit);
+    if (s != SIM_OK) return s;
+    h->day = d0 + ndays;
+    return SIM_OK;
+  }
   if (h->launch_mode == 2 && !h->profiling) {
     const int32_t until = d0 + ndays;
     sim_handle* one[1] = {h};
@@ -1893,6 +2166,18 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
   return SIM_OK;
 }
 
+sim_status sim_debug_flow_stall(sim_handle* h, int32_t ndays, int64_t spin_limit) {
+  if (!h) return SIM_E_INVALID_ARG;
+  if (h->phase) return fail(h, SIM_E_STATE, "the event step of day %d is due (sim_run_day_events)", h->day);
+  if (h->day < 1 || ndays < 1 || (int64_t)h->day + ndays > h->cfg.max_days || spin_limit < 1)
+    return fail(h, SIM_E_INVALID_ARG, "the stall needs day >= 1, ndays >= 1 within max_days, spin_limit >= 1");
+  if (!flow_usable(h)) return fail(h, SIM_E_STATE, "the handle cannot take the dataflow loop");
+  const sim_status s = enqueue_flow(h, h->day, ndays, nullptr, (long long)spin_limit, true);
+  if (s != SIM_OK) return s;
+  CK(h, cudaStreamSynchronize(nullptr), "stream synchronize");
+  return check_latched(h);
+}
+
 sim_status sim_debug_batch_spin_limit(int64_t limit) {
   if (limit < 1) return SIM_E_INVALID_ARG;
   g_batch_spin_limit = limit;
@@ -1931,7 +2216,7 @@ sim_status sim_set_option(sim_handle* h, int32_t option, int64_t value) {
     case SIM_OPT_WARP_THRESHOLD:
       return sim_tune(h, (int32_t)std::max<int64_t>(-1, std::min<int64_t>(value, 1 << 30)));
     case SIM_OPT_LAUNCH:
-      if (value < SIM_LAUNCH_STREAM || value > SIM_LAUNCH_PERSISTENT)
+      if (value < SIM_LAUNCH_STREAM || value > SIM_LAUNCH_FLOW)
         return fail(h, SIM_E_INVALID_ARG, "unknown launch mode %lld", (long long)value);
       CK(h, cudaDeviceSynchronize(), "synchronize");
       free_graph(h);

@@ -148,6 +148,42 @@ inline cudaError_t launch_maybe_pdl(void (*kernel)(P...), dim3 grid, dim3 block,
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 size_t events_df_smem_bytes(int64_t n_events, int64_t n_touched, int nc);
+
+// Dataflow day loop (flow.cu): one persistent kernel over a call's days; warps
+// take stochastic-step units and groups of 32 transfer-graph components from one
+// counter and wait on per-herd readiness words (half-days).
+constexpr int kFlowThreads = 256;
+constexpr int kFlowSlots = 8;     // herds of a component staged in a lane's shared-memory slots
+constexpr int kFlowLong = 4;      // components of at least this many events get a warp each
+struct FlowParts {
+  SsaArgs ssa;                    // the stochastic step (day and prologue set per item)
+  EvArgs ev;                      // the event step (counts, counters, error word, seed)
+  int32_t* err_word;              // the handle's latched error word
+};
+struct FlowArgs {
+  FlowParts a;
+  const int4* rec;                // per component, input order: {src slot, dst slot, position, packed}
+  const int32_t* cev;             // [components + 1] record offsets
+  const int32_t* cnode;           // component herds by slot
+  const int32_t* cnoff;           // [components + 1] offsets into cnode
+  const int32_t* day_comp;        // [max_days + 1] first component of each day (longest first)
+  const int32_t* day_long;        // [max_days] the day's components of >= kFlowLong events (they come first)
+  const int32_t* cunit;           // the distinct stochastic-step units of each component's herds
+  const int32_t* cuoff;           // [components + 1] offsets into cunit
+  const int32_t* K;               // [max_days + 1][U1]: components touching each unit before each day
+  int32_t U1;                     // stochastic-step units per replicate
+  unsigned* unit_cnt;             // [R][U1] completion counters
+  unsigned stall_extra;           // test hook: added to the first unit's first wait (0: none)
+  unsigned long long* next;       // item counter
+  int32_t* abort;
+  long long spin_limit;           // polls a wait makes before giving up
+  int32_t d0, ndays;
+  long long units;                // stochastic-step units per day (all replicates)
+  const long long* item_off;      // [ndays + 1] first item of each day of the call
+};
+// Clears the unit counters, the item counter and the abort flag, and launches
+// the persistent kernel on a resident grid (sms x blocks per SM).
+cudaError_t launch_flow(const FlowArgs& f, int n_age, int sms, cudaStream_t st);
 // Shared memory the staged event step needs for a day (0 if the day has no events).
 size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc);
 constexpr size_t kEventsSmemLimit = 220 * 1024;

@@ -4,12 +4,14 @@ captures day D's stochastic step).
 
     python -m paper_1502_02908_gb300.profile_case national --days 301
     python -m paper_1502_02908_gb300.profile_case batched --days 201
+    python -m paper_1502_02908_gb300.profile_case national --days 60 --launch flow
 
 Cases: ``national`` (SISe3, 37,000 herds, 3M events; warp path from 800
 animals, group path from 200, the bench's tuned shape), ``batched`` (the national
 network with 256 replicates, every herd on the per-thread path, as the bench
 runs it), ``general`` (SISe3 written in the general model).  Launches go to the
-stream one by one (no CUDA graph), so each kernel launch is capturable.
+stream one by one (no CUDA graph), so each kernel launch is capturable; with
+``--launch flow`` the days run as one dataflow launch.
 """
 from __future__ import annotations
 
@@ -21,6 +23,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["national", "batched", "general"])
     ap.add_argument("--days", type=int, default=301)
+    ap.add_argument("--launch", choices=["stream", "flow"], default="stream",
+                    help="stream: one launch per kernel and day; flow: one dataflow launch for all days")
     args = ap.parse_args(argv)
     import torch
     from . import binding as B
@@ -43,7 +47,7 @@ def main(argv=None):
         else:
             s.set_group_threshold(1 << 30)
             s.tune(1 << 30)
-    s.set_launch("stream")
+    s.set_launch(args.launch if args.case != "general" else "stream")
     s.run(w.T)
     torch.cuda.synchronize()
     s.close()
