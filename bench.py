@@ -312,7 +312,7 @@ def events_roofline(w, T, prof, hbm_peak):
                     "transfer-graph component, applied serially by one thread"}
 
 
-def plain_sise_leg(args, B, W, torch, oracle_check):
+def plain_sise_leg(args, B, W, torch, oracle_check, fp64=None, hbm_peak=None):
     """The plain SISe instance: 1,000 nodes x 365 days, 20,000 events; bit-exact
     against the oracle over the whole horizon."""
     from paper_1502_02908_gb300 import autotune
@@ -342,6 +342,11 @@ def plain_sise_leg(args, B, W, torch, oracle_check):
             "value": w.N * w.T / (ms / 1000), "unit": "node-days/s", "ms_per_step": ms, "steps": steps,
             "warmup": warm, "transitions_per_step": int(per[0]), "events_per_step": int(per[1]),
             "events_per_s": int(per[0] + per[1]) / (ms / 1000), "launch": best}
+    if fp64:
+        alone = ssa_alone(B, torch, w, 1, best)
+        line["roofline"] = dict(kernel="k_node_day_dealt (stochastic step)",
+                                **ssa_roofline(w, 1, alone, fp64, ms, hbm_peak))
+        line["roofline"]["hbm"]["note"] = "algorithmic bytes; the state stays in L2 within a step"
     if oracle_check:
         import oracle
         oracle.build()
@@ -418,7 +423,7 @@ def batched_leg(args, B, W, torch, plain_value, hbm_peak, fp64, oracle_check):
     return line
 
 
-def gradient_leg(args, B, W, G, torch):
+def gradient_leg(args, B, W, G, torch, oracle_check=False):
     """The score-function gradient on SISe, 10,000 nodes x 4,096 replicates x 365
     days, of the final prevalence and the 52 week-end prevalences with respect to
     (upsilon, gamma, beta, alpha): simulation with score terms, the reverse sweep of
@@ -452,6 +457,22 @@ def gradient_leg(args, B, W, G, torch):
                         "score": g1.tolist(), "score_se": se1.tolist(), "fd": fd.tolist(), "fd_se": fd_se.tolist(),
                         "z": z.tolist(), "max_z": float(z.max()), "within_3_se": bool(np.all(z < 3.0)),
                         "seconds": time.perf_counter() - t0}
+    if oracle_check:
+        # the oracle with score terms on 16 replicates, one per host thread, and the
+        # 4,096-replicate run extrapolated linearly from it
+        import oracle
+        oracle.build()
+        L = oracle.lib()
+        n = min(16, os.cpu_count() or 1)
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=n) as ex:
+            list(ex.map(lambda r: oracle.run(w, replicates=[r], score=True, lib_handle=L), range(n)))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n * w.N * w.T / dt, "unit": "node-days/s (with score terms)", "cores": n,
+                                "kind": "oracle",
+                                "sample": f"{n} replicates with score terms, whole horizon, one replicate per host "
+                                          f"thread; the {w.R}-replicate run extrapolated: "
+                                          f"{dt * w.R / n:.0f} s"}
     return line
 
 
@@ -931,13 +952,14 @@ def main():
         leg_s["sharded"] = time.perf_counter() - t
     if rank == 0:
         if not args.no_plain:
-            leg("sise_plain", lambda: plain_sise_leg(args, B, W, torch, oracle_check))
+            leg("sise_plain", lambda: plain_sise_leg(args, B, W, torch, oracle_check, fp64["fma_lane_ops_per_s"],
+                                                     peaks.get("hbm_gbs")))
         if not args.no_batched:
             leg("batched", lambda: batched_leg(args, B, W, torch, value / ws, peaks.get("hbm_gbs"),
                                                fp64["fma_lane_ops_per_s"], oracle_check))
         if not args.no_gradient:
             from paper_1502_02908_gb300 import gradient as G
-            leg("gradient", lambda: gradient_leg(args, B, W, G, torch))
+            leg("gradient", lambda: gradient_leg(args, B, W, G, torch, oracle_check))
         if not args.no_uneven:
             leg("uneven", lambda: uneven_leg(args, B, W, torch, oracle_check))
         if not args.no_synthetic:
