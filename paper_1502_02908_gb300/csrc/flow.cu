@@ -145,10 +145,11 @@ __device__ __forceinline__ void flow_release_units(const FlowArgs& f, int r, int
   for (int j = f.cuoff[c] + j0; j < f.cuoff[c + 1]; j += step) atomicAdd(f.unit_cnt + (size_t)r * f.U1 + f.cunit[j], 1u);
 }
 
-// A long component c of day d for replicate r, on a whole warp: lane s stages
-// herd s (up to kFlowSlots) in lane 0's slots; the lanes compute the Philox
-// blocks of 32 events at a time and lane 0 applies the events in input order
-// with each event's words shuffled to it.
+// A long component c of day d for replicate r, on a whole warp: its herds are
+// staged in the warp's shared-memory slots (the 32 lanes' regions are contiguous:
+// up to 32 x kFlowSlots herds); the lanes compute the Philox blocks of 32 events
+// at a time and lane 0 applies the events in input order with each event's words
+// shuffled to it.
 template <int NA>
 __device__ __forceinline__ bool flow_long_component(const FlowArgs& f, int d, int r, int c, int32_t* cnt0) {
   constexpr int NC = 2 * NA;
@@ -163,11 +164,11 @@ __device__ __forceinline__ bool flow_long_component(const FlowArgs& f, int d, in
   const uint32_t k0 = (uint32_t)ev.seed, k1 = (uint32_t)(ev.seed >> 32);
   const int q0 = f.cev[c], q1 = f.cev[c + 1];
   unsigned applied = 0, clamped = 0, skipped = 0;
-  if (k <= kFlowSlots) {
-    if (lane < k) {
-      const int v = f.cnode[n0 + lane];
+  if (k <= 32 * kFlowSlots) {
+    for (int sl = lane; sl < k; sl += 32) {
+      const int v = f.cnode[n0 + sl];
 #pragma unroll
-      for (int cc = 0; cc < NC; ++cc) cnt0[lane * NC + cc] = __ldcg(X + (size_t)cc * ev.N + v);
+      for (int cc = 0; cc < NC; ++cc) cnt0[sl * NC + cc] = __ldcg(X + (size_t)cc * ev.N + v);
     }
     __syncwarp();
     for (int qb = q0; qb < q1; qb += 32) {
@@ -199,13 +200,13 @@ __device__ __forceinline__ bool flow_long_component(const FlowArgs& f, int d, in
       }
     }
     __syncwarp();
-    if (lane < k) {
-      const int v = f.cnode[n0 + lane];
+    for (int sl = lane; sl < k; sl += 32) {
+      const int v = f.cnode[n0 + sl];
 #pragma unroll
-      for (int cc = 0; cc < NC; ++cc) X[(size_t)cc * ev.N + v] = cnt0[lane * NC + cc];
+      for (int cc = 0; cc < NC; ++cc) X[(size_t)cc * ev.N + v] = cnt0[sl * NC + cc];
     }
   } else if (lane == 0) {
-    // more herds than slots: the events straight on the global counts
+    // more herds than the warp's slots: the events straight on the global counts
     EvArgs e = ev;
     e.day = d;
     for (int q = q0; q < q1; ++q) {
