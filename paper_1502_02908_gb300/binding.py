@@ -61,7 +61,7 @@ class GenConfig(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-GEN_OPT_LAUNCH, GEN_OPT_WARP_THRESHOLD, GEN_OPT_GROUP_THRESHOLD = 1, 2, 3
+GEN_OPT_LAUNCH, GEN_OPT_WARP_THRESHOLD, GEN_OPT_GROUP_THRESHOLD, GEN_OPT_CLOCK_MARGIN = 1, 2, 3, 4
 
 
 def library_path() -> pathlib.Path:
@@ -578,6 +578,10 @@ class GenSim:
 
     def set_launch(self, mode):
         self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_LAUNCH, {"stream": 0, "graph": 1}[mode]))
+
+    def set_clock_margin(self, k):
+        """Binary32 clock margin 2^-k of the one-per-thread nodes, k in [0, 16] (0: exact only)."""
+        self._check(self.h, self.L.gen_set_option(self.h, GEN_OPT_CLOCK_MARGIN, int(k)))
 
     def set_warp_threshold(self, population):
         """Nodes with at least this initial population run one per warp (-1: automatic)."""

@@ -11,6 +11,7 @@
 #include "devmath.cuh"
 #include "general.h"
 #include "softdiv.cuh"
+#include "ssa_device.cuh"   // the binary32 helpers of the speculative clock
 
 #include <algorithm>
 
@@ -226,6 +227,151 @@ constexpr int kGenSeg = 8;                          // lanes per node of the gro
 constexpr int kGenWarps = kGenThreads / 32;
 constexpr int kGenEventWarps = 8192;                // event step: a warp per component up to this many
 
+// ---------------------------------------------------------------------------
+// Speculative binary32 direct method of one node-day (one thread), the general
+// form of the SISe kernels' certified clock.  With u = 2^-24, nt <= 32 and every
+// rate constant and continuous variable 0 or within [2^-30, 2^30], counts below
+// 2^21 (so every population below 2^23 is exact in binary32): a binary32 rate
+// (constant and variable truncated to binary32, 2u each; at most three products
+// and one IEEE quotient, u each) is within 8u of the binary64 rate, and never 0
+// unless that rate is 0; a left-to-right partial sum P~_j of non-negative terms
+// is within (nt + 8)u of P_j, r~ = a0~ u2~ within (nt + 10)u of r.  A selection
+// is taken in binary32 only when r~ and every threshold it is compared with are
+// at least 2 nt + 32 float ulps apart (their relative gap then exceeds the sum of
+// the two bounds), else the exact binary64 rule decides that step.  The clock:
+// tau~ = E~ / a0~ (E~ within 16u, the fast quotient 4u) is within (nt + 28)u <=
+// 60u of tau; accumulated exactly in Q62 it stays, at a decision (sum < 2.5),
+// within 150u plus k (2^-53 + 2^-62) of the binary64 chain, so a margin of 2^-16
+// (256u) makes "sum >= 1 + margin" a certain stop and "sum + margin < 1" a
+// certain continue; a decision in between hands the node-day back to the exact
+// method.  The results are the specification's, bit for bit.
+constexpr uint32_t kGenSpecMaxSteps = 1u << 21;
+
+// binary32 of rate j, in gen_rate's order; exactly 0 when the binary64 rate is.
+__device__ __forceinline__ float gen_rate_f32(const GenModelDev& m, const GenRepParams& p, const int32_t* x,
+                                              int stride, const float* yf, int j) {
+  float a = trunc_to_f32(p.rate[j]);
+  const int q = m.fy[j], fa = m.fa[j], fb = m.fb[j];
+  const uint32_t pm = m.pop[j];
+  if (q >= 0) a = __fmul_rn(a, yf[q]);
+  if (fa >= 0) a = __fmul_rn(a, small_int_to_f32(x[fa * stride]));
+  if (fb >= 0) a = __fmul_rn(a, small_int_to_f32(x[fb * stride]));
+  if (pm) {
+    const long long P = mask_sum(x, stride, pm, m.nc);
+    a = (P > 0 && a > 0.0f) ? __fdiv_rn(a, small_int_to_f32((int32_t)P)) : 0.0f;
+  }
+  return a;
+}
+
+// The exact rule of Eq. (sampling2) for state x and uniform u2, in two passes of
+// binary64 rates (a0 first, then the running sums): the transition chosen.
+__device__ __forceinline__ int gen_exact_choice(const GenModelDev& m, const GenRepParams& p, const int32_t* x,
+                                                int stride, const double* y, double u2) {
+  const int nt = m.nt;
+  double a0 = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    const double aj = gen_rate(m, p, x, stride, y, j);
+    a0 = j == 0 ? aj : __dadd_rn(a0, aj);
+  }
+  const double r = __dmul_rn(a0, u2);
+  double run = 0.0;
+  int last = -1;
+  for (int j = 0; j < nt; ++j) {
+    const double aj = gen_rate(m, p, x, stride, y, j);
+    run = j == 0 ? aj : __dadd_rn(run, aj);
+    if (pos(aj)) {
+      last = j;
+      if (le_nonneg(r, run)) return j;
+    }
+  }
+  return last;
+}
+
+// Transitions fired, -1 when a clock decision was too close to call (the caller
+// reruns the node-day exactly from its start), -2 when the binary32 bounds do not
+// hold for this node-day (the caller runs it exactly; x is untouched).  The
+// binary32 rates af_j and partial sums Pf_j live in the thread's row of R.P,
+// viewed as pairs of floats.
+__device__ __forceinline__ int32_t gen_node_day_spec(const GenModelDev& m, const GenRepParams& p, int32_t* x,
+                                                     int stride, const RateRow& R, const double* y, uint32_t v,
+                                                     uint32_t day, uint32_t rep, uint32_t k0, uint32_t k1,
+                                                     uint64_t margin) {
+  const int nt = m.nt, nc = m.nc, ny = m.ny;
+  if (nt == 0) return 0;                                      // no transitions: nothing fires
+  bool ok = true;
+  for (int j = 0; j < nt; ++j) {
+    const double c = p.rate[j];
+    const int e = (int)(double_bits(c) >> 52) - 1023;
+    if (pos(c) && (e < -30 || e > 29)) ok = false;
+  }
+  float yf[kGenMaxCont];
+  for (int q = 0; q < ny; ++q) {
+    const double c = y[q];
+    const int e = (int)(double_bits(c) >> 52) - 1023;
+    if (pos(c) && (e < -30 || e > 29)) ok = false;
+    if (!pos(c) && double_bits(c) != 0ull) ok = false;       // negative or -0: exact method
+    yf[q] = pos(c) ? trunc_to_f32(c) : 0.0f;
+  }
+  long long tot = 0;
+  for (int c = 0; c < nc; ++c) tot += x[c * stride];
+  if (!ok || tot >= (1 << 21)) return -2;
+  float* F = reinterpret_cast<float*>(R.P);
+  const int S2 = 2 * R.stride;
+  const int M = 2 * nt + 32;                                  // decisive gap in float ulps
+  float run = 0.0f;
+  for (int j = 0; j < nt; ++j) {
+    const float aj = gen_rate_f32(m, p, x, stride, yf, j);
+    run = j == 0 ? aj : __fadd_rn(run, aj);
+    F[j * S2] = aj;
+    F[j * S2 + 1] = run;
+  }
+  uint64_t tq = 0;
+  uint4 wn = philox10(make_uint4(v, day, 0u, rep), k0, k1);
+  for (uint32_t k = 0;; ++k) {
+    const float a0f = F[(nt - 1) * S2 + 1];
+    const uint4 w = wn;
+    wn = philox10(make_uint4(v, day, k + 1u, rep), k0, k1);
+    if (!(a0f > 0.0f)) return (int32_t)k;                     // every rate 0: the day ends
+    const float Ef = neglog_f32(((((uint64_t)w.y) << 32) | w.x) >> 12);
+    const float u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
+    const uint64_t sq = tq + q62_of(fminf(__fdividef(Ef, a0f), 1.5f));
+    if (sq >= kQ62One + margin) return (int32_t)k;
+    if (sq + margin >= kQ62One || k + 1u >= kGenSpecMaxSteps) return -1;
+    // selection: the first j with a_j > 0 and r <= P_j, each comparison decisive
+    const float rf = __fmul_rn(a0f, u2f);
+    const int ir = __float_as_int(rf);
+    int chosen = -1;
+    bool amb = ir < 0x00800000;
+    for (int j = 0; j < nt && !amb && chosen < 0; ++j) {
+      if (!(F[j * S2] > 0.0f)) continue;
+      const int d = ir - __float_as_int(F[j * S2 + 1]);
+      if (d <= -M) chosen = j;
+      else if (d < M) amb = true;
+    }
+    if (amb || chosen < 0) chosen = gen_exact_choice(m, p, x, stride, y, uniform_open(w.z, w.w));
+    for (int q = m.chg_off[chosen]; q < m.chg_off[chosen + 1]; ++q) {
+      const uint32_t c = m.chg[q];
+      const int32_t dlt = (int32_t)c >> 8;
+      x[(c & 0xffu) * stride] += dlt;
+      tot += dlt;
+    }
+    if (tot >= (1 << 22)) return -1;                          // populations no longer exact in binary32
+    uint32_t dm = m.dep[chosen];
+    const int j0 = dm ? __ffs(dm) - 1 : nt;
+    while (dm) {
+      const int j = __ffs(dm) - 1;
+      dm &= dm - 1u;
+      F[j * S2] = gen_rate_f32(m, p, x, stride, yf, j);
+    }
+    float pr = j0 > 0 ? F[(j0 - 1) * S2 + 1] : 0.0f;
+    for (int j = j0; j < nt; ++j) {
+      pr = j == 0 ? F[0] : __fadd_rn(pr, F[j * S2]);
+      F[j * S2 + 1] = pr;
+    }
+    tq = sq;
+  }
+}
+
 __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
   extern __shared__ int4 smem4[];
   GenModelDev& m = *reinterpret_cast<GenModelDev*>(smem4);
@@ -323,8 +469,15 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
     else if (kind == 1)
       fired = gen_seg_node_day<kGenSeg>(m, p, x, base, stride, R, ctau + warp * 32 + sb, cch + warp * 32 + sb, y,
                                         vv, (uint32_t)a.day, rep, k0, k1, sl, sb, has);
-    else
-      fired = gen_node_day(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1);
+    else {
+      int32_t f = -2;
+      if (a.clock_margin) {
+        f = gen_node_day_spec(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1, a.clock_margin);
+        if (f == -1)                               // too close to call: rerun from the day's start
+          for (int c = 0; c < nc; ++c) x[c * stride] = X[(size_t)c * N + v];
+      }
+      fired = f >= 0 ? (uint32_t)f : gen_node_day(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1);
+    }
     if (writer) {
       for (int c = 0; c < nc; ++c) X[(size_t)c * N + v] = x0[c * s0];
       if (m.y_source == kGenYPreEvent) {

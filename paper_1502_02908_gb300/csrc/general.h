@@ -51,6 +51,7 @@ struct GenSsaArgs {
   int32_t warp_blocks;          // blocks holding the warp nodes (set by the launcher)
   int32_t group_blocks;         // blocks holding the group nodes (set by the launcher)
   int32_t prologue;             // 1: first apply day - 1's continuous update (post-event or midpoint)
+  uint64_t clock_margin;        // Q62 margin of the thread method's binary32 clock (0: exact method only)
 };
 
 // Event record, 16 bytes: {node, dest, count, kind | select << 8 | shift row << 16}.

@@ -40,6 +40,7 @@ struct gen_handle {
   int32_t launch_mode = 0;          // 0 stream, 1 CUDA graph
   std::vector<int64_t> pop_sorted;  // initial node populations in the node order (descending)
   int32_t warp_threshold = -1;      // initial population from which a node gets a warp (-1: automatic)
+  int32_t clock_margin_log2 = 16;   // binary32 clock margin 2^-k of the thread method (0: exact only)
   int32_t group_threshold = -1;     // ... an 8-lane segment (-1: automatic)
   int32_t n_big = 0;                // nodes simulated one per warp
   int32_t n_mid = 0;                // nodes simulated four per warp
@@ -198,6 +199,7 @@ sim_status enqueue_days(gen_handle* h, int32_t d0, int32_t nd, cudaStream_t st) 
     s.order = h->d_order; s.ctr = h->d_ctr; s.seed = h->cfg.seed; s.rep_base = h->cfg.replicate_base;
     s.N = N; s.R = R; s.day = d; s.n_big = h->n_big; s.n_mid = h->n_mid;
     s.prologue = (d > d0 && h->ny > 0 && h->model.y_source != GEN_Y_PRE_EVENT) ? 1 : 0;
+    s.clock_margin = h->clock_margin_log2 > 0 ? (1ull << (62 - h->clock_margin_log2)) : 0ull;
     GCK(h, launch_gen_ssa(s, h->nt, h->nc, st), "stochastic step launch");
     const int32_t c0 = h->day_comp[d], c1 = h->day_comp[d + 1];
     if (c1 > c0) {
@@ -545,6 +547,12 @@ sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value) {
     free_graph(h);
     h->group_threshold = (int32_t)value;
     set_n_big(h);
+    return SIM_OK;
+  }
+  if (option == GEN_OPT_CLOCK_MARGIN) {
+    if (value < 0 || value > 16) return gfail(h, SIM_E_INVALID_ARG, "clock margin exponent %lld outside [0, 16]", (long long)value);
+    free_graph(h);
+    h->clock_margin_log2 = (int32_t)value;
     return SIM_OK;
   }
   return gfail(h, SIM_E_INVALID_ARG, "option %d unknown", option);

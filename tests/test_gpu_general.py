@@ -23,11 +23,12 @@ def _cuda():
     B.load_library()
 
 
-def _run(w, launch="stream", splits=None, warp=-1, group=-1):
+def _run(w, launch="stream", splits=None, warp=-1, group=-1, margin=16):
     s = B.GenSim.from_workload(w)
     s.set_launch(launch)
     s.set_warp_threshold(warp)
     s.set_group_threshold(group)
+    s.set_clock_margin(margin)
     for nd in (splits or [w.T]):
         s.run(nd)
     counts, y, day = s.state()
@@ -282,3 +283,39 @@ def test_component_counts_at_the_warp_deal_edges_bitexact(counts):
     ref = _same(w, _run(w))
     assert ref.counters[:, 1].sum() == 2 * len(w.events)
     _same(w, _run(w, launch="graph"), ref)
+
+
+@pytest.mark.parametrize("margin", [16, 12, 6, 1, 0])
+def test_binary32_clock_bitexact_at_every_margin(margin):
+    # the one-per-thread nodes' binary32 clock and selections against the general
+    # oracle: from the tightest safe margin (2^-16) to none (0: exact only); SEIRS
+    # with two continuous variables and frequency-dependent rates, one per thread
+    w = W.seirs_env(N=1200, T=40, n_events=10_000, R=2)
+    ref = oracle.run_general(w)
+    _same(w, _run(w, warp=1 << 30, group=1 << 30, margin=margin), ref)
+
+
+@pytest.mark.parametrize("freq", [True, False])
+def test_binary32_clock_sir_and_erlang(freq):
+    w = W.sir_general(N=1500, T=50, n_events=6000, R=2, freq=freq)
+    _same(w, _run(w, warp=1 << 30, group=1 << 30))
+    e = W.erlang_sis(N=900, T=30, n_events=4000, R=2)
+    _same(e, _run(e, warp=1 << 30, group=1 << 30))
+
+
+def test_binary32_clock_falls_back_outside_its_bounds():
+    # a rate constant beyond 2^30 and a node of more than 2^21 animals take the
+    # exact method; the results stay the specification's
+    w = W.sir_general(N=300, T=12, n_events=1200, R=2, freq=True, beta=0.4, gamma=0.1)
+    w.rates = w.rates.copy()
+    w.rates[1, 1] = 3.0e9                            # replicate 1: recovery constant above 2^30
+    w.u0 = w.u0.copy()
+    w.u0[0, 7] = 3_000_000                           # node 7: above 2^21 animals
+    _same(w, _run(w, warp=1 << 30, group=1 << 30))
+
+
+def test_binary32_clock_national_sise3_general_bitexact():
+    w = W.as_general(W.sise3_national(N=6000, T=60, n_events=180_000))
+    ref = oracle.run_general(w)
+    _same(w, _run(w, launch="graph", warp=600, group=300), ref)
+    _same(w, _run(w, launch="graph", warp=1 << 30, group=1 << 30, margin=3), ref)
