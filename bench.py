@@ -476,7 +476,7 @@ def gradient_leg(args, B, W, G, torch, oracle_check=False):
     return line
 
 
-def uneven_leg(args, B, W, torch, oracle_check):
+def uneven_leg(args, B, W, torch, oracle_check, fp64=None):
     """The uneven batch: 512 instances mixing SISe and SISe3 (node counts log-uniform
     in [100, 50,000], horizons 90-1,460 days, 80 events per node-year) advanced in
     one persistent work-stealing launch, against running the instances one after
@@ -526,9 +526,21 @@ def uneven_leg(args, B, W, torch, oracle_check):
                         "T 90-1,460 days, 80 events per node-year), one persistent launch",
             "value": node_days / (ms / 1000), "unit": "node-days/s", "ms_per_step": ms, "steps": steps,
             "warmup": warm, "node_days_per_step": node_days, "events": n_events,
-            "events_per_s": float(per_run[:, 0].sum() + per_run[:, 1].sum()) / (ms / 1000),
+            "transitions_per_s": float(per_run[:, 0].sum()) / (ms / 1000),
+            "events_per_s": float(per_run[:, 1].sum()) / (ms / 1000),
+            "block_shape": list(B.BATCH_SHAPES[0]),
             "one_after_another_ms": seq_ms, "speedup_vs_one_after_another": seq_ms / ms,
             "batch_equals_one_after_another": bool(same), "generate_s": gen_s, "load_events_s": load_s}
+    if fp64:
+        # arithmetic view of the whole persistent launch (its event items included,
+        # so a lower bound for the stochastic step): 40 FP64 lane-ops per draw
+        draws = float(per_run[:, 0].sum()) + node_days
+        achieved = FP64_PER_DRAW * draws / (ms / 1000)
+        line["roofline"] = {"kernel": "k_batch (persistent: stochastic-step chunks and event items)",
+                            "bound": "alu", "achieved": achieved / 1e9, "peak": fp64 / 1e9,
+                            "unit": "G FP64 lane-ops/s", "frac": achieved / fp64,
+                            "ops_count": f"{FP64_PER_DRAW} per draw (draws = transitions + node-days)",
+                            "peak_source": "measured: sim_fp64_peak (FP64 FMA lane-ops/s on this GPU)"}
     if oracle_check:
         rng = np.random.default_rng(5)
         pick = sorted(int(i) for i in rng.choice(len(ws), size=min(16, len(ws)), replace=False))
@@ -961,7 +973,7 @@ def main():
             from paper_1502_02908_gb300 import gradient as G
             leg("gradient", lambda: gradient_leg(args, B, W, G, torch, oracle_check))
         if not args.no_uneven:
-            leg("uneven", lambda: uneven_leg(args, B, W, torch, oracle_check))
+            leg("uneven", lambda: uneven_leg(args, B, W, torch, oracle_check, fp64["fma_lane_ops_per_s"]))
         if not args.no_synthetic:
             leg("synthetic", lambda: synthetic_leg(args, B, W, torch, oracle_check))
         if not args.no_fitting:

@@ -398,6 +398,20 @@ sim_status sim_goal(sim_handle* h, const int64_t* ref, int32_t day0, int32_t nda
  * handle are latched in it as for sim_run_days. */
 sim_status sim_run_batch(sim_handle** handles, int32_t n, const int32_t* until, void* stream);
 
+/* Block shape of sim_run_batch's persistent kernel (and of SIM_LAUNCH_PERSISTENT)
+ * for the calls that follow, process-wide: `threads` threads a block and
+ * `blocks_per_sm` resident blocks an SM, one of 256 x 2 (the default), 256 x 1
+ * and 128 x 4.  A stochastic-step chunk is one block's worth of nodes, one a
+ * thread (or of herds on the warp path, one a warp).  The blocks of an SM share
+ * 220 KB of shared memory for the staged event step: a day whose staged step
+ * needs more than 220 KB / blocks_per_sm runs the global-memory variant.  More
+ * resident blocks hide more of the stochastic step's latency at a register budget
+ * of 65,536 / (threads x blocks_per_sm) a thread.  Results do not depend on the
+ * shape (every random number is keyed by node, day and event position).  The
+ * paper has no counterpart: this is a launch-tuning knob.  Errors:
+ * SIM_E_INVALID_ARG for any other shape. */
+sim_status sim_batch_shape(int32_t threads, int32_t blocks_per_sm);
+
 /* Test hook for the dataflow loop's failure path: runs ndays days from the
  * current day (>= 1) with SIM_LAUNCH_FLOW, but with the first stochastic-step
  * unit's herd (replicate 0) held at readiness 0, so that its wait makes

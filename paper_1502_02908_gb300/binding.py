@@ -115,6 +115,7 @@ def load_library(build_if_missing: bool = True):
             "sim_pack_touched": [vp, vp, vp],
             "sim_unpack_touched": [vp, vp, i32, pi32, vp],
             "sim_run_batch": [P(vp), i32, pi32, vp],
+            "sim_batch_shape": [i32, i32],
             "sim_set_option": [vp, i32, i64],
             "sim_set_regions": [vp, pi32, i32],
             "sim_set_params": [vp, vp],
@@ -480,6 +481,16 @@ def run_batch(sims, until=None, stream=None):
     st = current_stream() if stream is None else ctypes.c_void_p(stream)
     status = L.sim_run_batch(arr, len(sims), _p(u, ctypes.c_int32), st)
     _check(L, None, status)
+
+
+BATCH_SHAPES = ((256, 2), (256, 1), (128, 4))   # the first is the library's default
+
+
+def batch_shape(threads: int, blocks_per_sm: int):
+    """Block shape (threads a block, resident blocks an SM) of run_batch's
+    persistent kernel, process-wide; one of BATCH_SHAPES."""
+    L = load_library()
+    _check(L, None, L.sim_batch_shape(int(threads), int(blocks_per_sm)))
 
 
 def debug_div(x, y, out, ref, n, device):

@@ -11,7 +11,8 @@ HERE = pathlib.Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 BUILD = HERE / "_build"
 LIB = BUILD / "libepisim.so"
-SOURCES = ["ssa.cu", "events.cu", "batch.cu", "noalloc.cu", "regions.cu", "general.cu", "peak.cu", "shard.cu", "flow.cu", "host.cpp",
+SOURCES = ["ssa.cu", "events.cu", "batch.cu", "batch_shape_256x1.cu", "batch_shape_256x2.cu", "batch_shape_128x4.cu",
+           "noalloc.cu", "regions.cu", "general.cu", "peak.cu", "shard.cu", "flow.cu", "host.cpp",
            "general_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",

@@ -4,11 +4,18 @@
 
 namespace episim {
 
-constexpr int kBatchThreads = 256;
+// Block shapes of the persistent kernel: threads a block x blocks an SM (the
+// register budget).  A stochastic-step chunk is one block's worth of nodes (one a
+// thread) or of large herds (one a warp), so the shape also sets the chunk size.
+enum class BatchShape { k256x1, k256x2, k128x4 };
+constexpr int batch_threads(BatchShape s) { return s == BatchShape::k128x4 ? 128 : 256; }
+constexpr int batch_min_blocks(BatchShape s) {
+  return s == BatchShape::k256x2 ? 2 : s == BatchShape::k128x4 ? 4 : 1;
+}
 constexpr int kBatchTimeout = 2;      // error bit: a bounded wait ran out
 
 struct BatchInst {
-  SsaArgs ssa;            // node order / warp split set for kBatchThreads-thread chunks
+  SsaArgs ssa;            // node order / warp split set for one block's chunks
   EvSmemArgs evs;
   EvArgs evg;
   const int32_t* day_smem;  // [max_days] shared memory of the staged event step (0: global variant)
@@ -36,7 +43,12 @@ struct BatchCtl {
   int smem_cap;
 };
 
-cudaError_t launch_batch(const BatchCtl& c, int grid, cudaStream_t st);
-cudaError_t batch_occupancy(int smem_bytes, int* blocks_per_sm);
+using BatchKernel = void (*)(BatchCtl);
+BatchKernel batch_kernel_256x1(bool score_any);
+BatchKernel batch_kernel_256x2(bool score_any);
+BatchKernel batch_kernel_128x4(bool score_any);
+
+cudaError_t launch_batch(const BatchCtl& c, BatchShape s, bool score_any, int grid, cudaStream_t st);
+cudaError_t batch_occupancy(BatchShape s, bool score_any, int smem_bytes, int* blocks_per_sm);
 
 }  // namespace episim

@@ -2023,6 +2023,7 @@ sim_status sim_debug_event_variant(sim_handle* h, int32_t global_only) {
 namespace {
 long long g_batch_spin_limit = 5000000;   // ~2 s of polling per wait
 bool g_batch_stall = false;               // test switch, see sim_debug_batch_stall
+BatchShape g_batch_shape = BatchShape::k256x2;   // see sim_batch_shape
 }
 
 sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void* stream) {
@@ -2053,7 +2054,13 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
   std::vector<long long> cumA(ni + 1, 0), cumB(ni + 1, 0), cumF(ni + 1, 0);
   long long n_counters = 0;
   int smem_cap = 0;
-  const int wpb = kBatchThreads / 32;
+  const BatchShape shape = g_batch_shape;
+  const int threads = batch_threads(shape);
+  // two blocks an SM share its 228 KB of shared memory; a day whose staged event
+  // step needs more takes the global-memory variant
+  const int smem_limit = batch_min_blocks(shape) > 1 ? (int)(kBatchSmemSM / batch_min_blocks(shape)) : (int)kEventsSmemLimit;
+  bool score_any = false;
+  const int wpb = threads / 32;
   for (int k = 0; k < ni; ++k) {
     sim_handle* h = hs[idx[k]];
     BatchInst& I = inst[k];
@@ -2064,8 +2071,9 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
     I.score = (h->cfg.flags & SIM_FLAG_SCORE) ? 1 : 0;
     if (I.score) { I.ssa.n_big = 0; I.ssa.warp_blocks = 0; }
     const int n_thread = h->cfg.n_nodes - I.ssa.n_big;
-    I.bpr = I.ssa.warp_blocks + (n_thread + kBatchThreads - 1) / kBatchThreads;
-    I.tbpr = (h->cfg.n_nodes + kBatchThreads - 1) / kBatchThreads;
+    I.bpr = I.ssa.warp_blocks + (n_thread + threads - 1) / threads;
+    I.tbpr = (h->cfg.n_nodes + threads - 1) / threads;
+    score_any = score_any || I.score;
     I.day0 = h->day;
     I.ndays = nd(idx[k]);
     I.has_events = h->events_loaded ? 1 : 0;
@@ -2081,7 +2089,8 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
     es.seed = h->cfg.seed; es.rep_base = h->cfg.replicate_base;
     es.N = h->cfg.n_nodes; es.R = h->cfg.n_replicates; es.Nc = h->nc; es.underflow_error = ev.underflow_error;
     if (h->events_loaded)
-      for (int32_t d = I.day0; d < I.day0 + I.ndays; ++d) smem_cap = std::max(smem_cap, h->day_smem[(size_t)d]);
+      for (int32_t d = I.day0; d < I.day0 + I.ndays; ++d)
+        if (h->day_smem[(size_t)d] <= smem_limit) smem_cap = std::max(smem_cap, h->day_smem[(size_t)d]);
     const long long R = h->cfg.n_replicates;
     cumA[k + 1] = cumA[k] + R * I.bpr;
     cumB[k + 1] = cumB[k] + R;
@@ -2146,13 +2155,13 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
   c.n_inst = ni; c.n_steps = S;
   c.smem_cap = smem_cap;
   int per_sm = 0, dev = 0, sms = 0;
-  cudaError_t e = batch_occupancy(smem_cap, &per_sm);
+  cudaError_t e = batch_occupancy(shape, score_any, smem_cap, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
   const long long want = (long long)sms * per_sm;
   const int grid = (int)std::max(1LL, std::min(want, c.total));
-  if (e == cudaSuccess) e = launch_batch(c, grid, st);
+  if (e == cudaSuccess) e = launch_batch(c, shape, score_any, grid, st);
   int berr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&berr, d_err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -2176,6 +2185,15 @@ sim_status sim_debug_flow_stall(sim_handle* h, int32_t ndays, int64_t spin_limit
   if (s != SIM_OK) return s;
   CK(h, cudaStreamSynchronize(nullptr), "stream synchronize");
   return check_latched(h);
+}
+
+sim_status sim_batch_shape(int32_t threads, int32_t blocks_per_sm) {
+  if (threads == 256 && blocks_per_sm == 1) g_batch_shape = BatchShape::k256x1;
+  else if (threads == 256 && blocks_per_sm == 2) g_batch_shape = BatchShape::k256x2;
+  else if (threads == 128 && blocks_per_sm == 4) g_batch_shape = BatchShape::k128x4;
+  else return fail(nullptr, SIM_E_INVALID_ARG, "batch shape %d x %d is not one of 256x1, 256x2, 128x4",
+                   threads, blocks_per_sm);
+  return SIM_OK;
 }
 
 sim_status sim_debug_batch_spin_limit(int64_t limit) {

@@ -187,6 +187,7 @@ cudaError_t launch_flow(const FlowArgs& f, int n_age, int sms, cudaStream_t st);
 // Shared memory the staged event step needs for a day (0 if the day has no events).
 size_t events_smem_bytes(int64_t n_events, int64_t n_levels, int64_t n_touched, int nc);
 constexpr size_t kEventsSmemLimit = 220 * 1024;
+constexpr size_t kBatchSmemSM = 220 * 1024;       // shared memory of the persistent batch blocks of an SM
 
 struct FinalizeArgs {
   SsaArgs s;                  // day = last simulated day; prologue semantics for day+1

@@ -134,3 +134,26 @@ def test_batch_and_graph_on_caller_tensors():
         assert np.array_equal(ct.cpu().numpy(), ref.counts), w.name
         np.testing.assert_allclose(pt.cpu().numpy(), ref.phi, rtol=1e-12, atol=0)
         s.close()
+
+
+@pytest.mark.parametrize("shape", B.BATCH_SHAPES)
+def test_batch_shapes_agree_and_match_oracle(shape):
+    # 12,000 events a day on 3,000 herds: the staged event step of a day needs
+    # more shared memory than one of two (or four) blocks an SM may take, so those
+    # shapes run such days through the global-memory variant
+    big = W.sise3_national(N=3000, T=16, n_events=192_000)
+    ws = [big] + W.uneven_batch(n_inst=5, N_lo=50, N_hi=2000, T_lo=10, T_hi=40, seed=13)
+    try:
+        B.batch_shape(*shape)
+        sims = [B.Sim.from_workload(w) for w in ws]
+        B.run_batch(sims)
+    finally:
+        B.batch_shape(*B.BATCH_SHAPES[0])
+    for w, s in zip(ws, sims):
+        ref = oracle.run(w)
+        c, p, d, pi, pn, ctr = _state(s)
+        assert d == w.T and np.array_equal(c, ref.counts), (shape, w.name)
+        assert np.array_equal(ctr, ref.counters), (shape, w.name)
+        np.testing.assert_allclose(p, ref.phi, rtol=1e-12, atol=0)
+        s.close()
+

@@ -225,3 +225,13 @@ def test_gradient_estimate_is_the_sample_covariance_of_f_and_the_score():
     np.testing.assert_allclose(se, np.sqrt((se8 ** 2) @ (J ** 2)), rtol=1e-10)
     with pytest.raises(B.SimError):
         B.gradient_estimate(np.stack(chunks), 1, J)
+
+
+def test_batch_shape_accepts_the_listed_shapes_only():
+    # host-side argument check only: no kernel runs until sim_run_batch
+    for shape in B.BATCH_SHAPES:
+        B.batch_shape(*shape)
+    for bad in ((384, 1), (256, 3), (512, 1), (0, 1), (-1, 2)):
+        with pytest.raises(B.SimError, match="batch shape"):
+            B.batch_shape(*bad)
+    B.batch_shape(*B.BATCH_SHAPES[0])
