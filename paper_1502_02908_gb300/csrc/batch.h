@@ -13,6 +13,7 @@ constexpr int batch_min_blocks(BatchShape s) {
   return s == BatchShape::k256x2 ? 2 : s == BatchShape::k128x4 ? 4 : 1;
 }
 constexpr int kBatchTimeout = 2;      // error bit: a bounded wait ran out
+constexpr int kBatchSubs = 4;         // blocks' worth of per-thread nodes in a chunk
 
 struct BatchInst {
   SsaArgs ssa;            // node order / warp split set for one block's chunks
@@ -21,6 +22,8 @@ struct BatchInst {
   const int32_t* day_smem;  // [max_days] shared memory of the staged event step (0: global variant)
   int32_t na, score, has_events;
   int32_t bpr;            // stochastic-step chunks per replicate
+  int32_t subs;           // blocks' worth of per-thread nodes in one chunk
+  int32_t n_thread;       // nodes on the per-thread path
   int32_t tbpr;           // finalisation chunks per replicate
   int32_t day0, ndays;
   unsigned* ssa_done;     // [R] chunks completed in this run

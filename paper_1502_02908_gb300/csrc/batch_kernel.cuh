@@ -65,7 +65,17 @@ __device__ __forceinline__ void run_chunk(const BatchInst& I, int r, int chunk, 
   SsaArgs a = I.ssa;
   a.day = day;
   a.prologue = prologue;
-  node_day_block<NA, SCORE, MODE>(a, r, chunk);
+  const int wb = (MODE == 0 && !SCORE) ? a.warp_blocks : 0;
+  if (MODE == 1 || chunk < wb) { node_day_block<NA, SCORE, MODE>(a, r, chunk); return; }
+  // A per-thread chunk is I.subs blocks' worth of nodes, run one after another with
+  // no barrier between them: a warp's time is then a sum over I.subs nodes a lane,
+  // and the block's closing barrier waits on sums that differ less than single
+  // node-days do.
+  const int q0 = (chunk - wb) * I.subs;
+  for (int j = 0; j < I.subs; ++j) {
+    if ((q0 + j) * (int)blockDim.x >= I.n_thread) break;
+    node_day_block<NA, SCORE, MODE>(a, r, wb + q0 + j);
+  }
 }
 
 template <bool SCORE_ANY>

@@ -2071,7 +2071,9 @@ sim_status sim_run_batch(sim_handle** hs, int32_t n, const int32_t* until, void*
     I.score = (h->cfg.flags & SIM_FLAG_SCORE) ? 1 : 0;
     if (I.score) { I.ssa.n_big = 0; I.ssa.warp_blocks = 0; }
     const int n_thread = h->cfg.n_nodes - I.ssa.n_big;
-    I.bpr = I.ssa.warp_blocks + (n_thread + threads - 1) / threads;
+    I.subs = kBatchSubs;
+    I.n_thread = n_thread;
+    I.bpr = I.ssa.warp_blocks + (n_thread + threads * kBatchSubs - 1) / (threads * kBatchSubs);
     I.tbpr = (h->cfg.n_nodes + threads - 1) / threads;
     score_any = score_any || I.score;
     I.day0 = h->day;
