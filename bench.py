@@ -370,12 +370,12 @@ def batched_leg(args, B, W, torch, plain_value, hbm_peak, fp64, oracle_check):
     also gives the all-core CPU baseline."""
     from paper_1502_02908_gb300 import autotune
     w = W.sise3_batched(R=256, T=365)
-    # the persistent kernel is for uneven batches; on one handle its per-replicate
-    # level-scheduled event step loses to the daily launches over a long horizon
-    best, _ = autotune.autotune(w, days=20, thresholds=(1 << 30,), modes=("stream", "graph"), repeats=1,
-                                groups=(1 << 30, 800))
+    # the daily CUDA-graph loop against the persistent work-stealing kernel in each
+    # block shape (256 replicates give it work enough to fill the GPU every day)
+    best, table = autotune.autotune(w, days=20, thresholds=(1 << 30,), modes=("graph", "persistent"), repeats=1,
+                                    groups=(1 << 30, 800), shapes=B.BATCH_SHAPES)
     sim = B.Sim.from_workload(w)
-    sim.set_group_threshold(best["group_threshold"]); sim.tune(best["warp_threshold"]); sim.set_launch(best["launch"])
+    autotune.apply(sim, best)
     u0 = np.repeat(w.u0[None], w.R, 0); phi0 = np.repeat(w.phi0[None], w.R, 0)
     steps, warm = 3, 1
     times = []
@@ -395,19 +395,35 @@ def batched_leg(args, B, W, torch, plain_value, hbm_peak, fp64, oracle_check):
     trans = int((c1[:, 0] - c0[:, 0]).sum()) // (warm + steps)
     evs = int((c1[:, 1] - c0[:, 1]).sum()) // (warm + steps)
     sim.close()
-    alone = ssa_alone(B, torch, w, w.R, best, steps=1)
+    B.batch_shape(*B.BATCH_SHAPES[0])
     line = {"workload": f"SISe3 national network, {w.R} replicates x {w.T} days, own (upsilon, gamma) each",
             "value": value, "unit": "node-days/s", "steps": steps, "warmup": warm, "ms_per_step": ms,
-            "events_per_s": (trans + evs) / (ms / 1000), "transitions_per_step": trans, "events_per_step": evs,
-            "launch": best, "vs_plain": value / plain_value,
-            "roofline": dict(kernel="k_node_day_dealt (stochastic step, 256 replicates)",
-                             **ssa_roofline(w, w.R, alone, fp64, ms, hbm_peak))}
-    line["roofline"]["hbm"]["note"] = "the state (counts and phi of 256 replicates, 0.6 GB read and written " \
-                                      "per launch) exceeds L2"
-    line["roofline"]["note"] = ("a fraction above 1: the kernel delivers the binary64 specification's "
-                                "decisions faster than the FP64 pipe could compute them, because it takes "
-                                "them in binary32 and fixed point within certified error margins (binary64 "
-                                "only inside them); its own limit is instruction issue")
+            "events_per_s": (trans + evs) / (ms / 1000), "transitions_per_s": trans / (ms / 1000),
+            "scheduled_events_per_s": evs / (ms / 1000), "transitions_per_step": trans, "events_per_step": evs,
+            "launch": best, "autotune_ms_20_days": {f"{m} {sh[0]}x{sh[1]}" if sh else m: round(t, 2)
+                                                     for _, g, m, sh, t in table if g == best["group_threshold"]},
+            "vs_plain": value / plain_value}
+    if best["launch"] == "persistent":
+        # arithmetic view of the whole persistent launch (event items included, so
+        # a lower bound for its stochastic-step chunks)
+        achieved = FP64_PER_DRAW * (trans + w.N * w.R * w.T) / (ms / 1000)
+        line["roofline"] = {"kernel": "k_batch %dx%d (persistent: stochastic-step chunks and event items)"
+                                      % tuple(best["batch_shape"]),
+                            "bound": "alu", "achieved": achieved / 1e9, "peak": fp64 / 1e9,
+                            "unit": "G FP64 lane-ops/s", "frac": achieved / fp64,
+                            "ops_count": f"{FP64_PER_DRAW} per draw (draws = transitions + node-days)",
+                            "peak_source": "measured: sim_fp64_peak (FP64 FMA lane-ops/s on this GPU)"}
+    else:
+        alone = ssa_alone(B, torch, w, w.R, best, steps=1)
+        line["roofline"] = dict(kernel="k_node_day_dealt (stochastic step, 256 replicates)",
+                                **ssa_roofline(w, w.R, alone, fp64, ms, hbm_peak))
+        line["roofline"]["hbm"]["note"] = "the state (counts and phi of 256 replicates, 0.6 GB read and " \
+                                          "written per launch) exceeds L2"
+    if line["roofline"]["frac"] > 1:
+        line["roofline"]["note"] = ("a fraction above 1: the kernel delivers the binary64 specification's "
+                                    "decisions faster than the FP64 pipe could compute them, because it takes "
+                                    "them in binary32 and fixed point within certified error margins (binary64 "
+                                    "only inside them); its own limit is instruction issue")
     if oracle_check:
         rng = np.random.default_rng(3)
         reps = sorted(int(r) for r in rng.choice(w.R, size=16, replace=False))
@@ -526,8 +542,9 @@ def uneven_leg(args, B, W, torch, oracle_check, fp64=None):
                         "T 90-1,460 days, 80 events per node-year), one persistent launch",
             "value": node_days / (ms / 1000), "unit": "node-days/s", "ms_per_step": ms, "steps": steps,
             "warmup": warm, "node_days_per_step": node_days, "events": n_events,
+            "events_per_s": float(per_run[:, 0].sum() + per_run[:, 1].sum()) / (ms / 1000),
             "transitions_per_s": float(per_run[:, 0].sum()) / (ms / 1000),
-            "events_per_s": float(per_run[:, 1].sum()) / (ms / 1000),
+            "scheduled_events_per_s": float(per_run[:, 1].sum()) / (ms / 1000),
             "block_shape": list(B.BATCH_SHAPES[0]),
             "one_after_another_ms": seq_ms, "speedup_vs_one_after_another": seq_ms / ms,
             "batch_equals_one_after_another": bool(same), "generate_s": gen_s, "load_events_s": load_s}

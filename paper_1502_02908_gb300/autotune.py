@@ -3,8 +3,8 @@
 For one workload it times each candidate setting -- the herd sizes from which a
 node gets a warp or an 8-lane group (warp-per-node, four-per-warp and
 thread-per-node stochastic step) and the launch mode of the daily loop (stream
-launches, a captured CUDA graph, or the persistent work-stealing kernel) -- over
-a short prefix of the horizon, checks
+launches, a captured CUDA graph, or the persistent work-stealing kernel, the
+latter in each of its block shapes) -- over a short prefix of the horizon, checks
 that every candidate ends in the bit-identical state (counts, phi, statistics,
 counters), and keeps the fastest.  Settings never change results; the check
 guards the implementation.
@@ -29,11 +29,31 @@ def _fingerprint(sim):
     return (c.tobytes(), p.tobytes(), pi.tobytes(), pn.tobytes(), ctr.tobytes(), d)
 
 
+def _candidates(thresholds, groups, modes, shapes):
+    for thr, gthr, mode in itertools.product(thresholds, groups, modes):
+        if gthr >= thr and gthr != groups[0]:
+            continue
+        for shape in (shapes if mode == "persistent" else (None,)):
+            yield thr, gthr, mode, shape
+
+
+def apply(sim, best):
+    """Puts an autotune result on a handle (the batch shape is process-wide)."""
+    sim.set_group_threshold(best["group_threshold"])
+    sim.tune(best["warp_threshold"])
+    sim.set_launch(best["launch"])
+    if best.get("batch_shape"):
+        B.batch_shape(*best["batch_shape"])
+
+
 def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES, repeats=2,
-             groups=(1 << 30,)):
-    """Returns (best {"warp_threshold", "group_threshold", "launch"}, table
-    [(threshold, group threshold, mode, ms)]).  Group thresholds at or above the
-    warp threshold are skipped (no herd would take the group path)."""
+             groups=(1 << 30,), shapes=(B.BATCH_SHAPES[0],)):
+    """Returns (best {"warp_threshold", "group_threshold", "launch", "batch_shape"},
+    table [(threshold, group threshold, mode, batch shape, ms)]).  Group thresholds
+    at or above the warp threshold are skipped (no herd would take the group path);
+    the persistent mode is timed in every block shape of `shapes` (batch_shape is
+    None for the other modes).  The library's default batch shape is restored
+    afterwards; apply() sets the winner's."""
     import torch
     w = workload
     nd = min(w.T, days if days is not None else max(10, w.T // 10))
@@ -43,12 +63,12 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
     ref = None
     table = []
     try:
-        for thr, gthr, mode in itertools.product(thresholds, groups, modes):
-            if gthr >= thr and gthr != groups[0]:
-                continue
+        for thr, gthr, mode, shape in _candidates(thresholds, groups, modes, shapes):
             sim.set_group_threshold(gthr)
             sim.tune(thr)
             sim.set_launch(mode)
+            if shape:
+                B.batch_shape(*shape)
             best = float("inf")
             for rep in range(repeats + 1):                 # first pass warms up (graph capture, caches)
                 sim.set_state(u0, phi0, 0)
@@ -64,12 +84,13 @@ def autotune(workload, days=None, thresholds=WARP_THRESHOLDS, modes=LAUNCH_MODES
             if ref is None:
                 ref = fp
             elif fp != ref:
-                raise AssertionError(f"setting ({thr}, {gthr}, {mode}) changed the results")
-            table.append((thr, gthr, mode, best))
+                raise AssertionError(f"setting ({thr}, {gthr}, {mode}, {shape}) changed the results")
+            table.append((thr, gthr, mode, shape, best))
     finally:
         sim.close()
-    thr, gthr, mode, _ = min(table, key=lambda x: x[3])
-    return {"warp_threshold": thr, "group_threshold": gthr, "launch": mode}, table
+        B.batch_shape(*B.BATCH_SHAPES[0])
+    thr, gthr, mode, shape, _ = min(table, key=lambda x: x[4])
+    return {"warp_threshold": thr, "group_threshold": gthr, "launch": mode, "batch_shape": shape}, table
 
 
 GENERAL_WARP_THRESHOLDS = (1 << 30, 1000, 600, 300)

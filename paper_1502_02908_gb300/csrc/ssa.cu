@@ -25,41 +25,44 @@ __global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_r
   node_day_block<NA, SCORE, MODE>(a, r, bx);
 }
 
-template <int NA>
+template <int NA, bool SCORE>
 __global__ void __launch_bounds__(512, 1) k_node_day_dealt(SsaArgs a) {
   grid_dependents_launch();
   grid_dependency_wait();                          // counts and phi of the previous step
-  node_day_dealt<NA>(a);
+  node_day_dealt<NA, SCORE>(a);
+}
+
+template <bool SCORE>
+static cudaError_t launch_dealt(const SsaArgs& a, int n_age, cudaStream_t st) {
+  // resident grid: G = SMs x (blocks of 8 warps an SM holds, fewer when the
+  // units do not fill them); W warps per block, each looping over its units
+  static int resident[2] = {0, 0};
+  const int which = n_age == 1 ? 0 : 1;
+  if (!resident[which]) {
+    int nb = 0;
+    cudaError_t e = n_age == 1
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<1, SCORE>, 256, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<3, SCORE>, 256, 0);
+    if (e != cudaSuccess) return e;
+    resident[which] = nb > 0 ? nb : 1;
+  }
+  const int64_t units =
+      (int64_t)a.R * (a.n_big + (a.n_mid + 3) / 4 + (a.n_list - a.n_big - a.n_mid + 31) / 32);
+  if (units == 0) return cudaSuccess;
+  const int64_t sms = a.sm_count > 0 ? a.sm_count : 1;
+  const int64_t wmax = a.max_warps > 0 ? a.max_warps : 8;
+  const int64_t fit = a.max_per_sm > 0 ? std::min(resident[which], a.max_per_sm) : resident[which];
+  const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(fit, (units + sms * wmax - 1) / (sms * wmax)));
+  const int64_t G = sms * per_sm;
+  const int W = (int)std::min<int64_t>(wmax, (units + G - 1) / G);
+  return n_age == 1
+      ? launch_maybe_pdl(k_node_day_dealt<1, SCORE>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a)
+      : launch_maybe_pdl(k_node_day_dealt<3, SCORE>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a);
 }
 
 template <int MODE>
 static cudaError_t launch_impl(const SsaArgs& a, int n_age, bool score, cudaStream_t st) {
-  if (MODE == 0 && !score && a.order) {
-    // resident grid: G = SMs x (blocks of 8 warps an SM holds, fewer when the
-    // units do not fill them); W warps per block, each looping over its units
-    static int resident[2] = {0, 0};
-    const int which = n_age == 1 ? 0 : 1;
-    if (!resident[which]) {
-      int nb = 0;
-      cudaError_t e = n_age == 1
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<1>, 256, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_node_day_dealt<3>, 256, 0);
-      if (e != cudaSuccess) return e;
-      resident[which] = nb > 0 ? nb : 1;
-    }
-    const int64_t units =
-        (int64_t)a.R * (a.n_big + (a.n_mid + 3) / 4 + (a.n_list - a.n_big - a.n_mid + 31) / 32);
-    if (units == 0) return cudaSuccess;
-    const int64_t sms = a.sm_count > 0 ? a.sm_count : 1;
-    const int64_t wmax = a.max_warps > 0 ? a.max_warps : 8;
-    const int64_t fit = a.max_per_sm > 0 ? std::min(resident[which], a.max_per_sm) : resident[which];
-    const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(fit, (units + sms * wmax - 1) / (sms * wmax)));
-    const int64_t G = sms * per_sm;
-    const int W = (int)std::min<int64_t>(wmax, (units + G - 1) / G);
-    return n_age == 1
-        ? launch_maybe_pdl(k_node_day_dealt<1>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a)
-        : launch_maybe_pdl(k_node_day_dealt<3>, dim3((unsigned)G), dim3(32 * W), 0, st, a.overlap != 0, a);
-  }
+  if (MODE == 0 && a.order) return score ? launch_dealt<true>(a, n_age, st) : launch_dealt<false>(a, n_age, st);
   const int warp_blocks = (MODE == 0 && !score) ? a.warp_blocks : 0;
   const int n_thread = (MODE == 0 && !score && a.order) ? a.n_list - a.n_big : a.node_hi - a.node_lo;
   const int bpr = warp_blocks + (n_thread + 255) / 256;

@@ -958,7 +958,10 @@ __device__ __forceinline__ void node_day_block(const SsaArgs& a, int r, int bx) 
 // one wave); warp w = slot * G + block takes units w, w + T, w + 2T, ... (T warps
 // in all), so every block receives the same mix of heavy and light units, the
 // heaviest ones first, and no SM carries the largest herds alone.
-template <int NA>
+// In score mode every node is a per-thread node (a.n_big = a.n_mid = 0) and runs
+// the binary64 method with its score terms; the dealing keeps herds of similar
+// size in a warp, so its lanes finish close together.
+template <int NA, bool SCORE>
 __device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
   const int lane = threadIdx.x & 31;
   const int64_t T = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -990,7 +993,7 @@ __device__ __forceinline__ void node_day_dealt(const SsaArgs& a) {
       v = active ? a.order[i] : 0;
     }
     if (a.skip && active && ((__ldg(a.skip + (v >> 5)) >> (v & 31)) & 1u)) active = false;
-    node_day_work<NA, false, 0>(a, r, v, active, role);
+    node_day_work<NA, SCORE, 0>(a, r, v, active, role);
   }
 }
 
