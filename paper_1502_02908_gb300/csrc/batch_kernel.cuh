@@ -4,18 +4,21 @@
 //
 // Work items, in a fixed global order that every block fetches from one atomic
 // counter: for each step s (day day0 + s of every instance still running), first
-// the stochastic-step chunks of every (instance, replicate) -- a chunk is 512
-// nodes with one thread each, or 16 large herds with one warp each -- then the
-// event item of every (instance, replicate); after the last step, finalisation
-// chunks (phi update and statistics of each instance's last day).  A chunk of
-// day d waits until the events of day d-1 of its replicate are applied; an event
-// item waits until every chunk of its day is done.  Dependencies always point to
-// earlier items, and a block fetches an item only while it runs, so the earliest
-// unfinished item can always proceed: no co-residency assumption is needed.
-// Waits spin on acquire loads with a bounded count (about two seconds); running
-// out sets an error and an abort flag that every block checks, and the kernel
-// returns instead of hanging.  State written by other blocks is read with
-// L2-coherent loads (see ssa_device.cuh, events_device.cuh).
+// the stochastic-step chunks of every (instance, replicate) -- a chunk is
+// kBatchSubs blocks' worth of nodes with one thread each, or one large herd per
+// warp -- then the event item of every (instance, replicate); after the last
+// step, finalisation chunks (phi update and statistics of each instance's last
+// day).  A chunk of day d waits until the events of day d-1 of its replicate are
+// applied; an event item waits until every chunk of its day is done.
+// Dependencies always point to earlier items, and a block fetches an item only
+// while it runs, so the earliest unfinished item can always proceed: no
+// co-residency assumption is needed.  The items a block fetches only increase,
+// so a block decodes each by a galloping search of the step and instance tables
+// from its previous item's position.  Waits spin on acquire loads with a bounded
+// count (about two seconds); running out sets an error and an abort flag that
+// every block checks, and the kernel returns instead of hanging.  State written
+// by other blocks is read with L2-coherent loads (see ssa_device.cuh,
+// events_device.cuh).
 #pragma once
 #include "batch.h"
 #include "events_device.cuh"
@@ -48,6 +51,22 @@ __device__ bool wait_at_least(const unsigned* p, unsigned target, const BatchCtl
   atomicOr(c.err, kBatchTimeout);
   atomicExch(c.abort, 1);
   return false;
+}
+
+// Largest k in [lo, n) with cum[k] <= x, for non-decreasing cum and cum[lo] <= x:
+// steps of 1, 2, 4, ... from lo, then a binary search within the last step.
+__device__ __forceinline__ int upper_index_from(const long long* cum, int n, int lo, long long x) {
+  int step = 1;
+  while (lo + step < n && cum[lo + step] <= x) {
+    lo += step;
+    step <<= 1;
+  }
+  int hi = min(lo + step, n) - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cum[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ int upper_index(const long long* cum, int n, long long x) {
@@ -115,6 +134,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_batch(BatchCtl c) {
   __shared__ int s_go;   // written by thread 0 only before the loop-top barrier
   __shared__ int s_ok;   // the item's dependency wait succeeded (its own flag: s_go
                          // may still be being read when the wait's result lands)
+  __shared__ int s_hs, s_hk, s_hkind;   // the previous item's step, instance and kind (0 chunk, 1 events)
+  if (threadIdx.x == 0) { s_hs = 0; s_hk = 0; s_hkind = -1; }   // read after the loop's first barrier
   for (;;) {
     if (threadIdx.x == 0) {
       s_item = (long long)atomicAdd(c.next, 1ull);
@@ -124,20 +145,21 @@ __global__ void __launch_bounds__(THREADS, MINB) k_batch(BatchCtl c) {
     const long long t = s_item;
     if (!s_go) break;
     if (t < c.total_main) {
-      const int s = upper_index(c.step_off, c.n_steps, t);
+      const int hs = s_hs, hk = s_hk, hkind = s_hkind;
+      const int s = upper_index_from(c.step_off, c.n_steps, hs, t);
       const long long local = t - c.step_off[s];
       const int act = c.active[s];
       const long long nA = c.cumA[act];
       int k, r, chunk = 0;
       const bool is_ssa = local < nA;
       if (is_ssa) {
-        k = upper_index(c.cumA, act, local);
+        k = upper_index_from(c.cumA, act, (hs == s && hkind == 0) ? hk : 0, local);
         const long long w = local - c.cumA[k];
         const BatchInst& I0 = c.inst[k];
         r = (int)(w / I0.bpr);
         chunk = (int)(w - (long long)r * I0.bpr);
       } else {
-        k = upper_index(c.cumB, act, local - nA);
+        k = upper_index_from(c.cumB, act, (hs == s && hkind == 1) ? hk : 0, local - nA);
         r = (int)(local - nA - c.cumB[k]);
       }
       const BatchInst& I = c.inst[k];
@@ -150,6 +172,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_batch(BatchCtl c) {
         else dispatch_events(I, r, day, smem, c.smem_cap);
       }
       __syncthreads();
+      if (threadIdx.x == 0) { s_hs = s; s_hk = k; s_hkind = is_ssa ? 0 : 1; }   // read after the next barrier
       if (threadIdx.x == 0 && s_ok) {
         __threadfence();
         if (is_ssa) atomicAdd(I.ssa_done + r, 1u);
