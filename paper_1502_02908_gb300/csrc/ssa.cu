@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256, 1) k_node_day(SsaArgs a, int blocks_per_r
 }
 
 template <int NA, bool SCORE>
-__global__ void __launch_bounds__(512, 1) k_node_day_dealt(SsaArgs a) {
+__global__ void __launch_bounds__(SCORE ? 256 : 512, SCORE ? (NA == 1 ? 4 : 3) : 1) k_node_day_dealt(SsaArgs a) {
   grid_dependents_launch();
   grid_dependency_wait();                          // counts and phi of the previous step
   node_day_dealt<NA, SCORE>(a);
