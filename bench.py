@@ -502,7 +502,10 @@ def uneven_leg(args, B, W, torch, oracle_check, fp64=None):
     ws = W.uneven_batch(n_inst=args.uneven_instances)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    sims = [B.Sim.from_workload(w) for w in ws]
+    # handles created on host threads, one instance each (their event scheduling is
+    # host work; the library keeps no state shared between handles)
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        sims = list(ex.map(B.Sim.from_workload, ws))
     load_s = time.perf_counter() - t0
     node_days = sum(w.N * w.T for w in ws)
     n_events = sum(len(w.events) for w in ws)
