@@ -169,17 +169,17 @@ sim_status gen_counters(gen_handle* h, int64_t* counters);
  *   GEN_OPT_GROUP_THRESHOLD: nodes below the warp threshold whose initial
  *       population is at least this run four per warp, 8 lanes and 8 draws at a
  *       time each (-1: automatic, 150); the rest one per thread;
- *   GEN_OPT_CLOCK_MARGIN: k in [0, 16].  The one-per-thread nodes first run each
- *       node-day with binary32 rates and partial sums and a binary32 clock
- *       accumulated in fixed point, whose distance to the binary64 clock of Eq.
- *       (numstep3) is bounded below 2^-16 of a day (product-form rates of at most
- *       32 transitions, constants and continuous variables within [2^-30, 2^30],
- *       populations below 2^21; other node-days run exactly); a selection is
- *       taken in binary32 only when decisive (Eq. (sampling2), else binary64), and
- *       a stop/continue decision within 2^-k of the day's end reruns the node-day
- *       with the binary64 arithmetic.  k = 16 (default) is the tightest safe
- *       margin; smaller k only reruns more node-days; 0 runs every node-day
- *       exactly. */
+ *   GEN_OPT_CLOCK_MARGIN: k in [0, 16].  Every node-day (one per thread, per
+ *       warp or per 8-lane segment) first runs with binary32 rates and partial
+ *       sums and a binary32 clock accumulated in fixed point, whose distance to
+ *       the binary64 clock of Eq. (numstep3) is bounded below 2^-16 of a day
+ *       (product-form rates of at most 32 transitions, constants and continuous
+ *       variables within [2^-30, 2^30], populations below 2^21; other node-days
+ *       run exactly); a selection is taken in binary32 only when decisive (Eq.
+ *       (sampling2), else binary64), and a stop/continue decision within 2^-k of
+ *       the day's end reruns the node-day with the binary64 arithmetic.  k = 16
+ *       (default) is the tightest safe margin; smaller k only reruns more
+ *       node-days; 0 runs every node-day exactly. */
 enum { GEN_OPT_LAUNCH = 1, GEN_OPT_WARP_THRESHOLD = 2, GEN_OPT_GROUP_THRESHOLD = 3, GEN_OPT_CLOCK_MARGIN = 4 };
 sim_status gen_set_option(gen_handle* h, int32_t option, int64_t value);
 

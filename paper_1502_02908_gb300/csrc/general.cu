@@ -372,7 +372,155 @@ __device__ __forceinline__ int32_t gen_node_day_spec(const GenModelDev& m, const
   }
 }
 
-__global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
+// The segment method (gen_seg_node_day) with the binary32 arithmetic of
+// gen_node_day_spec: each lane's draw gives E~ and u2~; the fixed-point iteration
+// over the segment's lanes chooses with binary32 rates and partial sums, a choice
+// taken in binary32 only when decisive (else gen_exact_choice at that lane's
+// state), so the converged choices are the binary64 method's; each lane's tau~ =
+// E~ / a0~ goes into an exact Q62 scan over the segment, and a lane is a certain
+// continue when its clock plus the margin is below 1, a certain stop when its
+// clock is at least 1 plus the margin (or it has no positive rate).  The day
+// ends at the first lane that is not a certain continue; when that lane is not a
+// certain stop, or a state it decides at leaves the bounds (a negative count, a
+// population of 2^22 or more), the segment gives up.  Returns, for every lane,
+// its segment's transitions fired; -1 when the segment gave up after changing
+// `base` (the caller reloads the day's start state and reruns the node-day with
+// gen_seg_node_day), -2 when the bounds fail at the day's start (nothing changed);
+// 0 for lanes without a node.  Every lane of the warp takes part in the
+// collectives.
+template <int SEG>
+__device__ __forceinline__ int32_t gen_seg_node_day_spec(const GenModelDev& m, const GenRepParams& p, int32_t* xl,
+                                                         int32_t* base, int stride, const RateRow& R,
+                                                         const double* y, uint32_t v, uint32_t day, uint32_t rep,
+                                                         uint32_t k0, uint32_t k1, int sl, int sb, bool live,
+                                                         uint64_t margin) {
+  const int nt = m.nt, nc = m.nc, ny = m.ny;
+  const unsigned full = 0xffffffffu;
+  const unsigned seg = SEG == 32 ? full : (((1u << SEG) - 1u) << sb);
+  const unsigned below = ((1u << sl) - 1u) << sb;
+  float* F = reinterpret_cast<float*>(R.P);
+  const int S2 = 2 * R.stride;
+  const int M = 2 * nt + 32;                                  // decisive gap in float ulps
+  int32_t status = 0;
+  float yf[kGenMaxCont];
+  bool act = live && nt > 0;
+  if (act) {
+    bool ok = true;
+    for (int j = 0; j < nt; ++j) {
+      const double c = p.rate[j];
+      const int e = (int)(double_bits(c) >> 52) - 1023;
+      if (pos(c) && (e < -30 || e > 29)) ok = false;
+    }
+    for (int q = 0; q < ny; ++q) {
+      const double c = y[q];
+      const int e = (int)(double_bits(c) >> 52) - 1023;
+      if (pos(c) && (e < -30 || e > 29)) ok = false;
+      if (!pos(c) && double_bits(c) != 0ull) ok = false;     // negative or -0: exact method
+      yf[q] = pos(c) ? trunc_to_f32(c) : 0.0f;
+    }
+    long long tot = 0;
+    for (int c = 0; c < nc; ++c) tot += base[c];
+    if (!ok || tot >= (1 << 21)) { status = -2; act = false; }
+  }
+  uint64_t tq = 0;
+  uint32_t fired = 0;
+  for (uint32_t kb = 0; __any_sync(full, act); kb += SEG) {
+    float Ef = 0.0f, u2f = 0.0f;
+    uint32_t wz = 0, ww = 0;
+    if (act) {
+      const uint4 w = philox10(make_uint4(v, day, kb + (uint32_t)sl, rep), k0, k1);
+      Ef = neglog_f32((((uint64_t)w.y << 32) | w.x) >> 12);
+      u2f = f32_of_q53(((((((uint64_t)w.w) << 32) | w.z) >> 12) << 1) | 1ull);
+      wz = w.z;
+      ww = w.w;
+    }
+    int choice = -1;
+    float a0f = 0.0f;
+    bool bad = false;
+    for (int pass = 0; pass <= SEG; ++pass) {
+      if (act)
+        for (int c = 0; c < nc; ++c) xl[c * stride] = base[c];
+      for (int j = 0; j < nt; ++j) {
+        const int cnt = __popc(__ballot_sync(full, act && choice == j) & below);
+        if (cnt) apply_changes(m, xl, stride, j, cnt);
+      }
+      int next = -1;
+      if (act) {
+        long long tot = 0;
+        bool neg = false;
+        for (int c = 0; c < nc; ++c) {
+          const int32_t xc = xl[c * stride];
+          tot += xc;
+          neg = neg || xc < 0;
+        }
+        bad = neg || tot >= (1 << 22);
+        float run = 0.0f;
+        for (int j = 0; j < nt; ++j) {
+          const float aj = bad ? 0.0f : gen_rate_f32(m, p, xl, stride, yf, j);
+          run = j == 0 ? aj : __fadd_rn(run, aj);
+          F[j * S2] = aj;
+          F[j * S2 + 1] = run;
+        }
+        a0f = run;
+        if (!bad && a0f > 0.0f) {
+          const float rf = __fmul_rn(a0f, u2f);
+          const int ir = __float_as_int(rf);
+          bool amb = ir < 0x00800000;
+          for (int j = 0; j < nt && !amb && next < 0; ++j) {
+            if (!(F[j * S2] > 0.0f)) continue;
+            const int d = ir - __float_as_int(F[j * S2 + 1]);
+            if (d <= -M) next = j;
+            else if (d < M) amb = true;
+          }
+          if (amb || next < 0) next = gen_exact_choice(m, p, xl, stride, y, uniform_open(wz, ww));
+        }
+      }
+      const bool changed = __any_sync(full, act && next != choice);
+      choice = next;
+      if (!changed) break;
+    }
+    // the segment's clock after each lane's draw, exactly in Q62
+    uint64_t S = (act && !bad && choice >= 0) ? q62_of(fminf(__fdividef(Ef, a0f), 1.5f)) : 0ull;
+    for (int d = 1; d < SEG; d <<= 1) {
+      const uint64_t o = __shfl_up_sync(full, S, d, SEG);
+      if (sl >= d) S += o;
+    }
+    S += tq;
+    const bool cont = act && !bad && choice >= 0 && S + margin < kQ62One;
+    const bool stop_ok = act && !bad && (choice < 0 || S >= kQ62One + margin);
+    const unsigned notc = __ballot_sync(full, act && !cont) & seg;
+    const unsigned sure = __ballot_sync(full, stop_ok) & seg;
+    int stop = SEG;
+    if (act && notc) {
+      const int e = __ffs(notc) - 1;                           // absolute lane of the first non-continue
+      if ((sure >> e) & 1u) stop = e - sb;
+      else status = -1;
+    }
+    if (act && status == 0 && stop == SEG && kb + 2u * SEG >= kGenSpecMaxSteps) status = -1;
+    const bool apply = act && status == 0;
+    const unsigned fired_lanes = stop == SEG ? seg : (((1u << stop) - 1u) << sb);
+    for (int j = 0; j < nt; ++j) {
+      const int cnt = __popc(__ballot_sync(full, apply && choice == j) & fired_lanes);
+      if (cnt && apply && sl == 0) apply_changes(m, base, 1, j, cnt);
+    }
+    __syncwarp();
+    const uint64_t tq_end = __shfl_sync(full, S, sb + SEG - 1);
+    if (act) {
+      if (status < 0) act = false;
+      else {
+        fired += (uint32_t)stop;
+        if (stop < SEG) act = false;
+        else tq = tq_end;
+      }
+    }
+  }
+  if (!live) return 0;
+  return status < 0 ? status : (int32_t)fired;
+}
+
+// At most 128 registers a thread (110 used): with __launch_bounds__ alone ptxas
+// settled at 72 and spilled inside the binary32 segment method.
+__global__ void __maxnreg__(128) k_gen_ssa(GenSsaArgs a) {
   extern __shared__ int4 smem4[];
   GenModelDev& m = *reinterpret_cast<GenModelDev*>(smem4);
   char* sp = reinterpret_cast<char*>(smem4) + sizeof(GenModelDev);
@@ -463,13 +611,31 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_ssa(GenSsaArgs a) {
     }
     const uint32_t rep = (uint32_t)(a.rep_base + r), k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const uint32_t vv = (uint32_t)(has ? v : 0);
-    if (kind == 0)
-      fired = gen_seg_node_day<32>(m, p, x, base, stride, R, ctau + warp * 32, cch + warp * 32, y, vv,
-                                   (uint32_t)a.day, rep, k0, k1, sl, sb, has);
-    else if (kind == 1)
-      fired = gen_seg_node_day<kGenSeg>(m, p, x, base, stride, R, ctau + warp * 32 + sb, cch + warp * 32 + sb, y,
-                                        vv, (uint32_t)a.day, rep, k0, k1, sl, sb, has);
-    else {
+    if (coop) {
+      // the binary32 segment method first; segments it hands back rerun with the
+      // binary64 one from the day's start (the global counts are the day's start
+      // until the writer stores below)
+      int32_t f = -2;
+      if (a.clock_margin)
+        f = kind == 0 ? gen_seg_node_day_spec<32>(m, p, x, base, stride, R, y, vv, (uint32_t)a.day, rep, k0, k1,
+                                                  sl, sb, has, a.clock_margin)
+                      : gen_seg_node_day_spec<kGenSeg>(m, p, x, base, stride, R, y, vv, (uint32_t)a.day, rep, k0,
+                                                       k1, sl, sb, has, a.clock_margin);
+      const bool redo = has && f < 0;
+      if (redo)
+        for (int c = sl; c < nc; c += (kind == 0 ? 32 : kGenSeg)) base[c] = X[(size_t)c * N + v];
+      __syncwarp();
+      uint32_t g = 0;
+      if (__any_sync(0xffffffffu, redo)) {
+        if (kind == 0)
+          g = gen_seg_node_day<32>(m, p, x, base, stride, R, ctau + warp * 32, cch + warp * 32, y, vv,
+                                   (uint32_t)a.day, rep, k0, k1, sl, sb, redo);
+        else
+          g = gen_seg_node_day<kGenSeg>(m, p, x, base, stride, R, ctau + warp * 32 + sb, cch + warp * 32 + sb,
+                                        y, vv, (uint32_t)a.day, rep, k0, k1, sl, sb, redo);
+      }
+      fired = redo ? g : (uint32_t)(f > 0 ? f : 0);
+    } else {
       int32_t f = -2;
       if (a.clock_margin) {
         f = gen_node_day_spec(m, p, x, stride, R, y, (uint32_t)v, (uint32_t)a.day, rep, k0, k1, a.clock_margin);

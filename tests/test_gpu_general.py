@@ -319,3 +319,29 @@ def test_binary32_clock_national_sise3_general_bitexact():
     ref = oracle.run_general(w)
     _same(w, _run(w, launch="graph", warp=600, group=300), ref)
     _same(w, _run(w, launch="graph", warp=1 << 30, group=1 << 30, margin=3), ref)
+
+
+@pytest.mark.parametrize("margin", [16, 6, 1])
+@pytest.mark.parametrize("tier", ["warp", "group"])
+def test_binary32_segment_methods_bitexact_at_margins(margin, tier):
+    # the warp (32-lane) and group (8-lane) methods' binary32 choices and Q62
+    # clock scan against the general oracle, every node on the one tier; smaller
+    # margins hand more node-days back to the binary64 segment method
+    w = W.seirs_env(N=600, T=30, n_events=5000, R=2)
+    ref = oracle.run_general(w)
+    kw = dict(warp=0) if tier == "warp" else dict(warp=1 << 30, group=0)
+    _same(w, _run(w, margin=margin, **kw), ref)
+
+
+@pytest.mark.parametrize("tier", ["warp", "group"])
+def test_binary32_segment_methods_fall_back_outside_bounds(tier):
+    # a rate constant beyond 2^30 (replicate 1) and a node of more than 2^21
+    # animals: those segments run the binary64 method while the others of their
+    # warp keep the binary32 one
+    w = W.sir_general(N=300, T=12, n_events=1200, R=2, freq=True, beta=0.4, gamma=0.1)
+    w.rates = w.rates.copy()
+    w.rates[1, 1] = 3.0e9
+    w.u0 = w.u0.copy()
+    w.u0[0, 7] = 3_000_000
+    kw = dict(warp=0) if tier == "warp" else dict(warp=1 << 30, group=0)
+    _same(w, _run(w, **kw))
