@@ -33,14 +33,18 @@ def test_score_gradient_agrees_with_central_differences():
 
 
 def test_score_gradient_agrees_with_central_differences_at_gradient_workload_size():
-    # the 10,000-node, 365-day gradient workload on 1,024 replicates: final
-    # prevalence and the week-26 prevalence, all four parameters
+    # the 10,000-node, 365-day gradient workload on 1,024 replicates: the final
+    # prevalence and the 52 week-end prevalences, all four parameters (212
+    # comparisons: none 4 standard errors apart, at most 3 beyond 3, where the
+    # normal law expects 0.57); final and week 26 each within 3
+    days = np.array([364] + [7 * k - 1 for k in range(1, 53)], np.int32)
     w = W.sise_gradient(R=1024)
-    spec = G.GradientSpec(w, np.array([364, 181]), chunk=1024)
+    spec = G.GradientSpec(w, days, chunk=1024)
     _, g, se = G.score_gradient(spec)
     fd, fd_se = G.fd_gradient(spec, rel_h=1e-3)
     z = np.abs(g - fd) / np.sqrt(se ** 2 + fd_se ** 2)
-    assert np.all(z < 3.0), (g, fd, se, fd_se)
+    assert z.max() < 4.0 and (z >= 3.0).sum() <= 3, (z.max(), (z >= 3.0).sum())
+    assert np.all(z[[0, 26]] < 3.0), (g[[0, 26]], fd[[0, 26]])
 
 
 def _sis_law(N, I0, ups, gam, alpha, beta, eps, phi0, T):
