@@ -235,3 +235,17 @@ def test_batch_shape_accepts_the_listed_shapes_only():
         with pytest.raises(B.SimError, match="batch shape"):
             B.batch_shape(*bad)
     B.batch_shape(*B.BATCH_SHAPES[0])
+
+
+def test_autotune_candidates_time_every_batch_shape_for_the_persistent_mode_only():
+    from paper_1502_02908_gb300 import autotune
+    shapes = B.BATCH_SHAPES
+    got = list(autotune._candidates((1 << 30, 200), (1 << 30, 100, 300), ("graph", "persistent"), shapes))
+    # a group threshold at or above the warp threshold is skipped (300 >= 200), except the first
+    pairs = {(t, g) for t, g, _, _ in got}
+    assert pairs == {(1 << 30, 1 << 30), (1 << 30, 100), (1 << 30, 300), (200, 1 << 30), (200, 100)}
+    for t, g, mode, shape in got:
+        assert (shape is None) == (mode != "persistent")
+    assert len(got) == len(pairs) * (1 + len(shapes))
+    per = [s for t, g, m, s in got if (t, g) == (200, 100) and m == "persistent"]
+    assert per == list(shapes)
